@@ -1,0 +1,353 @@
+"""Throughput of the DiffCloud loss + vertex gradient on GB300.
+
+One step = one dc_loss_traj call with the gradient (area CDF, sampling, fused bidirectional
+Chamfer, neighbour recovery, loss, adjoint scatter) over the 40-frame 50x50 cloth trajectory
+(10 000 samples against 10 000 target points per frame, 4.0e9 point pairs). The metric is
+point pairs per second (one pair = one (sim point, target point) distance of Eq. 1).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one independent trajectory per GPU (weak scaling, no collective
+on the data path). `--impl reference` times the FP64 CPU oracle on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+FLOP_PER_PAIR = 8        # 3 sub + 3 mul/fma products + 2 adds per distance, shared by both directions
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_chamfer launch on this workload, from
+# the ncu capture summarised in profiles/; None until measured for the current kernel.
+CHAMFER_TRAFFIC_BYTES = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="trajectory_50x50")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=20)
+    return p.parse_args()
+
+
+def make_workload(name):
+    if name == "trajectory_50x50":
+        return workloads.trajectory_50x50()
+    if name == "trajectory_100x100":
+        return workloads.trajectory_100x100()
+    if name == "single_frame":
+        return workloads.single_frame()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def config_of(tr, extra=None):
+    c = {"workload": tr.name, "frames": tr.T, "grid": f"{int(round(tr.V ** 0.5))}x"
+         f"{int(round(tr.V ** 0.5))}", "V": tr.V, "F": tr.F, "N": tr.n(0), "M": tr.m(0),
+         "pairs_per_step": tr.pairs(), "mode": "Eq. 1 bidirectional mean, fwd + vertex grad",
+         "seed": tr.meta.get("seed"),
+         "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+    c.update(extra or {})
+    return c
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), float(f[2]), f[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in busy for i, s in enumerate(r[3]) if s == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(busy), "power_w_max": max(r[2] for r in rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------------------------
+def oracle_sample_step(tr, k, n_s):
+    """One bounded sample: frame k % T with its first n_s draws and first n_s targets."""
+    import oracle
+
+    t = k % tr.T
+    oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t)[:n_s], tr.frame_targets(t)[:n_s],
+                 details=False)
+    return n_s * n_s
+
+
+def calibrate_oracle(tr, seconds):
+    """Largest sample size (up to a full frame) whose oracle step takes about `seconds`."""
+    n_full = min(tr.n(0), tr.m(0))
+    n_s = 1000
+    while True:
+        t0 = time.perf_counter()
+        oracle_sample_step(tr, 0, n_s)
+        el = time.perf_counter() - t0
+        if el >= seconds or n_s >= n_full:
+            return n_s, el
+        n_s = min(n_full, int(n_s * max(1.3, min(4.0, (seconds / max(el, 1e-4)) ** 0.5))))
+
+
+def cpu_baseline(tr, seconds):
+    import oracle
+
+    n_s, _ = calibrate_oracle(tr, min(seconds, 5.0))
+    t0 = time.perf_counter()
+    pairs, k = 0, 0
+    while time.perf_counter() - t0 < seconds or k == 0:
+        pairs += oracle_sample_step(tr, k, n_s)
+        k += 1
+    el = time.perf_counter() - t0
+    return {"value": pairs / el, "unit": "pairs/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{k} frames of {tr.name}, each cut to its first {n_s} draws and first "
+                      f"{n_s} targets (loss + vertex gradient, FP64 with float32 neighbour "
+                      f"decisions), {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    tr = make_workload(args.workload)
+    # size each step so that warmup + steps take about two minutes
+    per_step = max(0.02, min(1.0, 120.0 / max(1, args.steps + args.warmup)))
+    n_s, _ = calibrate_oracle(tr, per_step)
+    for k in range(args.warmup):
+        oracle_sample_step(tr, k, n_s)
+    t0 = time.perf_counter()
+    pairs = 0
+    for k in range(args.steps):
+        pairs += oracle_sample_step(tr, k, n_s)
+    el = time.perf_counter() - t0
+    value = pairs / el
+    cores = oracle.num_threads()
+    sample = (f"each step: one frame of {tr.name} cut to its first {n_s} draws and {n_s} "
+              f"targets (full frame: {tr.n(0)} x {tr.m(0)})")
+    line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_of(tr, {"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------------------------
+def run_gpu(args, rank, world, dist):
+    import torch
+
+    from paper_2204_03139_gb300 import _lib
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tr = make_workload(args.workload)
+    pairs = tr.pairs()
+    T, V, F, N, M = tr.T, tr.V, tr.F, tr.n(0), tr.m(0)
+
+    # inputs resident in HBM
+    v = torch.from_numpy(tr.verts).to(dev)
+    f = torch.from_numpy(tr.faces).to(dev)
+    d = torch.from_numpy(np.ascontiguousarray(tr.draws_tn3())).to(dev)
+    y = torch.from_numpy(np.ascontiguousarray(tr.targets_tm3())).to(dev)
+    out = {"loss_total": torch.empty(1, device=dev), "loss_frames": torch.empty(T, device=dev),
+           "grad_verts": torch.empty((T, V, 3), device=dev),
+           "nn_ab": torch.empty((T, N), dtype=torch.int32, device=dev),
+           "nn_ba": torch.empty((T, M), dtype=torch.int32, device=dev),
+           "ws": torch.empty(_lib.dc_workspace_size(T, V, F, N, M), dtype=torch.uint8,
+                             device=dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        _lib.dc_loss_traj(v, f, d, y, out=out)
+
+    clocks = ClockSampler(local)
+    r = _lib.dc_loss_traj(v, f, d, y, out=out, check=True)  # validates the inputs once
+    t_w = time.perf_counter()
+    k = 0
+    while k < args.warmup or time.perf_counter() - t_w < 1.0:
+        step()
+        k += 1
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = _lib.launch_count()
+    _lib.prof_start(args.steps)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    chamfer_ms, chamfer_n = _lib.prof_stop()
+    launches = _lib.launch_count() - launches0
+    clk = clocks.stop()
+    per = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(per)
+    if dist is not None:
+        import torch.distributed as td
+
+        tt = torch.tensor([total_ms], dtype=torch.float64)
+        td.all_reduce(tt, op=td.ReduceOp.MAX)
+        total_ms = float(tt[0])
+    ms_per_step = total_ms / args.steps
+    value = world * pairs / (ms_per_step / 1e3)
+
+    # end to end: host (pinned) inputs -> device, the call, gradient + loss back to the host
+    hv = torch.from_numpy(tr.verts).pin_memory()
+    hf = torch.from_numpy(tr.faces).pin_memory()
+    hd = torch.from_numpy(np.ascontiguousarray(tr.draws_tn3())).pin_memory()
+    hy = torch.from_numpy(np.ascontiguousarray(tr.targets_tm3())).pin_memory()
+    hg = torch.empty((T, V, 3), dtype=torch.float32).pin_memory()
+    hl = torch.empty(1, dtype=torch.float32).pin_memory()
+    dv, df, dd, dy = (torch.empty_like(hv, device=dev), torch.empty_like(hf, device=dev),
+                      torch.empty_like(hd, device=dev), torch.empty_like(hy, device=dev))
+    h2d = sum(t.numel() * t.element_size() for t in (hv, hf, hd, hy))
+    d2h = hg.numel() * 4 + 4
+
+    def e2e_step():
+        dv.copy_(hv, non_blocking=True)
+        df.copy_(hf, non_blocking=True)
+        dd.copy_(hd, non_blocking=True)
+        dy.copy_(hy, non_blocking=True)
+        rr = _lib.dc_loss_traj(dv, df, dd, dy, out=out)
+        hg.copy_(rr["grad_verts"], non_blocking=True)
+        hl.copy_(rr["loss_total"], non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    for _ in range(3):
+        e2e_step()
+    # wall time of each end-to-end step (the L2 flush before it is excluded)
+    e2e_times = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e_step()
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_value = world * pairs / statistics.mean(e2e_times)
+
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or 0.0
+    sm_max = clk.get("sm_max_mhz") or 0.0
+    peak_tflops = 2 * FP32_LANES_PER_SM * sms * sm_mhz * 1e6 / 1e12 if sm_mhz else None
+    chamfer_avg_s = chamfer_ms / max(1, chamfer_n) / 1e3
+    achieved = FLOP_PER_PAIR * pairs / chamfer_avg_s / 1e12 if chamfer_n else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": (achieved / peak_tflops) if (achieved and peak_tflops) else None,
+            "traffic": CHAMFER_TRAFFIC_BYTES, "kernel": "k_chamfer<true>",
+            "peak_basis": f"FP32 FMA peak 2 x {FP32_LANES_PER_SM} lanes x {sms} SMs x median "
+                          f"SM clock under load ({sm_mhz:.0f} MHz); at the {sm_max:.0f} MHz "
+                          f"maximum it is "
+                          f"{2 * FP32_LANES_PER_SM * sms * sm_max * 1e6 / 1e12:.1f} TFLOP/s",
+            "kernel_ms": chamfer_avg_s * 1e3,
+            "pairs_per_s_kernel": pairs / chamfer_avg_s if chamfer_n else None}
+    srt = sorted(per)
+    line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(tr, {"parallelism": f"{world} independent trajectories"
+                                     if world > 1 else "1 GPU"}),
+            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
+                                                                    int(0.99 * len(srt)))]},
+            "roofline": roof,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * statistics.mean(e2e_times)},
+            "loss_total": float(r["loss_total"][0])}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(tr, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+
+        td.init_process_group("gloo")
+        dist = td
+    if args.impl == "reference":
+        # the oracle pool runs before any GPU work (forking after CUDA init is unsafe)
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

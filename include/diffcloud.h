@@ -1,0 +1,192 @@
+/*
+ * diffcloud.h -- C ABI of the GB300 (sm_103a) DiffCloud loss library, libdiffcloud.so.
+ *
+ * The library computes the differentiable mesh-to-point-cloud loss of DiffCloud
+ * (Sundaresan et al., "DiffCloud: Real-to-Sim from Point Clouds with Differentiable
+ * Simulation and Rendering of Deformable Objects", 2022) and its gradient with respect to
+ * every mesh vertex, over a trajectory of T frames:
+ *
+ *   1. area-weighted surface sampling (Sec. III-B): face f_i = min{ f : C_f > r_f,i A },
+ *      C the inclusive prefix sum of the face areas, A = C_{F-1};
+ *      point x_i = w0 p_f0 + w1 p_f1 + w2 p_f2 (Eq. 3) with
+ *      w = (1 - sqrt(r1), sqrt(r1) (1 - r2), sqrt(r1) r2);
+ *   2. Chamfer distance against the frame's observed cloud by brute-force nearest
+ *      neighbours, bidirectional mean (Eq. 1) or unidirectional sim->real sum (Eq. 2);
+ *   3. the adjoint: dL/dx_i along the chosen neighbours, scattered to the face's vertices
+ *      with the barycentric weights as partial derivatives (Eq. 4). The face pick is
+ *      piecewise constant in the vertices and contributes nothing.
+ *
+ * Conventions shared by every entry point:
+ *   - Arithmetic is float32. Squared distances are evaluated as dx = a - b per coordinate,
+ *     d = fma(dz, dz, fma(dy, dy, dx * dx)); ties go to the lowest index.
+ *   - Every array pointer is a DEVICE pointer owned by the caller, C-contiguous, float32 or
+ *     int32 as typed, at least 4-byte aligned. The library never allocates device memory:
+ *     scratch comes from the caller's workspace `ws` (256-byte aligned, at least the size
+ *     the matching *_workspace_size function returns). A workspace serves one call at a
+ *     time; calls that overlap on the GPU need separate workspaces.
+ *   - Layouts: verts [T][V][3], faces [F][3] (0-based vertex indices, shared by all
+ *     frames), draws [T][N][3] holding (r_f, r1, r2) in [0, 1), targets [T][M][3].
+ *   - Coordinates must be finite with magnitude at most 1e15.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default
+ *     stream) and does not synchronise. Host-side argument errors are returned at once.
+ *     Errors found on the device (a face index out of range, a frame of zero total area,
+ *     a non-finite or oversized coordinate, a bounded wait that gave up) are recorded in
+ *     the workspace and read with dc_ws_status().
+ *   - Return value: DC_OK or a negative DC_E* code; dc_last_error() describes the last
+ *     failure of the calling thread.
+ */
+#ifndef DIFFCLOUD_H
+#define DIFFCLOUD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* dc_stream_t; /* the same type as cudaStream_t */
+
+enum {
+    DC_OK = 0,
+    DC_EINVAL = -1,       /* bad argument: null pointer, size <= 0, bad alignment, bad index */
+    DC_EDEGENERATE = -2,  /* a frame's total surface area is zero or not finite */
+    DC_ECUDA = -3,        /* a CUDA runtime call failed */
+    DC_ETIMEOUT = -4,     /* a bounded device-side wait gave up */
+    DC_EDEVICE = -5,      /* a device-side consistency check failed */
+    DC_ENOSPC = -6        /* the workspace is smaller than required */
+};
+
+enum {
+    DC_BIDIR_MEAN = 0, /* Eq. 1: mean_i min_j |x_i - y_j|^2 + mean_j min_i |y_j - x_i|^2 */
+    DC_UNIDIR_SUM = 1  /* Eq. 2: sum_i min_j |x_i - y_j|^2 (sim -> real only) */
+};
+
+/* Bytes of workspace the uniform-trajectory entry points need for T frames of V vertices,
+ * F faces, N samples and M target points (M may be 0 for dc_sample). */
+size_t dc_workspace_size(int T, int V, int F, int N, int M);
+
+/*
+ * dc_sample -- area-weighted surface sampling (Sec. III-B, Eq. 3).
+ *   points   [T][N][3] out: x_i of every frame.
+ *   face_idx [T][N] out, nullable: the picked face f_i.
+ *   bary     [T][N][3] out, nullable: (w0, w1, w2).
+ * Uses ws for the per-frame area CDF.
+ */
+int dc_sample(const float* verts, const int32_t* faces, const float* draws, int T, int V, int F,
+              int N, float* points, int32_t* face_idx, float* bary, void* ws, size_t ws_bytes,
+              dc_stream_t stream);
+
+/*
+ * dc_chamfer_fwd -- Chamfer distance of given clouds, per frame (Eq. 1 or Eq. 2).
+ *   a [T][N][3], b [T][M][3]; mode DC_BIDIR_MEAN or DC_UNIDIR_SUM.
+ *   loss  [T] out: L_t.
+ *   nn_ab [T][N] out, nullable: index into b of the nearest neighbour of each a point.
+ *   nn_ba [T][M] out, nullable (ignored in DC_UNIDIR_SUM): index into a of each b point's.
+ * ws sized by dc_workspace_size(T, 1, 1, N, M).
+ */
+int dc_chamfer_fwd(const float* a, const float* b, int T, int N, int M, int mode, float* loss,
+                   int32_t* nn_ab, int32_t* nn_ba, void* ws, size_t ws_bytes,
+                   dc_stream_t stream);
+
+/*
+ * dc_chamfer_bwd -- gradient of sum_t g_t L_t with respect to a (derivative of Eq. 1 / 2:
+ * 2 (a_i - b_j) along each chosen pair, scaled by 1/N, 1/M or 1).
+ *   nn_ab [T][N], nn_ba [T][M] (ignored in DC_UNIDIR_SUM) from dc_chamfer_fwd.
+ *   grad_loss [T]: g_t.   grad_a [T][N][3] out, overwritten.
+ * Needs no workspace. Accumulates with float atomics: the last bits may vary run to run.
+ */
+int dc_chamfer_bwd(const float* a, const float* b, const int32_t* nn_ab, const int32_t* nn_ba,
+                   int T, int N, int M, int mode, const float* grad_loss, float* grad_a,
+                   dc_stream_t stream);
+
+/*
+ * dc_loss_traj -- the whole loss over a trajectory, and optionally its vertex gradient
+ * (Sec. III-B, Eq. 1-4; the per-frame loss of Sec. III-C).
+ *   frame_w     [T] nullable (all ones): weights w_t.
+ *   loss_total  [1] out, nullable: sum_t w_t L_t (fixed summation order).
+ *   loss_frames [T] out: L_t.
+ *   grad_verts  [T][V][3] out, nullable: w_t dL_t/dverts_t (overwritten). When NULL only
+ *               the forward runs.
+ *   nn_ab [T][N], nn_ba [T][M] out, nullable: the neighbours (kept for dc_loss_traj_bwd).
+ * ws sized by dc_workspace_size(T, V, F, N, M). Sampled points live in ws only.
+ */
+int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
+                 const float* targets, int T, int V, int F, int N, int M, int mode,
+                 const float* frame_w, float* loss_total, float* loss_frames, float* grad_verts,
+                 int32_t* nn_ab, int32_t* nn_ba, void* ws, size_t ws_bytes,
+                 dc_stream_t stream);
+
+/*
+ * dc_loss_traj_bwd -- vertex gradient of sum_t g_t L_t given the neighbours a previous
+ * dc_loss_traj returned. The sampled points are recomputed from the draws (nothing from
+ * the forward is stored but nn_ab / nn_ba).
+ *   grad_frames [T]: g_t = dObjective/dL_t.   grad_verts [T][V][3] out, overwritten.
+ */
+int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draws,
+                     const float* targets, int T, int V, int F, int N, int M, int mode,
+                     const int32_t* nn_ab, const int32_t* nn_ba, const float* grad_frames,
+                     float* grad_verts, void* ws, size_t ws_bytes, dc_stream_t stream);
+
+/*
+ * Batched frames of uneven sizes (many trajectories, one launch sequence).
+ * One dc_frame per frame; pointers are device pointers; outputs are nullable.
+ */
+typedef struct dc_frame {
+    const float* verts;   /* [V][3] */
+    const int32_t* faces; /* [F][3] */
+    const float* draws;   /* [N][3] */
+    const float* targets; /* [M][3] */
+    int32_t V, F, N, M;
+    float weight;         /* w: weight of L in loss_total and multiplier of its gradient */
+    int32_t tag;          /* caller's label (e.g. trajectory id); not read by the library */
+    float* loss;          /* [1] out: L */
+    float* grad_verts;    /* [V][3] out, overwritten; NULL: no gradient for this frame */
+    int32_t* nn_ab;       /* [N] out, nullable */
+    int32_t* nn_ba;       /* [M] out, nullable */
+} dc_frame;
+
+/* Bytes of workspace a batch of n_frames frames needs. */
+size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames);
+
+/*
+ * dc_batch_plan -- validate the frames (host array), lay them out in ws and copy the
+ * descriptor tables into it (a host-to-device copy on `stream`). The plan stays valid
+ * while the frames' buffers stay where they are; it can be run many times.
+ */
+int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size_t ws_bytes,
+                  dc_stream_t stream);
+
+/*
+ * dc_batch_run -- forward (and the gradient of every frame whose grad_verts is set) of a
+ * planned batch: sampling, one persistent Chamfer launch over all frames, neighbours,
+ * losses, gradient scatter. loss_total [1] out, nullable: sum of w L over the frames.
+ * Reads only device memory, so the launch sequence can be captured in a CUDA graph.
+ */
+int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
+
+/*
+ * dc_ws_status -- synchronise `stream` and return the first device-side error recorded in
+ * ws by the calls issued so far (DC_OK if none). The next call on ws clears it.
+ */
+int dc_ws_status(const void* ws, dc_stream_t stream);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char* dc_last_error(void);
+
+/* Number of kernels this library has launched in this process (host-side count). */
+long long dc_launch_count(void);
+
+/*
+ * Timing of the Chamfer kernel: dc_prof_start(cap) makes the next (up to cap) Chamfer
+ * launches record a CUDA event pair on their stream; dc_prof_stop synchronises those
+ * events and returns their summed duration (ms) and count, and ends recording.
+ */
+int dc_prof_start(int cap);
+int dc_prof_stop(float* total_ms, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFCLOUD_H */

@@ -1,0 +1,268 @@
+"""ctypes binding of libdiffcloud.so: the C-ABI entry points under the same names.
+
+Argument marshalling only: tensors in, device pointers and the current CUDA stream out to
+the library, outputs and workspaces allocated with torch. Every step of the loss runs in the
+library's CUDA kernels; there is no other code path. If the library has not been built this
+module raises at first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+DC_OK, DC_EINVAL, DC_EDEGENERATE, DC_ECUDA, DC_ETIMEOUT, DC_EDEVICE, DC_ENOSPC = (
+    0, -1, -2, -3, -4, -5, -6)
+BIDIR_MEAN, UNIDIR_SUM = 0, 1
+_NAMES = {0: "DC_OK", -1: "DC_EINVAL", -2: "DC_EDEGENERATE", -3: "DC_ECUDA",
+          -4: "DC_ETIMEOUT", -5: "DC_EDEVICE", -6: "DC_ENOSPC"}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class DCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dc_frame(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("faces", ctypes.c_void_p),
+                ("draws", ctypes.c_void_p), ("targets", ctypes.c_void_p),
+                ("V", ctypes.c_int32), ("F", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("M", ctypes.c_int32), ("weight", ctypes.c_float), ("tag", ctypes.c_int32),
+                ("loss", ctypes.c_void_p), ("grad_verts", ctypes.c_void_p),
+                ("nn_ab", ctypes.c_void_p), ("nn_ba", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdiffcloud.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(
+                    f"{_build.LIB} is missing: build it with `python -c \"import "
+                    f"__graft_entry__ as g; g.build()\"` (nvcc, sm_103a)")
+            L = ctypes.CDLL(_build.LIB)
+            P, I, S, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
+            sig = {
+                "dc_workspace_size": (S, [I, I, I, I, I]),
+                "dc_sample": (I, [P, P, P, I, I, I, I, P, P, P, P, S, P]),
+                "dc_chamfer_fwd": (I, [P, P, I, I, I, I, P, P, P, P, S, P]),
+                "dc_chamfer_bwd": (I, [P, P, P, P, I, I, I, I, P, P, P]),
+                "dc_loss_traj": (I, [P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P, S, P]),
+                "dc_loss_traj_bwd": (I, [P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, S, P]),
+                "dc_batch_workspace_size": (S, [P, I]),
+                "dc_batch_plan": (I, [P, I, I, P, S, P]),
+                "dc_batch_run": (I, [P, P, P]),
+                "dc_ws_status": (I, [P, P]),
+                "dc_last_error": (ctypes.c_char_p, []),
+                "dc_launch_count": (ctypes.c_longlong, []),
+                "dc_prof_start": (I, [I]),
+                "dc_prof_stop": (I, [ctypes.POINTER(F), ctypes.POINTER(I)]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().dc_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != DC_OK:
+        raise DCError(rc, last_error())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("tensors must be on a CUDA device")
+    return t.device
+
+
+def _f32(t, name):
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def _i32(t, name):
+    if t.dtype != torch.int32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous int32 CUDA tensor")
+    return t
+
+
+# one workspace per (device, stream): calls on one stream are ordered, so they may share it
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    key = (torch.device(device).index, torch.cuda.current_stream(device).cuda_stream)
+    ws = _ws_cache.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        _ws_cache[key] = ws
+    return ws
+
+
+def ws_status(ws: torch.Tensor) -> int:
+    return int(lib().dc_ws_status(_ptr(ws), _stream(ws.device)))
+
+
+def check_ws(ws: torch.Tensor):
+    rc = ws_status(ws)
+    if rc != DC_OK:
+        raise DCError(rc, "device-side error recorded in the workspace")
+
+
+def dc_workspace_size(T, V, F, N, M) -> int:
+    return int(lib().dc_workspace_size(T, V, F, N, M))
+
+
+def dc_sample(verts, faces, draws, face_idx=True, bary=True, check=False):
+    """Area-weighted sampling (Sec. III-B, Eq. 3). verts [T,V,3], faces [F,3], draws [T,N,3].
+    Returns points [T,N,3], face_idx [T,N] and bary [T,N,3] (or None)."""
+    dev = _dev(verts)
+    _f32(verts, "verts"), _i32(faces, "faces"), _f32(draws, "draws")
+    T, V, F, N = verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1]
+    pts = torch.empty((T, N, 3), dtype=torch.float32, device=dev)
+    fi = torch.empty((T, N), dtype=torch.int32, device=dev) if face_idx else None
+    bc = torch.empty((T, N, 3), dtype=torch.float32, device=dev) if bary else None
+    nb = dc_workspace_size(T, V, F, N, 0)
+    if nb == 0:
+        raise DCError(DC_EINVAL, "bad sizes")
+    ws = workspace(nb, dev)
+    _check(lib().dc_sample(_ptr(verts), _ptr(faces), _ptr(draws), T, V, F, N, _ptr(pts),
+                           _ptr(fi), _ptr(bc), _ptr(ws), ws.numel(), _stream(dev)))
+    if check:
+        check_ws(ws)
+    return pts, fi, bc
+
+
+def dc_chamfer_fwd(a, b, mode=BIDIR_MEAN, check=False):
+    """Chamfer distance per frame (Eq. 1 / Eq. 2). a [T,N,3], b [T,M,3].
+    Returns loss [T], nn_ab [T,N], nn_ba [T,M] (None in Eq. 2)."""
+    dev = _dev(a)
+    _f32(a, "a"), _f32(b, "b")
+    T, N, M = a.shape[0], a.shape[1], b.shape[1]
+    loss = torch.empty(T, dtype=torch.float32, device=dev)
+    nn_ab = torch.empty((T, N), dtype=torch.int32, device=dev)
+    nn_ba = torch.empty((T, M), dtype=torch.int32, device=dev) if mode == BIDIR_MEAN else None
+    nb = dc_workspace_size(T, 1, 1, N, M)
+    if nb == 0:
+        raise DCError(DC_EINVAL, "bad sizes")
+    ws = workspace(nb, dev)
+    _check(lib().dc_chamfer_fwd(_ptr(a), _ptr(b), T, N, M, mode, _ptr(loss), _ptr(nn_ab),
+                                _ptr(nn_ba), _ptr(ws), ws.numel(), _stream(dev)))
+    if check:
+        check_ws(ws)
+    return loss, nn_ab, nn_ba
+
+
+def dc_chamfer_bwd(a, b, nn_ab, nn_ba, grad_loss, mode=BIDIR_MEAN):
+    """Gradient of sum_t g_t L_t w.r.t. a. Returns grad_a [T,N,3]."""
+    dev = _dev(a)
+    T, N, M = a.shape[0], a.shape[1], b.shape[1]
+    g = torch.empty_like(a)
+    _check(lib().dc_chamfer_bwd(_ptr(a), _ptr(b), _ptr(nn_ab), _ptr(nn_ba), T, N, M, mode,
+                                _ptr(_f32(grad_loss, "grad_loss")), _ptr(g), _stream(dev)))
+    return g
+
+
+def dc_loss_traj(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None, grad=True,
+                 total=True, nn=True, check=False, out=None):
+    """The whole loss over a trajectory (Sec. III-B, Eq. 1-4).
+
+    verts [T,V,3], faces [F,3], draws [T,N,3], targets [T,M,3] (CUDA, contiguous).
+    Returns a dict with loss_total [1] (or None), loss_frames [T], grad_verts [T,V,3] (or
+    None), nn_ab [T,N], nn_ba [T,M] (or None). `out` may supply preallocated outputs."""
+    dev = _dev(verts)
+    _f32(verts, "verts"), _i32(faces, "faces"), _f32(draws, "draws"), _f32(targets, "targets")
+    T, V, F, N, M = (verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1],
+                     targets.shape[1])
+    o = out if out is not None else {}
+    lt = o.get("loss_total") if total else None
+    if total and lt is None:
+        lt = torch.empty(1, dtype=torch.float32, device=dev)
+    lf = o.get("loss_frames")
+    if lf is None:
+        lf = torch.empty(T, dtype=torch.float32, device=dev)
+    gv = o.get("grad_verts") if grad else None
+    if grad and gv is None:
+        gv = torch.empty((T, V, 3), dtype=torch.float32, device=dev)
+    nab = nba = None
+    if nn:
+        nab = o.get("nn_ab")
+        if nab is None:
+            nab = torch.empty((T, N), dtype=torch.int32, device=dev)
+        if mode == BIDIR_MEAN:
+            nba = o.get("nn_ba")
+            if nba is None:
+                nba = torch.empty((T, M), dtype=torch.int32, device=dev)
+    nb = dc_workspace_size(T, V, F, N, M)
+    if nb == 0:
+        raise DCError(DC_EINVAL, "bad sizes")
+    ws = o.get("ws")
+    if ws is None or ws.numel() < nb:
+        ws = workspace(nb, dev)
+    _check(lib().dc_loss_traj(_ptr(verts), _ptr(faces), _ptr(draws), _ptr(targets), T, V, F, N,
+                              M, mode, _ptr(frame_w), _ptr(lt), _ptr(lf), _ptr(gv), _ptr(nab),
+                              _ptr(nba), _ptr(ws), ws.numel(), _stream(dev)))
+    if check:
+        check_ws(ws)
+    return {"loss_total": lt, "loss_frames": lf, "grad_verts": gv, "nn_ab": nab, "nn_ba": nba}
+
+
+def dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab, nn_ba, grad_frames,
+                     mode=BIDIR_MEAN, check=False, grad_verts=None):
+    """Vertex gradient of sum_t g_t L_t, recomputing the samples from the draws."""
+    dev = _dev(verts)
+    T, V, F, N, M = (verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1],
+                     targets.shape[1])
+    gv = grad_verts if grad_verts is not None else torch.empty_like(verts)
+    nb = dc_workspace_size(T, V, F, N, M)
+    ws = workspace(nb, dev)
+    _check(lib().dc_loss_traj_bwd(_ptr(verts), _ptr(faces), _ptr(draws), _ptr(targets), T, V,
+                                  F, N, M, mode, _ptr(nn_ab), _ptr(nn_ba),
+                                  _ptr(_f32(grad_frames, "grad_frames")), _ptr(gv), _ptr(ws),
+                                  ws.numel(), _stream(dev)))
+    if check:
+        check_ws(ws)
+    return gv
+
+
+def launch_count() -> int:
+    return int(lib().dc_launch_count())
+
+
+def prof_start(cap: int):
+    _check(lib().dc_prof_start(cap))
+
+
+def prof_stop() -> tuple[float, int]:
+    ms = ctypes.c_float(0.0)
+    n = ctypes.c_int(0)
+    _check(lib().dc_prof_stop(ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)

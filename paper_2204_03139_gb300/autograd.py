@@ -1,0 +1,40 @@
+"""torch.autograd binding of the trajectory loss (Sec. III-B / III-C, Eq. 1-4).
+
+The forward runs dc_loss_traj without the gradient and keeps only the nearest-neighbour
+indices; the backward calls dc_loss_traj_bwd, which recomputes the sampled points from the
+stored draws instead of storing them.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+
+class DCLoss(torch.autograd.Function):
+    """loss_frames[t] = L_t(verts[t]); differentiable with respect to verts only."""
+
+    @staticmethod
+    def forward(ctx, verts, faces, draws, targets, mode=_lib.BIDIR_MEAN):
+        verts = verts.detach().contiguous()
+        r = _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode, grad=False, total=False,
+                              nn=True)
+        ctx.mode = mode
+        nn_ba = r["nn_ba"] if r["nn_ba"] is not None else r["nn_ab"]
+        ctx.save_for_backward(verts, faces, draws, targets, r["nn_ab"], nn_ba)
+        return r["loss_frames"]
+
+    @staticmethod
+    def backward(ctx, grad_frames):
+        verts, faces, draws, targets, nn_ab, nn_ba = ctx.saved_tensors
+        g = _lib.dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab,
+                                  nn_ba if ctx.mode == _lib.BIDIR_MEAN else None,
+                                  grad_frames.detach().float().contiguous(), mode=ctx.mode)
+        return g, None, None, None, None
+
+
+def loss_traj(verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, frame_w=None):
+    """Differentiable sum_t w_t L_t (w_t = 1 by default) and the per-frame losses."""
+    lf = DCLoss.apply(verts, faces, draws, targets, mode)
+    w = torch.ones_like(lf) if frame_w is None else frame_w
+    return (w * lf).sum(), lf

@@ -1,0 +1,529 @@
+// Host entry points of libdiffcloud.so (declared in include/diffcloud.h).
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "dc_internal.cuh"
+
+namespace dc {
+
+// ---------------------------------------------------------------------------------------
+// bookkeeping: launch count, Chamfer-kernel event timing
+// ---------------------------------------------------------------------------------------
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static int g_prof_cap = 0, g_prof_n = 0;
+static std::vector<cudaEvent_t> g_prof_ev;
+
+void prof_before(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_on && g_prof_n < g_prof_cap) cudaEventRecord(g_prof_ev[2 * g_prof_n], s);
+}
+void prof_after(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_on && g_prof_n < g_prof_cap) {
+        cudaEventRecord(g_prof_ev[2 * g_prof_n + 1], s);
+        ++g_prof_n;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------------------
+Layout make_layout(const Sizes& s) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](long long bytes) {
+        size_t o = off;
+        off += ((size_t)(bytes > 0 ? bytes : 0) + 255) / 256 * 256;
+        return o;
+    };
+    L.hdr = take(sizeof(WsHeader));
+    L.frames = take(s.n_frames * (long long)sizeof(FrameDesc));
+    L.rowpre = take((s.n_frames + 1) * 4);
+    L.colpre = take((s.n_frames + 1) * 4);
+    L.unit_frame = take(s.n_units * 4);
+    L.unit_rb = take(s.n_units * 4);
+    L.unit_pre = take((s.n_units + 1) * 4);
+    L.cdf = take(s.sum_f * 4);
+    L.x = take(s.rows * 16);
+    L.fw = take(s.rows * 16);
+    L.tsoa = take(3 * s.cols * 4);
+    L.pab = take(s.rows * 8);
+    L.pba = take(s.cols * 8);
+    L.nnab = take(s.rows * 4);
+    L.nnba = take(s.cols * 4);
+    L.loss = take(s.n_frames * 4);
+    L.total = off;
+    return L;
+}
+
+Ws make_ws(void* base, const Layout& L) {
+    char* p = static_cast<char*>(base);
+    Ws w;
+    w.hdr = reinterpret_cast<WsHeader*>(p + L.hdr);
+    w.frames = reinterpret_cast<FrameDesc*>(p + L.frames);
+    w.rowpre = reinterpret_cast<int*>(p + L.rowpre);
+    w.colpre = reinterpret_cast<int*>(p + L.colpre);
+    w.unit_frame = reinterpret_cast<int*>(p + L.unit_frame);
+    w.unit_rb = reinterpret_cast<int*>(p + L.unit_rb);
+    w.unit_pre = reinterpret_cast<int*>(p + L.unit_pre);
+    w.cdf = reinterpret_cast<float*>(p + L.cdf);
+    w.x = reinterpret_cast<float4*>(p + L.x);
+    w.fw = reinterpret_cast<int4*>(p + L.fw);
+    w.tsoa = reinterpret_cast<float*>(p + L.tsoa);
+    w.pab = reinterpret_cast<unsigned long long*>(p + L.pab);
+    w.pba = reinterpret_cast<unsigned long long*>(p + L.pba);
+    w.nnab = reinterpret_cast<int*>(p + L.nnab);
+    w.nnba = reinterpret_cast<int*>(p + L.nnba);
+    w.loss = reinterpret_cast<float*>(p + L.loss);
+    return w;
+}
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(DC_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+constexpr long long INT_LIMIT = 0x7fffffffLL;
+
+// Sizes of a uniform trajectory; false if any derived count overflows int32.
+bool uniform_sizes(int T, int F, int N, int M, Sizes& s, int& upf, int& spu) {
+    const long long Npad = (long long)div_up(N, ROW_PAD) * ROW_PAD;
+    const long long Mpad = M > 0 ? (long long)div_up(M, COL_PAD) * COL_PAD : 0;
+    upf = div_up(N, ROWS_PER_UNIT);
+    spu = M > 0 ? div_up(M, SUB) : 0;
+    s.n_frames = T;
+    s.n_units = (long long)T * upf;
+    s.sum_f = (long long)T * F;
+    s.rows = (long long)T * Npad;
+    s.cols = (long long)T * Mpad;
+    const long long total_sub = s.n_units * spu;
+    return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
+           total_sub < INT_LIMIT && s.rows * 3 < INT_LIMIT * 16;
+}
+
+enum : unsigned {
+    PH_AREA = 1,
+    PH_SAMPLE = 2,
+    PH_TARGETS = 4,
+    PH_CHAMFER = 8,
+    PH_FINAL = 16,
+    PH_LOSS = 32,
+    PH_BWD = 64,
+};
+
+int check_ws(void* ws, size_t ws_bytes, size_t need) {
+    if (!ws) return fail(DC_EINVAL, "workspace is NULL");
+    if (!aligned(ws, 256)) return fail(DC_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(DC_ENOSPC, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+    return DC_OK;
+}
+
+int run_uniform(UniformArgs a, unsigned phases, float* loss_total, void* ws, size_t ws_bytes,
+                cudaStream_t st) {
+    Sizes sz;
+    int upf = 0, spu = 0;
+    if (!uniform_sizes(a.T, a.F, a.N, a.M, sz, upf, spu))
+        return fail(DC_EINVAL, "problem too large for 32-bit offsets");
+    a.units_per_frame = upf;
+    a.subs_per_unit = spu;
+    const Layout L = make_layout(sz);
+    int rc = check_ws(ws, ws_bytes, L.total);
+    if (rc) return rc;
+    const Ws w = make_ws(ws, L);
+    const int T = a.T, rows = (int)sz.rows, cols = (int)sz.cols;
+    cudaError_t e = launch_build_uniform(a, w, st);
+    if (!e && (phases & PH_AREA)) e = launch_area_cdf(w, T, st);
+    if (!e && (phases & PH_SAMPLE)) e = launch_sample(w, T, rows, st);
+    if (!e && (phases & PH_TARGETS) && cols > 0) e = launch_targets(w, T, cols, st);
+    if (!e && (phases & PH_CHAMFER))
+        e = launch_chamfer(w, (int)sz.n_units, (int)(sz.n_units * spu), a.mode, st);
+    if (!e && (phases & PH_FINAL)) e = launch_finalize(w, T, rows, cols, a.mode, st);
+    if (!e && (phases & PH_LOSS)) e = launch_loss(w, T, a.mode, loss_total, st);
+    if (!e && (phases & PH_BWD)) e = launch_bwd(w, T, a.V, a.mode, st);
+    if (e) return cuda_fail(e, "kernel launch");
+    return DC_OK;
+}
+
+int check_common(int T, int N, int M, int mode) {
+    if (T <= 0 || N <= 0 || M <= 0) return fail(DC_EINVAL, "T, N and M must be positive");
+    if (mode != DC_BIDIR_MEAN && mode != DC_UNIDIR_SUM) return fail(DC_EINVAL, "bad mode");
+    return DC_OK;
+}
+
+int check_ptrs(std::initializer_list<const void*> ps, const char* what) {
+    for (const void* p : ps) {
+        if (!p) return fail(DC_EINVAL, "%s: required pointer is NULL", what);
+        if (!aligned(p, 4)) return fail(DC_EINVAL, "%s: pointer not 4-byte aligned", what);
+    }
+    return DC_OK;
+}
+
+// ---- batch plans (host copy of what dc_batch_run needs to launch) ----
+struct Plan {
+    Sizes sz;
+    int mode, any_grad, max_v, total_sub;
+    size_t bytes;
+};
+std::mutex g_plan_mu;
+std::unordered_map<const void*, Plan> g_plans;
+
+}  // namespace
+}  // namespace dc
+
+using namespace dc;
+
+extern "C" {
+
+const char* dc_last_error(void) { return g_err; }
+
+long long dc_launch_count(void) { return g_launches.load(); }
+
+int dc_prof_start(int cap) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (cap <= 0) return fail(DC_EINVAL, "cap must be positive");
+    for (cudaEvent_t e : g_prof_ev) cudaEventDestroy(e);
+    g_prof_ev.assign(2 * (size_t)cap, nullptr);
+    for (auto& e : g_prof_ev) {
+        cudaError_t r = cudaEventCreate(&e);
+        if (r) return cuda_fail(r, "cudaEventCreate");
+    }
+    g_prof_cap = cap;
+    g_prof_n = 0;
+    g_prof_on = true;
+    return DC_OK;
+}
+
+int dc_prof_stop(float* total_ms, int* launches) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = false;
+    float sum = 0.f;
+    for (int i = 0; i < g_prof_n; ++i) {
+        cudaError_t r = cudaEventSynchronize(g_prof_ev[2 * i + 1]);
+        if (r) return cuda_fail(r, "cudaEventSynchronize");
+        float ms = 0.f;
+        r = cudaEventElapsedTime(&ms, g_prof_ev[2 * i], g_prof_ev[2 * i + 1]);
+        if (r) return cuda_fail(r, "cudaEventElapsedTime");
+        sum += ms;
+    }
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = g_prof_n;
+    return DC_OK;
+}
+
+size_t dc_workspace_size(int T, int V, int F, int N, int M) {
+    if (T <= 0 || V <= 0 || F <= 0 || N <= 0 || M < 0) return 0;
+    Sizes sz;
+    int upf, spu;
+    if (!uniform_sizes(T, F, N, M, sz, upf, spu)) return 0;
+    return make_layout(sz).total;
+}
+
+int dc_ws_status(const void* ws, dc_stream_t stream) {
+    if (!ws) return fail(DC_EINVAL, "workspace is NULL");
+    int st = 0;
+    const WsHeader* h = static_cast<const WsHeader*>(ws);
+    cudaError_t e = cudaMemcpyAsync(&st, &h->status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (!e) e = cudaStreamSynchronize(stream);
+    if (e) return cuda_fail(e, "dc_ws_status");
+    if (st != DC_OK) fail(st, "device-side error %d recorded in the workspace", st);
+    return st;
+}
+
+int dc_sample(const float* verts, const int32_t* faces, const float* draws, int T, int V, int F,
+              int N, float* points, int32_t* face_idx, float* bary, void* ws, size_t ws_bytes,
+              dc_stream_t stream) {
+    if (T <= 0 || V <= 0 || F <= 0 || N <= 0) return fail(DC_EINVAL, "sizes must be positive");
+    int rc = check_ptrs({verts, faces, draws, points}, "dc_sample");
+    if (rc) return rc;
+    UniformArgs a{};
+    a.verts = verts;
+    a.faces = faces;
+    a.draws = draws;
+    a.out_pts = points;
+    a.out_face = face_idx;
+    a.out_bary = bary;
+    a.T = T;
+    a.V = V;
+    a.F = F;
+    a.N = N;
+    a.M = 0;
+    a.mode = DC_BIDIR_MEAN;
+    return run_uniform(a, PH_AREA | PH_SAMPLE, nullptr, ws, ws_bytes, stream);
+}
+
+int dc_chamfer_fwd(const float* a_pts, const float* b, int T, int N, int M, int mode,
+                   float* loss, int32_t* nn_ab, int32_t* nn_ba, void* ws, size_t ws_bytes,
+                   dc_stream_t stream) {
+    int rc = check_common(T, N, M, mode);
+    if (rc) return rc;
+    rc = check_ptrs({a_pts, b, loss}, "dc_chamfer_fwd");
+    if (rc) return rc;
+    UniformArgs a{};
+    a.pts = a_pts;
+    a.tgt = b;
+    a.loss = loss;
+    a.nn_ab = nn_ab;
+    a.nn_ba = mode == DC_BIDIR_MEAN ? nn_ba : nullptr;
+    a.T = T;
+    a.V = 1;
+    a.F = 0;
+    a.N = N;
+    a.M = M;
+    a.mode = mode;
+    return run_uniform(a, PH_SAMPLE | PH_TARGETS | PH_CHAMFER | PH_FINAL | PH_LOSS, nullptr, ws,
+                       ws_bytes, stream);
+}
+
+int dc_chamfer_bwd(const float* a, const float* b, const int32_t* nn_ab, const int32_t* nn_ba,
+                   int T, int N, int M, int mode, const float* grad_loss, float* grad_a,
+                   dc_stream_t stream) {
+    int rc = check_common(T, N, M, mode);
+    if (rc) return rc;
+    rc = check_ptrs({a, b, nn_ab, grad_loss, grad_a}, "dc_chamfer_bwd");
+    if (rc) return rc;
+    if (mode == DC_BIDIR_MEAN && !nn_ba) return fail(DC_EINVAL, "nn_ba is required in Eq. 1");
+    cudaError_t e = launch_chamfer_bwd_points(a, b, nn_ab, nn_ba, T, N, M, mode, grad_loss,
+                                              grad_a, stream);
+    if (e) return cuda_fail(e, "dc_chamfer_bwd");
+    return DC_OK;
+}
+
+int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
+                 const float* targets, int T, int V, int F, int N, int M, int mode,
+                 const float* frame_w, float* loss_total, float* loss_frames, float* grad_verts,
+                 int32_t* nn_ab, int32_t* nn_ba, void* ws, size_t ws_bytes,
+                 dc_stream_t stream) {
+    int rc = check_common(T, N, M, mode);
+    if (rc) return rc;
+    if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
+    rc = check_ptrs({verts, faces, draws, targets, loss_frames}, "dc_loss_traj");
+    if (rc) return rc;
+    UniformArgs a{};
+    a.verts = verts;
+    a.faces = faces;
+    a.draws = draws;
+    a.tgt = targets;
+    a.loss = loss_frames;
+    a.nn_ab = nn_ab;
+    a.nn_ba = mode == DC_BIDIR_MEAN ? nn_ba : nullptr;
+    a.grad = grad_verts;
+    a.weight = frame_w;
+    a.T = T;
+    a.V = V;
+    a.F = F;
+    a.N = N;
+    a.M = M;
+    a.mode = mode;
+    unsigned ph = PH_AREA | PH_SAMPLE | PH_TARGETS | PH_CHAMFER | PH_FINAL | PH_LOSS;
+    if (grad_verts) ph |= PH_BWD;
+    return run_uniform(a, ph, loss_total, ws, ws_bytes, stream);
+}
+
+int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draws,
+                     const float* targets, int T, int V, int F, int N, int M, int mode,
+                     const int32_t* nn_ab, const int32_t* nn_ba, const float* grad_frames,
+                     float* grad_verts, void* ws, size_t ws_bytes, dc_stream_t stream) {
+    int rc = check_common(T, N, M, mode);
+    if (rc) return rc;
+    if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
+    rc = check_ptrs({verts, faces, draws, targets, nn_ab, grad_frames, grad_verts},
+                    "dc_loss_traj_bwd");
+    if (rc) return rc;
+    if (mode == DC_BIDIR_MEAN && !nn_ba) return fail(DC_EINVAL, "nn_ba is required in Eq. 1");
+    UniformArgs a{};
+    a.verts = verts;
+    a.faces = faces;
+    a.draws = draws;
+    a.tgt = targets;
+    a.nn_ab = const_cast<int32_t*>(nn_ab);
+    a.nn_ba = mode == DC_BIDIR_MEAN ? const_cast<int32_t*>(nn_ba) : nullptr;
+    a.grad = grad_verts;
+    a.gscale = grad_frames;
+    a.T = T;
+    a.V = V;
+    a.F = F;
+    a.N = N;
+    a.M = M;
+    a.mode = mode;
+    return run_uniform(a, PH_AREA | PH_SAMPLE | PH_BWD, nullptr, ws, ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------------------
+static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long& total_sub) {
+    s = Sizes{n, 0, 0, 0, 0};
+    total_sub = 0;
+    for (int k = 0; k < n; ++k) {
+        const long long upf = div_up(fr[k].N, ROWS_PER_UNIT);
+        s.n_units += upf;
+        s.sum_f += fr[k].F;
+        s.rows += (long long)div_up(fr[k].N, ROW_PAD) * ROW_PAD;
+        s.cols += (long long)div_up(fr[k].M, COL_PAD) * COL_PAD;
+        total_sub += upf * div_up(fr[k].M, SUB);
+    }
+    return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
+           total_sub < INT_LIMIT && s.n_units < INT_LIMIT;
+}
+
+size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames) {
+    if (!frames || n_frames <= 0) return 0;
+    for (int k = 0; k < n_frames; ++k)
+        if (frames[k].N <= 0 || frames[k].M <= 0 || frames[k].F <= 0 || frames[k].V <= 0)
+            return 0;
+    Sizes sz;
+    long long ts;
+    if (!batch_sizes(frames, n_frames, sz, ts)) return 0;
+    return make_layout(sz).total;
+}
+
+int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size_t ws_bytes,
+                  dc_stream_t stream) {
+    if (!frames || n_frames <= 0) return fail(DC_EINVAL, "no frames");
+    if (mode != DC_BIDIR_MEAN && mode != DC_UNIDIR_SUM) return fail(DC_EINVAL, "bad mode");
+    for (int k = 0; k < n_frames; ++k) {
+        const dc_frame& f = frames[k];
+        if (f.N <= 0 || f.M <= 0 || f.F <= 0 || f.V <= 0)
+            return fail(DC_EINVAL, "frame %d: sizes must be positive", k);
+        if (!f.verts || !f.faces || !f.draws || !f.targets)
+            return fail(DC_EINVAL, "frame %d: verts, faces, draws and targets are required", k);
+        if (!aligned(f.verts, 4) || !aligned(f.faces, 4) || !aligned(f.draws, 4) ||
+            !aligned(f.targets, 4))
+            return fail(DC_EINVAL, "frame %d: pointers must be 4-byte aligned", k);
+    }
+    Sizes sz;
+    long long total_sub;
+    if (!batch_sizes(frames, n_frames, sz, total_sub))
+        return fail(DC_EINVAL, "batch too large for 32-bit offsets");
+    const Layout L = make_layout(sz);
+    int rc = check_ws(ws, ws_bytes, L.total);
+    if (rc) return rc;
+    const Ws w = make_ws(ws, L);
+
+    // host image of the table regions [hdr, cdf)
+    std::vector<char> img(L.cdf, 0);
+    WsHeader* h = reinterpret_cast<WsHeader*>(img.data() + L.hdr);
+    FrameDesc* fd = reinterpret_cast<FrameDesc*>(img.data() + L.frames);
+    int* rowpre = reinterpret_cast<int*>(img.data() + L.rowpre);
+    int* colpre = reinterpret_cast<int*>(img.data() + L.colpre);
+    int* ufr = reinterpret_cast<int*>(img.data() + L.unit_frame);
+    int* urb = reinterpret_cast<int*>(img.data() + L.unit_rb);
+    int* upre = reinterpret_cast<int*>(img.data() + L.unit_pre);
+    int row0 = 0, col0 = 0, cdf0 = 0, unit = 0, sub = 0, any_grad = 0, max_v = 0;
+    for (int k = 0; k < n_frames; ++k) {
+        const dc_frame& f = frames[k];
+        FrameDesc d{};
+        d.verts = f.verts;
+        d.faces = f.faces;
+        d.draws = f.draws;
+        d.tgt = f.targets;
+        d.loss = f.loss ? f.loss : w.loss + k;
+        d.Npad = div_up(f.N, ROW_PAD) * ROW_PAD;
+        d.Mpad = div_up(f.M, COL_PAD) * COL_PAD;
+        d.nn_ab = f.nn_ab ? f.nn_ab : w.nnab + row0;
+        d.nn_ba = f.nn_ba ? f.nn_ba : w.nnba + col0;
+        d.grad = f.grad_verts;
+        d.V = f.V;
+        d.F = f.F;
+        d.N = f.N;
+        d.M = f.M;
+        d.weight = f.weight;
+        d.gscale = f.weight;
+        d.row0 = row0;
+        d.col0 = col0;
+        d.cdf0 = cdf0;
+        d.unit0 = unit;
+        fd[k] = d;
+        rowpre[k] = row0;
+        colpre[k] = col0;
+        const int upf = div_up(f.N, ROWS_PER_UNIT), spu = div_up(f.M, SUB);
+        for (int r = 0; r < upf; ++r, ++unit) {
+            ufr[unit] = k;
+            urb[unit] = r;
+            upre[unit] = sub;
+            sub += spu;
+        }
+        if (f.grad_verts) {
+            any_grad = 1;
+            if (f.V > max_v) max_v = f.V;
+        }
+        row0 += d.Npad;
+        col0 += d.Mpad;
+        cdf0 += f.F;
+    }
+    rowpre[n_frames] = row0;
+    colpre[n_frames] = col0;
+    upre[unit] = sub;
+    h->status = DC_OK;
+    h->n_frames = n_frames;
+    h->n_units = unit;
+    h->total_sub = sub;
+    h->total_rows = row0;
+    h->total_cols = col0;
+    h->sum_f = cdf0;
+    h->mode = mode;
+    h->planned = 1;
+    h->any_grad = any_grad;
+    h->max_v = max_v;
+    cudaError_t e = cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, stream);
+    if (!e) e = cudaStreamSynchronize(stream);
+    if (e) return cuda_fail(e, "dc_batch_plan copy");
+    Plan p;
+    p.sz = sz;
+    p.mode = mode;
+    p.any_grad = any_grad;
+    p.max_v = max_v;
+    p.total_sub = sub;
+    p.bytes = L.total;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[ws] = p;
+    return DC_OK;
+}
+
+int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
+    Plan p;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_plans.find(ws);
+        if (it == g_plans.end()) return fail(DC_EINVAL, "workspace holds no batch plan");
+        p = it->second;
+    }
+    const Layout L = make_layout(p.sz);
+    const Ws w = make_ws(ws, L);
+    const int n = (int)p.sz.n_frames, rows = (int)p.sz.rows, cols = (int)p.sz.cols;
+    cudaError_t e = launch_reset(w, stream);
+    if (!e) e = launch_area_cdf(w, n, stream);
+    if (!e) e = launch_sample(w, n, rows, stream);
+    if (!e) e = launch_targets(w, n, cols, stream);
+    if (!e) e = launch_chamfer(w, (int)p.sz.n_units, p.total_sub, p.mode, stream);
+    if (!e) e = launch_finalize(w, n, rows, cols, p.mode, stream);
+    if (!e) e = launch_loss(w, n, p.mode, loss_total, stream);
+    if (!e && p.any_grad) e = launch_bwd(w, n, p.max_v, p.mode, stream);
+    if (e) return cuda_fail(e, "dc_batch_run");
+    return DC_OK;
+}
+
+}  // extern "C"

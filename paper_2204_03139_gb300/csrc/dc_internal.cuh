@@ -1,0 +1,151 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/diffcloud.h"
+
+namespace dc {
+
+// ---------------------------------------------------------------------------------------
+// Chamfer tiling. A CTA of WARPS warps owns one "unit": ROWS_PER_UNIT consecutive sim points
+// of one frame, ROWS_PER_THREAD per thread held in registers. Targets stream through shared
+// memory in chunks of CHUNK points (structure-of-arrays planes, bulk-copied); inside a
+// chunk the per-row minimum is tracked per sub-chunk of SUB targets, so that a row's
+// nearest neighbour can later be found again by re-scanning one sub-chunk.
+// ---------------------------------------------------------------------------------------
+constexpr int ROWS_PER_THREAD = 8;
+constexpr int WARPS = 4;
+constexpr int THREADS = 32 * WARPS;
+constexpr int ROWS_PER_WARP = 32 * ROWS_PER_THREAD;       // 256
+constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * WARPS;      // 1024
+constexpr int SUB = 64;                                   // targets per tracked sub-chunk
+constexpr int CHUNK = 256;                                // targets per staged chunk
+constexpr int SUBS_PER_CHUNK = CHUNK / SUB;
+constexpr int ROW_PAD = ROWS_PER_WARP;                    // sim points padded to this
+constexpr int COL_PAD = CHUNK;                            // target points padded to this
+
+constexpr float COORD_MAX = 1e15f;
+constexpr unsigned long long EMPTY = ~0ull;
+
+// Everything a kernel needs to know about one frame. Built on the device for uniform
+// trajectories, on the host for batches.
+struct FrameDesc {
+    const float* verts;   // [V][3]; NULL for a frame given as points (Chamfer only)
+    const int* faces;     // [F][3]
+    const float* draws;   // [N][3]
+    const float* pts;     // [N][3] sim points given directly; NULL when sampled
+    const float* tgt;     // [M][3]
+    float* loss;          // [1] out
+    int* nn_ab;           // [N] out (user buffer or workspace)
+    int* nn_ba;           // [M] out (user buffer or workspace)
+    float* grad;          // [V][3] out, NULL: no gradient
+    float* out_pts;       // [N][3] out of dc_sample, nullable
+    int* out_face;        // [N] out of dc_sample, nullable
+    float* out_bary;      // [N][3] out of dc_sample, nullable
+    int V, F, N, M;
+    int Npad, Mpad;       // N rounded up to ROW_PAD, M to COL_PAD
+    float weight;         // w_t in the total loss
+    float gscale;         // multiplier of dL_t in the gradient
+    int row0;             // offset of this frame's sim points in the padded row buffers
+    int col0;             // offset of this frame's targets in the padded column buffers
+    int cdf0;             // offset of this frame's CDF
+    int unit0;            // first Chamfer unit of this frame
+};
+
+// Header at the start of every workspace.
+struct WsHeader {
+    int status;       // first device-detected error (DC_OK if none)
+    int n_frames;
+    int n_units;
+    int total_sub;    // sum over units of their sub-chunk count
+    int total_rows;   // sum of Npad
+    int total_cols;   // sum of Mpad
+    int sum_f;        // sum of F
+    int mode;
+    int planned;      // batch plan written
+    int any_grad;
+    int max_v;        // largest V among frames with a gradient
+    int pad[53];
+};
+
+// Byte offsets of every region of a workspace (computed on the host).
+struct Layout {
+    size_t hdr, frames, rowpre, colpre, unit_frame, unit_rb, unit_pre, cdf, x, fw, tsoa, pab,
+        pba, nnab, nnba, loss, total;
+};
+
+struct Sizes {
+    long long n_frames, n_units, sum_f, rows, cols;
+};
+
+Layout make_layout(const Sizes& s);
+
+// Typed views of a workspace.
+struct Ws {
+    WsHeader* hdr;
+    FrameDesc* frames;
+    int* rowpre;       // [n_frames + 1] prefix of Npad
+    int* colpre;       // [n_frames + 1] prefix of Mpad
+    int* unit_frame;   // [n_units]
+    int* unit_rb;      // [n_units] row block of the unit within its frame
+    int* unit_pre;     // [n_units + 1] prefix of sub-chunk counts
+    float* cdf;        // [sum F]
+    float4* x;         // [rows] sampled points (w lane unused), NaN beyond N
+    int4* fw;          // [rows] (face, w0, w1, w2 bits)
+    float* tsoa;       // [3 * cols] per frame: X[Mpad], Y[Mpad], Z[Mpad], NaN beyond M
+    unsigned long long* pab;  // [rows] packed (d bits << 32 | sub-chunk)
+    unsigned long long* pba;  // [cols] packed (d bits << 32 | row group)
+    int* nnab;         // [rows] fallback neighbour buffers
+    int* nnba;         // [cols]
+    float* loss;       // [n_frames] fallback loss buffer
+};
+
+Ws make_ws(void* base, const Layout& L);
+
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+__host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------------------
+// kernel launchers (kernels.cu); each returns cudaGetLastError()
+// ---------------------------------------------------------------------------------------
+struct UniformArgs {
+    const float* verts;
+    const int* faces;
+    const float* draws;
+    const float* pts;
+    const float* tgt;
+    float* loss;
+    int* nn_ab;
+    int* nn_ba;
+    float* grad;
+    float* out_pts;
+    int* out_face;
+    float* out_bary;
+    const float* weight;   // [T] nullable
+    const float* gscale;   // [T] nullable: defaults to weight
+    int T, V, F, N, M, mode, units_per_frame, subs_per_unit;
+};
+
+cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s);
+cudaError_t launch_reset(const Ws& w, cudaStream_t s);
+cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s);
+cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s);
+cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s);
+cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, cudaStream_t s);
+cudaError_t launch_finalize(const Ws& w, int n_frames, int rows, int cols, int mode,
+                            cudaStream_t s);
+cudaError_t launch_loss(const Ws& w, int n_frames, int mode, float* total, cudaStream_t s);
+cudaError_t launch_bwd(const Ws& w, int n_frames, int max_v, int mode, cudaStream_t s);
+cudaError_t launch_chamfer_bwd_points(const float* a, const float* b, const int* nn_ab,
+                                      const int* nn_ba, int T, int N, int M, int mode,
+                                      const float* g, float* grad_a, cudaStream_t s);
+
+void count_launch(int n = 1);
+
+// Chamfer-kernel event timing hooks (api.cu)
+void prof_before(cudaStream_t s);
+void prof_after(cudaStream_t s);
+
+}  // namespace dc

@@ -1,0 +1,337 @@
+// Frame tables, area CDF, area-weighted sampling and target staging (Sec. III-B, Eq. 3).
+#include <math.h>
+
+#include "dc_internal.cuh"
+
+namespace dc {
+
+namespace {
+
+constexpr float ROW_SENTINEL = 1e18f;   // coordinate of padded sim points
+constexpr float COL_SENTINEL = -1e18f;  // coordinate of padded target points
+
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, DC_OK, code); }
+
+// largest k in [0, n) with pre[k] <= g (pre is non-decreasing, pre[0] = 0)
+__device__ __forceinline__ int last_le(const int* pre, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool coord_ok(float v) { return fabsf(v) <= COORD_MAX; }
+
+// ---------------------------------------------------------------------------------------
+// uniform trajectory -> frame table, row/column prefixes and Chamfer units
+// ---------------------------------------------------------------------------------------
+__global__ void k_build_uniform(UniformArgs a, Ws w) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Npad = ((a.N + ROW_PAD - 1) / ROW_PAD) * ROW_PAD;
+    const int Mpad = ((a.M + COL_PAD - 1) / COL_PAD) * COL_PAD;
+    const int n_units = a.T * a.units_per_frame;
+    if (g == 0) {
+        WsHeader* h = w.hdr;
+        h->status = DC_OK;
+        h->n_frames = a.T;
+        h->n_units = n_units;
+        h->total_sub = n_units * a.subs_per_unit;
+        h->total_rows = a.T * Npad;
+        h->total_cols = a.T * Mpad;
+        h->sum_f = a.T * a.F;
+        h->mode = a.mode;
+        h->planned = 0;
+        h->any_grad = a.grad != nullptr;
+        h->max_v = a.V;
+    }
+    if (g <= a.T) {
+        w.rowpre[g] = g * Npad;
+        w.colpre[g] = g * Mpad;
+    }
+    if (g < a.T) {
+        const int k = g;
+        FrameDesc f;
+        f.verts = a.verts ? a.verts + 3LL * k * a.V : nullptr;
+        f.faces = a.faces;
+        f.draws = a.draws ? a.draws + 3LL * k * a.N : nullptr;
+        f.pts = a.pts ? a.pts + 3LL * k * a.N : nullptr;
+        f.tgt = a.tgt ? a.tgt + 3LL * k * a.M : nullptr;
+        f.loss = a.loss ? a.loss + k : w.loss + k;
+        f.nn_ab = a.nn_ab ? a.nn_ab + (long long)k * a.N : w.nnab + (long long)k * Npad;
+        f.nn_ba = a.nn_ba ? a.nn_ba + (long long)k * a.M : w.nnba + (long long)k * Mpad;
+        f.grad = a.grad ? a.grad + 3LL * k * a.V : nullptr;
+        f.out_pts = a.out_pts ? a.out_pts + 3LL * k * a.N : nullptr;
+        f.out_face = a.out_face ? a.out_face + (long long)k * a.N : nullptr;
+        f.out_bary = a.out_bary ? a.out_bary + 3LL * k * a.N : nullptr;
+        f.V = a.V;
+        f.F = a.F;
+        f.N = a.N;
+        f.M = a.M;
+        f.Npad = Npad;
+        f.Mpad = Mpad;
+        f.weight = a.weight ? a.weight[k] : 1.0f;
+        f.gscale = a.gscale ? a.gscale[k] : f.weight;
+        f.row0 = k * Npad;
+        f.col0 = k * Mpad;
+        f.cdf0 = k * a.F;
+        f.unit0 = k * a.units_per_frame;
+        w.frames[k] = f;
+    }
+    if (g <= n_units) w.unit_pre[g] = g * a.subs_per_unit;
+    if (g < n_units) {
+        w.unit_frame[g] = g / a.units_per_frame;
+        w.unit_rb[g] = g % a.units_per_frame;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// area CDF: two-float (compensated) prefix sum of the float32 face areas, so that the
+// stored C_f is the float32 rounding of the exact prefix sum of those areas
+// ---------------------------------------------------------------------------------------
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+    float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return ff_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ FF ff_add1(FF a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    return ff_norm(s, __fadd_rn(e, a.lo));
+}
+
+// area of face f = 1/2 |(p1 - p0) x (p2 - p0)|; flags bad indices / coordinates
+__device__ __forceinline__ float face_area(const float* __restrict__ verts,
+                                           const int* __restrict__ faces, int V, int f,
+                                           bool& bad_idx, bool& bad_val) {
+    const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
+    if ((unsigned)i0 >= (unsigned)V || (unsigned)i1 >= (unsigned)V ||
+        (unsigned)i2 >= (unsigned)V) {
+        bad_idx = true;
+        return 0.0f;
+    }
+    const float* p0 = verts + 3LL * i0;
+    const float* p1 = verts + 3LL * i1;
+    const float* p2 = verts + 3LL * i2;
+    float q[9] = {p0[0], p0[1], p0[2], p1[0], p1[1], p1[2], p2[0], p2[1], p2[2]};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) bad_val |= !coord_ok(q[k]);
+    // explicit roundings: both passes of the scan must see bit-identical areas
+    const float e1x = __fsub_rn(q[3], q[0]), e1y = __fsub_rn(q[4], q[1]),
+                e1z = __fsub_rn(q[5], q[2]);
+    const float e2x = __fsub_rn(q[6], q[0]), e2y = __fsub_rn(q[7], q[1]),
+                e2z = __fsub_rn(q[8], q[2]);
+    const float cx = __fsub_rn(__fmul_rn(e1y, e2z), __fmul_rn(e1z, e2y));
+    const float cy = __fsub_rn(__fmul_rn(e1z, e2x), __fmul_rn(e1x, e2z));
+    const float cz = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
+    const float n2 = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
+    return __fmul_rn(0.5f, __fsqrt_rn(n2));
+}
+
+constexpr int CDF_THREADS = 1024;
+
+__global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
+    __shared__ FF s_w[32];
+    const FrameDesc* fr = w.frames + blockIdx.x;
+    const float* verts = fr->verts;
+    if (!verts) return;
+    const int* faces = fr->faces;
+    const int F = fr->F, V = fr->V;
+    float* cdf = w.cdf + fr->cdf0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (F + CDF_THREADS - 1) / CDF_THREADS;
+    const int f0 = min(F, tid * per), f1 = min(F, f0 + per);
+    bool bad_idx = false, bad_val = false;
+
+    FF v = {0.0f, 0.0f};
+    for (int f = f0; f < f1; ++f) v = ff_add1(v, face_area(verts, faces, V, f, bad_idx, bad_val));
+
+    // block-wide inclusive scan of the segment sums
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        FF u = {__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+        if (lane >= o) v = ff_add(u, v);
+    }
+    if (lane == 31) s_w[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        FF t = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            FF u = {__shfl_up_sync(0xffffffffu, t.hi, o), __shfl_up_sync(0xffffffffu, t.lo, o)};
+            if (lane >= o) t = ff_add(u, t);
+        }
+        s_w[lane] = t;
+    }
+    __syncthreads();
+    FF ex = {__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
+    if (lane == 0) ex = {0.0f, 0.0f};
+    FF run = warp > 0 ? ff_add(s_w[warp - 1], ex) : ex;
+
+    for (int f = f0; f < f1; ++f) {
+        run = ff_add1(run, face_area(verts, faces, V, f, bad_idx, bad_val));
+        cdf[f] = run.hi;
+    }
+    if (bad_idx || bad_val) set_status(&w.hdr->status, DC_EINVAL);
+    if (f1 == F && f0 < f1) {
+        const float A = run.hi;
+        if (!(A > 0.0f) || !isfinite(A)) set_status(&w.hdr->status, DC_EDEGENERATE);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// sampling: face pick by inverse CDF (Sec. III-B) and barycentric point (Eq. 3)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += gridDim.x * blockDim.x) {
+        const int k = last_le(w.rowpre, n_frames, g);
+        const FrameDesc* fr = w.frames + k;
+        const int i = g - fr->row0;
+        float4 x = make_float4(ROW_SENTINEL, ROW_SENTINEL, ROW_SENTINEL, 0.0f);
+        int4 q = make_int4(-1, 0, 0, 0);
+        if (i < fr->N) {
+            if (fr->pts) {
+                const float* p = fr->pts + 3LL * i;
+                x = make_float4(p[0], p[1], p[2], 0.0f);
+                if (!coord_ok(x.x) || !coord_ok(x.y) || !coord_ok(x.z))
+                    set_status(&w.hdr->status, DC_EINVAL);
+            } else {
+                const float* r = fr->draws + 3LL * i;
+                const float rf = r[0], r1 = r[1], r2 = r[2];
+                if (!(rf >= 0.0f && rf <= 1.0f && r1 >= 0.0f && r1 <= 1.0f && r2 >= 0.0f &&
+                      r2 <= 1.0f))
+                    set_status(&w.hdr->status, DC_EINVAL);
+                const float* cdf = w.cdf + fr->cdf0;
+                const int F = fr->F;
+                const float t = __fmul_rn(rf, cdf[F - 1]);
+                int lo = 0, hi = F;  // first f with cdf[f] > t
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cdf[mid] > t)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                const int f = min(lo, F - 1);
+                const int i0 = fr->faces[3 * f], i1 = fr->faces[3 * f + 1],
+                          i2 = fr->faces[3 * f + 2];
+                const int V = fr->V;
+                if ((unsigned)i0 < (unsigned)V && (unsigned)i1 < (unsigned)V &&
+                    (unsigned)i2 < (unsigned)V) {
+                    const float* p0 = fr->verts + 3LL * i0;
+                    const float* p1 = fr->verts + 3LL * i1;
+                    const float* p2 = fr->verts + 3LL * i2;
+                    const float s = __fsqrt_rn(r1);
+                    const float w0 = __fsub_rn(1.0f, s);
+                    const float w1 = __fmul_rn(s, __fsub_rn(1.0f, r2));
+                    const float w2 = __fmul_rn(s, r2);
+                    x.x = __fmaf_rn(w2, p2[0], __fmaf_rn(w1, p1[0], __fmul_rn(w0, p0[0])));
+                    x.y = __fmaf_rn(w2, p2[1], __fmaf_rn(w1, p1[1], __fmul_rn(w0, p0[1])));
+                    x.z = __fmaf_rn(w2, p2[2], __fmaf_rn(w1, p1[2], __fmul_rn(w0, p0[2])));
+                    q = make_int4(f, __float_as_int(w0), __float_as_int(w1), __float_as_int(w2));
+                    if (fr->out_face) fr->out_face[i] = f;
+                    if (fr->out_bary) {
+                        fr->out_bary[3LL * i] = w0;
+                        fr->out_bary[3LL * i + 1] = w1;
+                        fr->out_bary[3LL * i + 2] = w2;
+                    }
+                } else {
+                    set_status(&w.hdr->status, DC_EINVAL);
+                    x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+                if (fr->out_pts) {
+                    fr->out_pts[3LL * i] = x.x;
+                    fr->out_pts[3LL * i + 1] = x.y;
+                    fr->out_pts[3LL * i + 2] = x.z;
+                }
+            }
+        }
+        w.x[g] = x;
+        w.fw[g] = q;
+        w.pab[g] = EMPTY;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// targets: [M][3] -> X/Y/Z planes padded to Mpad (sentinel beyond M); reset column minima
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < cols; g += gridDim.x * blockDim.x) {
+        const int k = last_le(w.colpre, n_frames, g);
+        const FrameDesc* fr = w.frames + k;
+        const int j = g - fr->col0;
+        float vx = COL_SENTINEL, vy = COL_SENTINEL, vz = COL_SENTINEL;
+        if (j < fr->M) {
+            const float* p = fr->tgt + 3LL * j;
+            vx = p[0];
+            vy = p[1];
+            vz = p[2];
+            if (!coord_ok(vx) || !coord_ok(vy) || !coord_ok(vz))
+                set_status(&w.hdr->status, DC_EINVAL);
+        }
+        float* X = w.tsoa + 3LL * fr->col0;
+        X[j] = vx;
+        X[fr->Mpad + j] = vy;
+        X[2 * fr->Mpad + j] = vz;
+        w.pba[g] = EMPTY;
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > 65535LL * 16 ? 65535LL * 16 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s) {
+    const long long n = 1 + (long long)(a.T > a.T * a.units_per_frame ? a.T
+                                                                        : a.T * a.units_per_frame);
+    k_build_uniform<<<grid_for(n, 256), 256, 0, s>>>(a, w);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const Ws& w, cudaStream_t s) {
+    return cudaMemsetAsync(&w.hdr->status, 0, sizeof(int), s);
+}
+
+cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s) {
+    k_area_cdf<<<n_frames, CDF_THREADS, 0, s>>>(w);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s) {
+    k_sample<<<grid_for(rows, 256), 256, 0, s>>>(w, n_frames, rows);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s) {
+    k_targets<<<grid_for(cols, 256), 256, 0, s>>>(w, n_frames, cols);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace dc

@@ -1,0 +1,279 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (GB300 only).
+
+Inputs are the seeded workloads; draws that the oracle finds within 1e-6 of a CDF boundary
+are moved to their face's CDF midpoint (parity.nudge_draws) wherever the loss and gradient
+are compared, since a point that may fall on either face moves the loss by more than the
+loss tolerance; test_raw_draws_face_picks_and_neighbours covers the raw draws.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_03139_gb300 import _lib as L
+
+    L.lib()
+    return L
+
+
+def L():
+    from paper_2204_03139_gb300 import _lib as L
+
+    return L
+
+
+def to_dev(tr):
+    return (torch.from_numpy(tr.verts).to(DEV), torch.from_numpy(tr.faces).to(DEV),
+            torch.from_numpy(np.ascontiguousarray(tr.draws_tn3())).to(DEV),
+            torch.from_numpy(np.ascontiguousarray(tr.targets_tm3())).to(DEV))
+
+
+def run_traj(tr, mode=0, frame_w=None):
+    v, f, d, y = to_dev(tr)
+    w = None if frame_w is None else torch.tensor(frame_w, dtype=torch.float32, device=DEV)
+    r = L().dc_loss_traj(v, f, d, y, mode=mode, frame_w=w, check=True)
+    torch.cuda.synchronize()
+    return {k: (x.cpu().numpy() if isinstance(x, torch.Tensor) else x) for k, x in r.items()}
+
+
+def compare_traj(tr, g, ref, frames, mode=0, weights=None):
+    """Per-frame loss / neighbours / gradient of the frames the oracle ran."""
+    for t in frames:
+        per = ref["frames"][t]
+        parity.check_nn(g["nn_ab"][t], per["nn_ab"],
+                        g["nn_ba"][t] if mode == 0 else None, per["nn_ba"] if mode == 0 else None)
+    parity.check_loss(g["loss_frames"][frames], ref["loss_frames"][frames])
+    parity.check_grad(g["grad_verts"][frames], ref["grad_verts"][frames])
+    if len(frames) == tr.T:
+        w = np.ones(tr.T) if weights is None else np.asarray(weights)
+        parity.check_loss(g["loss_total"], [np.sum(w * ref["loss_frames"])], what="total")
+
+
+# ---------------------------------------------------------------------------------------------
+# the five workloads' sizes
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1])
+def test_single_frame_25x25(mode):
+    tr, moved = parity.nudge_draws(W.single_frame())
+    g = run_traj(tr, mode)
+    ref = oracle.loss_traj(tr, mode=mode)
+    compare_traj(tr, g, ref, [0], mode)
+
+
+def test_trajectory_50x50_full_size_sampled_frames():
+    """The 40-frame 50x50 trajectory at full size (10 000 x 10 000 per frame), in the launch
+    configuration the bench times; the oracle checks frames 0, 19 and 39."""
+    tr, moved = parity.nudge_draws(W.trajectory_50x50())
+    g = run_traj(tr)
+    frames = [0, 19, 39]
+    ref = oracle.loss_traj(tr, frames=frames)
+    compare_traj(tr, g, ref, frames)
+    assert np.all(np.isfinite(g["loss_frames"])) and np.all(g["loss_frames"] > 0)
+
+
+def test_trajectory_50x50_weights_total():
+    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=4, n=3000, m=2500))
+    w = [0.0, 0.5, 1.0, 2.0]
+    g = run_traj(tr, frame_w=w)
+    ref = oracle.loss_traj(tr, weights=w)
+    compare_traj(tr, g, ref, list(range(tr.T)), weights=w)
+
+
+@pytest.mark.slow
+def test_trajectory_100x100_full_size_sampled_frames():
+    """100x100 grid, T = 100, 32 768 x 32 768 per frame; the oracle checks two frames."""
+    tr, moved = parity.nudge_draws(W.trajectory_100x100())
+    g = run_traj(tr)
+    frames = [0, 99]
+    ref = oracle.loss_traj(tr, frames=frames)
+    compare_traj(tr, g, ref, frames)
+
+
+# ---------------------------------------------------------------------------------------------
+# ragged sizes: tails of every tile level (8-row groups, 256-row warps, 1024-row units,
+# 64-target sub-chunks, 256-target chunks)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m", [(1, 1), (1, 300), (300, 1), (2, 3), (63, 65), (255, 257),
+                                 (1023, 1025), (1025, 511), (2049, 4097), (3000, 64)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ragged_sizes(n, m, mode):
+    tr = W.lift_trajectory(7 + n + 3 * m, 9, 2, n, m, name="ragged")
+    tr, _ = parity.nudge_draws(tr)
+    g = run_traj(tr, mode)
+    ref = oracle.loss_traj(tr, mode=mode)
+    compare_traj(tr, g, ref, [0, 1], mode)
+
+
+def test_raw_draws_face_picks_and_neighbours():
+    """Without moving any draw: face picks exact outside the 1e-6 window, neighbours exact
+    except for points whose face pick fell inside it."""
+    tr = W.trajectory_50x50(T=3, n=10000, m=10000)
+    v, f, d, y = to_dev(tr)
+    pts, fi, bc = L().dc_sample(v, f, d, check=True)
+    r = L().dc_loss_traj(v, f, d, y, check=True)
+    torch.cuda.synchronize()
+    for t in range(tr.T):
+        per = oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t), tr.frame_targets(t))
+        diff = parity.check_face_picks(fi[t].cpu().numpy(), per["face_idx"], per["margin"])
+        same = np.setdiff1d(np.arange(tr.n(t)), diff)
+        np.testing.assert_array_equal(pts[t].cpu().numpy()[same], per["x32"][same])
+        parity.check_nn(r["nn_ab"][t].cpu().numpy(), per["nn_ab"],
+                        r["nn_ba"][t].cpu().numpy(), per["nn_ba"], moved_rows=diff)
+
+
+# ---------------------------------------------------------------------------------------------
+# the individual entry points
+# ---------------------------------------------------------------------------------------------
+def test_dc_sample_matches_oracle():
+    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=2, n=5000, m=1))
+    v, f, d, _ = to_dev(tr)
+    pts, fi, bc = L().dc_sample(v, f, d, check=True)
+    torch.cuda.synchronize()
+    for t in range(2):
+        per = oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t), tr.frame_targets(t))
+        np.testing.assert_array_equal(fi[t].cpu().numpy(), per["face_idx"])
+        np.testing.assert_array_equal(pts[t].cpu().numpy(), per["x32"])
+        np.testing.assert_allclose(bc[t].cpu().numpy(), per["bary"], rtol=0, atol=3e-7)
+        np.testing.assert_allclose(pts[t].cpu().numpy(), per["x64"], rtol=0, atol=5e-7)
+
+
+def test_equal_area_grid_picks_are_floor():
+    """On the exactly-equal-area flat 17x17 grid the pick is floor(r_f F) for every draw,
+    including draws exactly on a boundary."""
+    tr = W.flat_square(17, 20000, seed=5)
+    d = tr.draws.copy()
+    d[:512, 0] = (np.arange(512) / 512).astype(np.float32)
+    _, fi, _ = L().dc_sample(torch.from_numpy(tr.verts).to(DEV), torch.from_numpy(tr.faces).to(DEV),
+                             torch.from_numpy(d[None]).to(DEV), check=True)
+    np.testing.assert_array_equal(fi[0].cpu().numpy(), np.floor(d[:, 0].astype(np.float64) * 512))
+
+
+@pytest.mark.parametrize("n,m,mode", [(700, 900, 0), (2048, 333, 1), (5000, 5000, 0)])
+def test_chamfer_fwd_bwd_points(n, m, mode):
+    a, b = W.random_cloud_pair(n + m, n, m)
+    nn = oracle.nn_pair(a, b)
+    loss, ga = oracle.chamfer(a, b, mode=mode, gscale=1.5)
+    ta, tb = torch.from_numpy(a[None]).to(DEV), torch.from_numpy(b[None]).to(DEV)
+    l, nab, nba = L().dc_chamfer_fwd(ta, tb, mode=mode, check=True)
+    g = L().dc_chamfer_bwd(ta, tb, nab, nba, torch.tensor([1.5], device=DEV), mode=mode)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(nab[0].cpu().numpy(), nn["nn_ab"])
+    if mode == 0:
+        np.testing.assert_array_equal(nba[0].cpu().numpy(), nn["nn_ba"])
+    parity.check_loss(l.cpu().numpy(), [loss])
+    parity.check_grad(g[0].cpu().numpy(), ga)
+
+
+def test_chamfer_self_zero_and_shift():
+    u, v = W.grid_uv(60)
+    a = np.stack([u, v, np.zeros_like(u)], 1).astype(np.float32)
+    b = a.copy()
+    b[:, 2] += np.float32(0.004)
+    ta, tb = torch.from_numpy(a[None]).to(DEV), torch.from_numpy(b[None]).to(DEV)
+    l0, n0, m0 = L().dc_chamfer_fwd(ta, ta, check=True)
+    l1, n1, m1 = L().dc_chamfer_fwd(ta, tb, check=True)
+    torch.cuda.synchronize()
+    assert float(l0[0]) == 0.0
+    np.testing.assert_array_equal(n0[0].cpu().numpy(), np.arange(a.shape[0]))
+    np.testing.assert_array_equal(m1[0].cpu().numpy(), np.arange(a.shape[0]))
+    assert float(l1[0]) == pytest.approx(2 * float(np.float32(0.004)) ** 2, rel=1e-6)
+
+
+def test_loss_traj_bwd_recompute_equals_fused():
+    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=3, n=4000, m=3500))
+    v, f, d, y = to_dev(tr)
+    r = L().dc_loss_traj(v, f, d, y, check=True)
+    gf = torch.ones(3, device=DEV)
+    g2 = L().dc_loss_traj_bwd(v, f, d, y, r["nn_ab"], r["nn_ba"], gf, check=True)
+    torch.cuda.synchronize()
+    assert parity.rel_l2(g2.cpu().numpy(), r["grad_verts"].cpu().numpy()) < 1e-6
+
+
+def test_autograd_matches_oracle_and_fd():
+    """DCLoss backward (samples recomputed from the draws) against the oracle gradient, and
+    the oracle's own FP64 central differences on 200 random vertex coordinates."""
+    from paper_2204_03139_gb300.autograd import loss_traj
+
+    tr, _ = parity.nudge_draws(W.lift_trajectory(99, 100, 2, 2048, 2048, name="fd"))
+    v, f, d, y = to_dev(tr)
+    vv = v.clone().requires_grad_(True)
+    total, lf = loss_traj(vv, f, d, y)
+    total.backward()
+    torch.cuda.synchronize()
+    ref = oracle.loss_traj(tr)
+    parity.check_loss(lf.detach().cpu().numpy(), ref["loss_frames"])
+    gpu_g = vv.grad.cpu().numpy()
+    parity.check_grad(gpu_g, ref["grad_verts"])
+    # FD of the oracle loss at h = 1e-6 m; coordinates whose +-h runs change a pick or a
+    # neighbour are skipped
+    rng = W.rng_for(7)
+    t = 1
+    base = oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t), tr.frame_targets(t))
+    checked = 0
+    for _ in range(200):
+        vi, k = int(rng.integers(tr.V)), int(rng.integers(3))
+        vp, vm = tr.verts[t].copy(), tr.verts[t].copy()
+        vp[vi, k] = np.float32(vp[vi, k] + 1e-6)
+        vm[vi, k] = np.float32(vm[vi, k] - 1e-6)
+        rp = oracle.frame(vp, tr.faces, tr.frame_draws(t), tr.frame_targets(t), grads=False)
+        rm = oracle.frame(vm, tr.faces, tr.frame_draws(t), tr.frame_targets(t), grads=False)
+        if not all(np.array_equal(rp[q], rm[q]) and np.array_equal(rp[q], base[q])
+                   for q in ("face_idx", "nn_ab", "nn_ba")):
+            continue
+        a_, b_ = float(vp[vi, k]) - float(tr.verts[t][vi, k]), float(tr.verts[t][vi, k]) - float(vm[vi, k])
+        fd = (b_ * b_ * (rp["loss"] - base["loss"]) + a_ * a_ * (base["loss"] - rm["loss"])) / (
+            a_ * b_ * (a_ + b_))
+        # the GPU gradient of this coordinate agrees with the FP64 difference quotient
+        scale = np.abs(ref["grad_verts"][t]).max()
+        assert abs(gpu_g[t, vi, k] - fd) <= 1e-4 * scale + 1e-6 * abs(fd)
+        checked += 1
+    assert checked >= 150
+
+
+# ---------------------------------------------------------------------------------------------
+# device-side errors, determinism
+# ---------------------------------------------------------------------------------------------
+def test_device_errors_are_reported():
+    v = torch.zeros((1, 3, 3), device=DEV)
+    f = torch.tensor([[0, 1, 2]], dtype=torch.int32, device=DEV)
+    d = torch.full((1, 4, 3), 0.5, device=DEV)
+    y = torch.zeros((1, 4, 3), device=DEV)
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj(v, f, d, y, check=True)
+    assert e.value.code == L().DC_EDEGENERATE
+    v2 = torch.tensor([[[0, 0, 0], [1, 0, 0], [0, 1, 0]]], dtype=torch.float32, device=DEV)
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj(v2, torch.tensor([[0, 1, 3]], dtype=torch.int32, device=DEV), d, y,
+                         check=True)
+    assert e.value.code == L().DC_EINVAL
+    y2 = y.clone()
+    y2[0, 1, 1] = float("nan")
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj(v2, f, d, y2, check=True)
+    assert e.value.code == L().DC_EINVAL
+    # the next good call clears the status
+    r = L().dc_loss_traj(v2, f, d, y, check=True)
+    assert torch.isfinite(r["loss_frames"]).all()
+
+
+def test_loss_is_deterministic():
+    tr = W.trajectory_50x50(T=4, n=6000, m=7000)
+    a = run_traj(tr)
+    b = run_traj(tr)
+    np.testing.assert_array_equal(a["loss_frames"], b["loss_frames"])
+    np.testing.assert_array_equal(a["loss_total"], b["loss_total"])
+    np.testing.assert_array_equal(a["nn_ab"], b["nn_ab"])
+    np.testing.assert_array_equal(a["nn_ba"], b["nn_ba"])
+    assert parity.rel_l2(a["grad_verts"], b["grad_verts"]) < 1e-6
