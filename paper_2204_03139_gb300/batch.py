@@ -1,0 +1,159 @@
+"""Batched loss over many trajectories of uneven sizes (one launch sequence, CUDA graph).
+
+Every frame of every trajectory becomes one dc_frame; dc_batch_plan lays them out in one
+workspace, and dc_batch_run issues the whole sequence -- area CDFs, sampling, ONE persistent
+Chamfer launch whose work split covers all frames, neighbour recovery, losses and the vertex
+gradients -- reading only device memory, so it can be replayed from a CUDA graph.
+
+The plain per-frame form (`per_frame_loss`) is the comparison point: the same kernels, one
+dc_loss_traj call per frame, no graph.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+@dataclass
+class DeviceTrajectory:
+    """Device tensors of one trajectory. Frames may be ragged: draws and targets are flat
+    [sum_t N_t, 3] / [sum_t M_t, 3] with host offsets n_off / m_off ([T+1])."""
+
+    verts: torch.Tensor    # [T, V, 3] float32
+    faces: torch.Tensor    # [F, 3] int32
+    draws: torch.Tensor    # [sum N_t, 3] float32
+    targets: torch.Tensor  # [sum M_t, 3] float32
+    n_off: np.ndarray
+    m_off: np.ndarray
+
+    @property
+    def T(self):
+        return int(self.verts.shape[0])
+
+    @staticmethod
+    def from_host(tr, device) -> "DeviceTrajectory":
+        return DeviceTrajectory(torch.from_numpy(tr.verts).to(device),
+                                torch.from_numpy(tr.faces).to(device),
+                                torch.from_numpy(tr.draws).to(device),
+                                torch.from_numpy(tr.targets).to(device),
+                                np.asarray(tr.n_off, np.int64), np.asarray(tr.m_off, np.int64))
+
+    def pairs(self) -> int:
+        return int(np.sum(np.diff(self.n_off) * np.diff(self.m_off)))
+
+
+class BatchedLoss:
+    """Loss (and vertex gradients) of a list of trajectories in one planned launch sequence.
+
+    After run(): loss_frames[k] [T_k] and grad_verts[k] [T_k, V_k, 3] hold each trajectory's
+    per-frame losses and gradients (gradient of sum_t w_t L_t), and the returned tensor is the
+    weighted total over all trajectories.
+    """
+
+    def __init__(self, trajs, mode=_lib.BIDIR_MEAN, weights=None, grad=True, graph=False,
+                 nn=False):
+        self.trajs = list(trajs)
+        self.mode = mode
+        dev = self.trajs[0].verts.device
+        self.device = dev
+        nfr = sum(t.T for t in self.trajs)
+        self.frames = (_lib.dc_frame * nfr)()
+        self.loss_frames, self.grad_verts, self.nn_ab, self.nn_ba = [], [], [], []
+        k = 0
+        for i, tr in enumerate(self.trajs):
+            T, V, F = tr.T, int(tr.verts.shape[1]), int(tr.faces.shape[0])
+            lf = torch.empty(T, dtype=torch.float32, device=dev)
+            gv = torch.empty((T, V, 3), dtype=torch.float32, device=dev) if grad else None
+            nab = torch.empty(int(tr.n_off[-1]), dtype=torch.int32, device=dev) if nn else None
+            nba = (torch.empty(int(tr.m_off[-1]), dtype=torch.int32, device=dev)
+                   if nn and mode == _lib.BIDIR_MEAN else None)
+            self.loss_frames.append(lf)
+            self.grad_verts.append(gv)
+            self.nn_ab.append(nab)
+            self.nn_ba.append(nba)
+            w = None if weights is None else weights[i]
+            for t in range(T):
+                fr = self.frames[k]
+                n0, n1 = int(tr.n_off[t]), int(tr.n_off[t + 1])
+                m0, m1 = int(tr.m_off[t]), int(tr.m_off[t + 1])
+                fr.verts = tr.verts.data_ptr() + 4 * 3 * V * t
+                fr.faces = tr.faces.data_ptr()
+                fr.draws = tr.draws.data_ptr() + 4 * 3 * n0
+                fr.targets = tr.targets.data_ptr() + 4 * 3 * m0
+                fr.V, fr.F, fr.N, fr.M = V, F, n1 - n0, m1 - m0
+                fr.weight = 1.0 if w is None else float(w[t])
+                fr.tag = i
+                fr.loss = lf.data_ptr() + 4 * t
+                fr.grad_verts = gv.data_ptr() + 4 * 3 * V * t if grad else None
+                fr.nn_ab = nab.data_ptr() + 4 * n0 if nn else None
+                fr.nn_ba = nba.data_ptr() + 4 * m0 if nba is not None else None
+                k += 1
+        L = _lib.lib()
+        nb = int(L.dc_batch_workspace_size(self.frames, nfr))
+        if nb == 0:
+            raise _lib.DCError(_lib.DC_EINVAL, "bad batch sizes")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        self.total = torch.empty(1, dtype=torch.float32, device=dev)
+        self.n_frames = nfr
+        _lib._check(L.dc_batch_plan(self.frames, nfr, mode, ctypes.c_void_p(self.ws.data_ptr()),
+                                    nb, _lib._stream(dev)))
+        self.graph = None
+        if graph:
+            self._capture()
+
+    def _launch(self):
+        _lib._check(_lib.lib().dc_batch_run(ctypes.c_void_p(self.ws.data_ptr()),
+                                            ctypes.c_void_p(self.total.data_ptr()),
+                                            _lib._stream(self.device)))
+
+    def _capture(self):
+        # one eager run first: per-device one-time set-up happens outside the capture
+        self._launch()
+        torch.cuda.synchronize(self.device)
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self._launch()
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        self.graph = g
+
+    def run(self, check: bool = False) -> torch.Tensor:
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._launch()
+        if check:
+            _lib.check_ws(self.ws)
+        return self.total
+
+    def pairs(self) -> int:
+        return sum(t.pairs() for t in self.trajs)
+
+
+def per_frame_loss(trajs, mode=_lib.BIDIR_MEAN, grad=True):
+    """The plain per-frame form: one dc_loss_traj call per frame, no graph, one stream.
+    Returns (per-trajectory loss_frames, per-trajectory grad_verts)."""
+    losses, grads = [], []
+    for tr in trajs:
+        T, V = tr.T, int(tr.verts.shape[1])
+        lf = torch.empty(T, dtype=torch.float32, device=tr.verts.device)
+        gv = torch.empty((T, V, 3), dtype=torch.float32, device=tr.verts.device) if grad else None
+        for t in range(T):
+            n0, n1 = int(tr.n_off[t]), int(tr.n_off[t + 1])
+            m0, m1 = int(tr.m_off[t]), int(tr.m_off[t + 1])
+            out = {"loss_frames": lf[t:t + 1]}
+            if grad:
+                out["grad_verts"] = gv[t:t + 1]
+            _lib.dc_loss_traj(tr.verts[t:t + 1], tr.faces, tr.draws[n0:n1].unsqueeze(0),
+                              tr.targets[m0:m1].unsqueeze(0), mode=mode, grad=grad, total=False,
+                              nn=False, out=out)
+        losses.append(lf)
+        grads.append(gv)
+    return losses, grads

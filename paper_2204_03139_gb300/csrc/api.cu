@@ -55,12 +55,14 @@ Layout make_layout(const Sizes& s) {
     L.cdf = take(s.sum_f * 4);
     L.x = take(s.rows * 16);
     L.fw = take(s.rows * 16);
-    L.tsoa = take(3 * s.cols * 4);
+    L.tsoa = take(6 * s.cols * 4);
     L.pab = take(s.rows * 8);
     L.pba = take(s.cols * 8);
     L.nnab = take(s.rows * 4);
     L.nnba = take(s.cols * 4);
     L.loss = take(s.n_frames * 4);
+    L.part = take(s.n_frames * s.slices * 2 * 4);
+    L.gscr = take(s.gscr * 4);
     L.total = off;
     return L;
 }
@@ -84,6 +86,8 @@ Ws make_ws(void* base, const Layout& L) {
     w.nnab = reinterpret_cast<int*>(p + L.nnab);
     w.nnba = reinterpret_cast<int*>(p + L.nnba);
     w.loss = reinterpret_cast<float*>(p + L.loss);
+    w.part = reinterpret_cast<float*>(p + L.part);
+    w.gscr = reinterpret_cast<float*>(p + L.gscr);
     return w;
 }
 
@@ -108,7 +112,7 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 constexpr long long INT_LIMIT = 0x7fffffffLL;
 
 // Sizes of a uniform trajectory; false if any derived count overflows int32.
-bool uniform_sizes(int T, int F, int N, int M, Sizes& s, int& upf, int& spu) {
+bool uniform_sizes(int T, int V, int F, int N, int M, Sizes& s, int& upf, int& spu) {
     const long long Npad = (long long)div_up(N, ROW_PAD) * ROW_PAD;
     const long long Mpad = M > 0 ? (long long)div_up(M, COL_PAD) * COL_PAD : 0;
     upf = div_up(N, ROWS_PER_UNIT);
@@ -118,9 +122,12 @@ bool uniform_sizes(int T, int F, int N, int M, Sizes& s, int& upf, int& spu) {
     s.sum_f = (long long)T * F;
     s.rows = (long long)T * Npad;
     s.cols = (long long)T * Mpad;
+    s.slices = epilogue_slices(T);
+    s.gscr = s.slices > 1 ? (long long)T * s.slices * 3 * V : 0;
     const long long total_sub = s.n_units * spu;
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
-           total_sub < INT_LIMIT && s.rows * 3 < INT_LIMIT * 16;
+           total_sub < INT_LIMIT && s.rows * 3 < INT_LIMIT * 16 && s.cols * 6 < INT_LIMIT * 16 &&
+           s.gscr < INT_LIMIT * 4;
 }
 
 enum : unsigned {
@@ -128,9 +135,6 @@ enum : unsigned {
     PH_SAMPLE = 2,
     PH_TARGETS = 4,
     PH_CHAMFER = 8,
-    PH_FINAL = 16,
-    PH_LOSS = 32,
-    PH_BWD = 64,
 };
 
 int check_ws(void* ws, size_t ws_bytes, size_t need) {
@@ -141,14 +145,15 @@ int check_ws(void* ws, size_t ws_bytes, size_t need) {
     return DC_OK;
 }
 
-int run_uniform(UniformArgs a, unsigned phases, float* loss_total, void* ws, size_t ws_bytes,
-                cudaStream_t st) {
+int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total, void* ws,
+                size_t ws_bytes, cudaStream_t st) {
     Sizes sz;
     int upf = 0, spu = 0;
-    if (!uniform_sizes(a.T, a.F, a.N, a.M, sz, upf, spu))
+    if (!uniform_sizes(a.T, a.V, a.F, a.N, a.M, sz, upf, spu))
         return fail(DC_EINVAL, "problem too large for 32-bit offsets");
     a.units_per_frame = upf;
     a.subs_per_unit = spu;
+    a.slices = (int)sz.slices;
     const Layout L = make_layout(sz);
     int rc = check_ws(ws, ws_bytes, L.total);
     if (rc) return rc;
@@ -160,9 +165,9 @@ int run_uniform(UniformArgs a, unsigned phases, float* loss_total, void* ws, siz
     if (!e && (phases & PH_TARGETS) && cols > 0) e = launch_targets(w, T, cols, st);
     if (!e && (phases & PH_CHAMFER))
         e = launch_chamfer(w, (int)sz.n_units, (int)(sz.n_units * spu), a.mode, st);
-    if (!e && (phases & PH_FINAL)) e = launch_finalize(w, T, rows, cols, a.mode, st);
-    if (!e && (phases & PH_LOSS)) e = launch_loss(w, T, a.mode, loss_total, st);
-    if (!e && (phases & PH_BWD)) e = launch_bwd(w, T, a.V, a.mode, st);
+    if (!e && epi_flags)
+        e = launch_epilogue(w, T, (int)sz.slices, a.grad ? a.V : 0, a.mode, epi_flags,
+                            loss_total, st);
     if (e) return cuda_fail(e, "kernel launch");
     return DC_OK;
 }
@@ -237,7 +242,7 @@ size_t dc_workspace_size(int T, int V, int F, int N, int M) {
     if (T <= 0 || V <= 0 || F <= 0 || N <= 0 || M < 0) return 0;
     Sizes sz;
     int upf, spu;
-    if (!uniform_sizes(T, F, N, M, sz, upf, spu)) return 0;
+    if (!uniform_sizes(T, V, F, N, M, sz, upf, spu)) return 0;
     return make_layout(sz).total;
 }
 
@@ -271,7 +276,7 @@ int dc_sample(const float* verts, const int32_t* faces, const float* draws, int 
     a.N = N;
     a.M = 0;
     a.mode = DC_BIDIR_MEAN;
-    return run_uniform(a, PH_AREA | PH_SAMPLE, nullptr, ws, ws_bytes, stream);
+    return run_uniform(a, PH_AREA | PH_SAMPLE, 0, nullptr, ws, ws_bytes, stream);
 }
 
 int dc_chamfer_fwd(const float* a_pts, const float* b, int T, int N, int M, int mode,
@@ -293,8 +298,8 @@ int dc_chamfer_fwd(const float* a_pts, const float* b, int T, int N, int M, int 
     a.N = N;
     a.M = M;
     a.mode = mode;
-    return run_uniform(a, PH_SAMPLE | PH_TARGETS | PH_CHAMFER | PH_FINAL | PH_LOSS, nullptr, ws,
-                       ws_bytes, stream);
+    return run_uniform(a, PH_SAMPLE | PH_TARGETS | PH_CHAMFER, EPI_RESCAN | EPI_LOSS, nullptr,
+                       ws, ws_bytes, stream);
 }
 
 int dc_chamfer_bwd(const float* a, const float* b, const int32_t* nn_ab, const int32_t* nn_ba,
@@ -337,9 +342,9 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
     a.N = N;
     a.M = M;
     a.mode = mode;
-    unsigned ph = PH_AREA | PH_SAMPLE | PH_TARGETS | PH_CHAMFER | PH_FINAL | PH_LOSS;
-    if (grad_verts) ph |= PH_BWD;
-    return run_uniform(a, ph, loss_total, ws, ws_bytes, stream);
+    const unsigned ph = PH_AREA | PH_SAMPLE | PH_TARGETS | PH_CHAMFER;
+    const int epi = EPI_RESCAN | EPI_LOSS | (grad_verts ? EPI_GRAD : 0);
+    return run_uniform(a, ph, epi, loss_total, ws, ws_bytes, stream);
 }
 
 int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draws,
@@ -368,15 +373,16 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draw
     a.N = N;
     a.M = M;
     a.mode = mode;
-    return run_uniform(a, PH_AREA | PH_SAMPLE | PH_BWD, nullptr, ws, ws_bytes, stream);
+    return run_uniform(a, PH_AREA | PH_SAMPLE, EPI_GRAD, nullptr, ws, ws_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------------------
 // batches
 // ---------------------------------------------------------------------------------------
 static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long& total_sub) {
-    s = Sizes{n, 0, 0, 0, 0};
+    s = Sizes{n, 0, 0, 0, 0, epilogue_slices(n), 0};
     total_sub = 0;
+    long long max_v = 0;
     for (int k = 0; k < n; ++k) {
         const long long upf = div_up(fr[k].N, ROWS_PER_UNIT);
         s.n_units += upf;
@@ -384,9 +390,12 @@ static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long& total_su
         s.rows += (long long)div_up(fr[k].N, ROW_PAD) * ROW_PAD;
         s.cols += (long long)div_up(fr[k].M, COL_PAD) * COL_PAD;
         total_sub += upf * div_up(fr[k].M, SUB);
+        if (fr[k].grad_verts && fr[k].V > max_v) max_v = fr[k].V;
     }
+    s.gscr = s.slices > 1 ? (long long)n * s.slices * 3 * max_v : 0;
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
-           total_sub < INT_LIMIT && s.n_units < INT_LIMIT;
+           total_sub < INT_LIMIT && s.n_units < INT_LIMIT && s.cols * 6 < INT_LIMIT * 16 &&
+           s.gscr < INT_LIMIT * 4;
 }
 
 size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames) {
@@ -488,6 +497,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     h->planned = 1;
     h->any_grad = any_grad;
     h->max_v = max_v;
+    h->slices = (int)sz.slices;
     cudaError_t e = cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, stream);
     if (!e) e = cudaStreamSynchronize(stream);
     if (e) return cuda_fail(e, "dc_batch_plan copy");
@@ -519,9 +529,10 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
     if (!e) e = launch_sample(w, n, rows, stream);
     if (!e) e = launch_targets(w, n, cols, stream);
     if (!e) e = launch_chamfer(w, (int)p.sz.n_units, p.total_sub, p.mode, stream);
-    if (!e) e = launch_finalize(w, n, rows, cols, p.mode, stream);
-    if (!e) e = launch_loss(w, n, p.mode, loss_total, stream);
-    if (!e && p.any_grad) e = launch_bwd(w, n, p.max_v, p.mode, stream);
+    if (!e)
+        e = launch_epilogue(w, n, (int)p.sz.slices, p.any_grad ? p.max_v : 0, p.mode,
+                            EPI_RESCAN | EPI_LOSS | (p.any_grad ? EPI_GRAD : 0), loss_total,
+                            stream);
     if (e) return cuda_fail(e, "dc_batch_run");
     return DC_OK;
 }

@@ -7,8 +7,8 @@
 // of sub-chunks whatever the frame sizes. Partial minima of different CTAs merge through
 // 64-bit atomicMin on (distance bits << 32 | position), which keeps the smallest distance
 // and, among equal distances, the lowest position. The inner loop tracks minima only; the
-// argmin is recovered afterwards by re-scanning the one sub-chunk (rows) or the one 8-row
-// group (columns) that holds it, with bit-identical arithmetic.
+// argmin is recovered afterwards (epilogue.cu) by re-scanning the one sub-chunk (rows) or
+// the one thread's 16-row group (columns) that holds it, with bit-identical arithmetic.
 #include <math.h>
 
 #include "dc_internal.cuh"
@@ -33,41 +33,11 @@ __device__ __forceinline__ int last_le(const int* pre, int n, int g) {
     return lo;
 }
 
-// ---- packed float32 pairs (sm_100+ f32x2 arithmetic, each lane IEEE round-to-nearest) ----
-__device__ __forceinline__ u64 pk(float lo, float hi) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(u64 v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-    u64 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-    u64 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-    u64 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
+// ---- three-input minimum (one instruction on sm_100+) ----
 __device__ __forceinline__ float min3(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
-}
-
-// The scalar twin of the packed distance: dx = a - b, d = fma(dz, dz, fma(dy, dy, dx*dx)).
-__device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, float by,
-                                       float bz) {
-    const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
-    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
 // ---- mbarrier + bulk copy (global -> shared), all waits bounded ----
@@ -121,11 +91,76 @@ __device__ __forceinline__ bool mbar_wait(u64* bar, uint32_t parity) {
 // ---------------------------------------------------------------------------------------
 // the fused bidirectional kernel
 // ---------------------------------------------------------------------------------------
+constexpr int PAIRS = ROWS_PER_THREAD / 2;  // packed row pairs per thread
+
+// What the CTA knows about the unit segment it is working on (kept in shared memory so that
+// the inner loop's registers go to the rows and the running minima).
+struct UnitState {
+    const float* tx;  // the frame's negated, duplicated target planes (-X2, -Y2, -Z2)
+    int N, M, Mpad, row0, col0, rb, sub_lo, sub_hi;
+};
+
+// one sub-chunk: SUB targets against this thread's rows; row minima into cm, per-target warp
+// minima and the ballot of the lanes holding them into smv / smb
 template <bool BIDIR>
-__global__ void __launch_bounds__(THREADS, 4)
+__device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const float* __restrict__ ty,
+                                          const float* __restrict__ tz, const float2 (&rx)[PAIRS],
+                                          const float2 (&ry)[PAIRS], const float2 (&rz)[PAIRS],
+                                          float (&cm)[ROWS_PER_THREAD], unsigned* __restrict__ smv,
+                                          unsigned* __restrict__ smb) {
+#pragma unroll 2
+    for (int jj = 0; jj < SUB; jj += 2) {
+        // targets j, j+1 as {-X_j, -X_j} and {-X_j+1, -X_j+1}
+        const float4 xq = *reinterpret_cast<const float4*>(tx + 2 * jj);
+        const float4 yq = *reinterpret_cast<const float4*>(ty + 2 * jj);
+        const float4 zq = *reinterpret_cast<const float4*>(tz + 2 * jj);
+        const float2 X0 = make_float2(xq.x, xq.y), X1 = make_float2(xq.z, xq.w);
+        const float2 Y0 = make_float2(yq.x, yq.y), Y1 = make_float2(yq.z, yq.w);
+        const float2 Z0 = make_float2(zq.x, zq.y), Z1 = make_float2(zq.z, zq.w);
+        float c0 = INFINITY, c1 = INFINITY;
+#pragma unroll
+        for (int p = 0; p < PAIRS; ++p) {
+            // x + (-X) rounds exactly like x - X
+            float2 dx = __fadd2_rn(rx[p], X0), dy = __fadd2_rn(ry[p], Y0),
+                   dz = __fadd2_rn(rz[p], Z0);
+            const float2 d0 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            dx = __fadd2_rn(rx[p], X1);
+            dy = __fadd2_rn(ry[p], Y1);
+            dz = __fadd2_rn(rz[p], Z1);
+            const float2 d1 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            cm[2 * p] = min3(cm[2 * p], d0.x, d1.x);
+            cm[2 * p + 1] = min3(cm[2 * p + 1], d0.y, d1.y);
+            if (BIDIR) {
+                c0 = min3(c0, d0.x, d0.y);
+                c1 = min3(c1, d1.x, d1.y);
+            }
+        }
+        if (BIDIR) {
+            // warp minimum of each target and the lanes holding it; every lane stores the
+            // same value (no divergent branch); the first lane is taken later
+            const unsigned v0 = __float_as_uint(c0), v1 = __float_as_uint(c1);
+            const unsigned m0 = __reduce_min_sync(0xffffffffu, v0);
+            const unsigned m1 = __reduce_min_sync(0xffffffffu, v1);
+            const unsigned q0 = __ballot_sync(0xffffffffu, v0 == m0);
+            const unsigned q1 = __ballot_sync(0xffffffffu, v1 == m1);
+            *reinterpret_cast<uint2*>(smv + jj) = make_uint2(m0, m1);
+            *reinterpret_cast<uint2*>(smb + jj) = make_uint2(q0, q1);
+        }
+    }
+}
+
+template <bool BIDIR>
+__global__ void __launch_bounds__(THREADS, DC_CHAMFER_MIN_BLOCKS)
     k_chamfer(Ws w, int n_units, int total_sub) {
-    __shared__ __align__(128) float s_t[2][3][CHUNK];
-    __shared__ __align__(16) u64 s_col[BIDIR ? 2 : 1][BIDIR ? WARPS : 1][BIDIR ? CHUNK : 1];
+    // targets of two chunks, each coordinate negated and twice: [buffer][plane][2 * CHUNK]
+    __shared__ __align__(128) float s_t[2][3][2 * CHUNK];
+    // per-warp column minima of the chunk and the ballot of the lanes that hold them
+    __shared__ __align__(16) unsigned s_cv[BIDIR ? 2 : 1][BIDIR ? WARPS : 1][BIDIR ? CHUNK : 1];
+    __shared__ __align__(16) unsigned s_cb[BIDIR ? 2 : 1][BIDIR ? WARPS : 1][BIDIR ? CHUNK : 1];
+    // per-row running minimum over the unit and the sub-chunk that holds it
+    __shared__ float s_best[ROWS_PER_THREAD][THREADS];
+    __shared__ unsigned s_bidx[ROWS_PER_THREAD][THREADS];
+    __shared__ UnitState s_u;
     __shared__ __align__(8) u64 s_bar[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -140,141 +175,128 @@ __global__ void __launch_bounds__(THREADS, 4)
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
 
     uint32_t par = 0;     // bit b: the phase parity to wait for on buffer b
-    uint32_t pending = 0; // bit b: a copy into buffer b is in flight
+    uint32_t pending = 0; // bit b: a copy into buffer b is in flight (thread 0)
     int seq = 0;          // chunks consumed so far; buffer = seq & 1
     bool abort = false;
+    constexpr uint32_t PLANE_BYTES = 2 * CHUNK * sizeof(float);
 
     while (s < s_end) {
-        const int k = w.unit_frame[u], rb = w.unit_rb[u];
-        const FrameDesc* fr = w.frames + k;
-        const int N = fr->N, M = fr->M, Mpad = fr->Mpad, row0 = fr->row0, col0 = fr->col0;
-        const int upre = w.unit_pre[u], unext = w.unit_pre[u + 1];
-        const int sub_lo = s - upre, sub_hi = min(s_end, unext) - upre;
-        const float* TX = w.tsoa + 3LL * col0;
-        const int c_lo = sub_lo / SUBS_PER_CHUNK, c_hi = (sub_hi - 1) / SUBS_PER_CHUNK;
-
-        // stage the first two chunks of this unit (both buffers are free here)
+        __syncthreads();  // the previous segment is done with s_u
         if (tid == 0) {
+            const FrameDesc* fr = w.frames + w.unit_frame[u];
+            const int upre = w.unit_pre[u];
+            s_u.N = fr->N;
+            s_u.M = fr->M;
+            s_u.Mpad = fr->Mpad;
+            s_u.row0 = fr->row0;
+            s_u.col0 = fr->col0;
+            s_u.rb = w.unit_rb[u];
+            s_u.sub_lo = s - upre;
+            s_u.sub_hi = min(s_end, w.unit_pre[u + 1]) - upre;
+            s_u.tx = w.tsoa + 6LL * fr->col0;
+            // stage the first two chunks of this segment (both buffers are free here)
+            const int c_lo = s_u.sub_lo / SUBS_PER_CHUNK;
+            const int c_hi = (s_u.sub_hi - 1) / SUBS_PER_CHUNK;
             for (int c = c_lo; c <= min(c_hi, c_lo + 1); ++c) {
                 const int b = (seq + c - c_lo) & 1;
-                mbar_expect_tx(&s_bar[b], 3 * CHUNK * sizeof(float));
+                mbar_expect_tx(&s_bar[b], 3 * PLANE_BYTES);
                 for (int p = 0; p < 3; ++p)
-                    bulk_g2s(&s_t[b][p][0], TX + (long long)p * Mpad + (long long)c * CHUNK,
-                             CHUNK * sizeof(float), &s_bar[b]);
+                    bulk_g2s(&s_t[b][p][0], s_u.tx + 2LL * p * s_u.Mpad + 2LL * c * CHUNK,
+                             PLANE_BYTES, &s_bar[b]);
                 pending |= 1u << b;
             }
         }
-
-        // this thread's ROWS_PER_THREAD sim points, duplicated into both f32x2 lanes
-        const int wrow0 = rb * ROWS_PER_UNIT + warp * ROWS_PER_WARP;
+        __syncthreads();
+        const int N = s_u.N;
+        const int wrow0 = s_u.rb * ROWS_PER_UNIT + warp * ROWS_PER_WARP;
         const bool wactive = wrow0 < N;
         const int trow0 = wrow0 + lane * ROWS_PER_THREAD;
-        const unsigned rg_base = (unsigned)(wrow0 / ROWS_PER_THREAD);
-        const int n_active = min(WARPS, div_up(N - rb * ROWS_PER_UNIT, ROWS_PER_WARP));
-        u64 rx[ROWS_PER_THREAD], ry[ROWS_PER_THREAD], rz[ROWS_PER_THREAD];
-        float best[ROWS_PER_THREAD];
-        unsigned bidx[ROWS_PER_THREAD];
+
+        // this thread's rows as packed pairs {x_2p, x_2p+1}, loaded straight into the pair
+        // halves (inactive warps read valid rows of the frame and never use them); building
+        // the pairs from whole float4 loads instead costs register moves in the inner loop
+        float2 rx[PAIRS], ry[PAIRS], rz[PAIRS];
+        {
+            const float* xs =
+                reinterpret_cast<const float*>(w.x + s_u.row0 + (wactive ? trow0 : 0));
+#pragma unroll
+            for (int p = 0; p < PAIRS; ++p) {
+                rx[p].x = xs[8 * p + 0];
+                rx[p].y = xs[8 * p + 4];
+                ry[p].x = xs[8 * p + 1];
+                ry[p].y = xs[8 * p + 5];
+                rz[p].x = xs[8 * p + 2];
+                rz[p].y = xs[8 * p + 6];
+            }
+        }
 #pragma unroll
         for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (wactive) p = w.x[row0 + trow0 + r];
-            rx[r] = pk(p.x, p.x);
-            ry[r] = pk(p.y, p.y);
-            rz[r] = pk(p.z, p.z);
-            best[r] = INFINITY;
-            bidx[r] = 0;
+            s_best[r][tid] = INFINITY;
+            s_bidx[r][tid] = 0u;
         }
 
+        const int c_lo = s_u.sub_lo / SUBS_PER_CHUNK, c_hi = (s_u.sub_hi - 1) / SUBS_PER_CHUNK;
         for (int c = c_lo; c <= c_hi; ++c, ++seq) {
             const int b = seq & 1;
-            // every lane of a warp must agree before the warp-wide reductions below
+            // every lane of a warp must agree before the warp-wide reductions
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&s_bar[b], (par >> b) & 1u));
             if (ok) par ^= 1u << b;
-            const int sc0 = max(sub_lo, c * SUBS_PER_CHUNK);
-            const int sc1 = min(sub_hi, (c + 1) * SUBS_PER_CHUNK);
+            const int sc0 = max(s_u.sub_lo, c * SUBS_PER_CHUNK);
+            const int sc1 = min(s_u.sub_hi, (c + 1) * SUBS_PER_CHUNK);
             if (ok && wactive) {
                 for (int sc = sc0; sc < sc1; ++sc) {
                     const int off = (sc - c * SUBS_PER_CHUNK) * SUB;
                     float cm[ROWS_PER_THREAD];
 #pragma unroll
                     for (int r = 0; r < ROWS_PER_THREAD; ++r) cm[r] = INFINITY;
-#pragma unroll 2
-                    for (int jj = 0; jj < SUB; jj += 4) {
-                        const float4 xq = *reinterpret_cast<const float4*>(&s_t[b][0][off + jj]);
-                        const float4 yq = *reinterpret_cast<const float4*>(&s_t[b][1][off + jj]);
-                        const float4 zq = *reinterpret_cast<const float4*>(&s_t[b][2][off + jj]);
-                        const u64 X01 = pk(xq.x, xq.y), X23 = pk(xq.z, xq.w);
-                        const u64 Y01 = pk(yq.x, yq.y), Y23 = pk(yq.z, yq.w);
-                        const u64 Z01 = pk(zq.x, zq.y), Z23 = pk(zq.z, zq.w);
-                        float c0 = INFINITY, c1 = INFINITY, c2 = INFINITY, c3 = INFINITY;
-#pragma unroll
-                        for (int r = 0; r < ROWS_PER_THREAD; r += 2) {
-                            float a[2][4];
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                u64 dx = sub2(rx[r + h], X01), dy = sub2(ry[r + h], Y01),
-                                    dz = sub2(rz[r + h], Z01);
-                                const u64 d01 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-                                dx = sub2(rx[r + h], X23);
-                                dy = sub2(ry[r + h], Y23);
-                                dz = sub2(rz[r + h], Z23);
-                                const u64 d23 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-                                upk(d01, a[h][0], a[h][1]);
-                                upk(d23, a[h][2], a[h][3]);
-                                cm[r + h] = min3(cm[r + h], a[h][0], a[h][1]);
-                                cm[r + h] = min3(cm[r + h], a[h][2], a[h][3]);
-                            }
-                            if (BIDIR) {
-                                c0 = min3(c0, a[0][0], a[1][0]);
-                                c1 = min3(c1, a[0][1], a[1][1]);
-                                c2 = min3(c2, a[0][2], a[1][2]);
-                                c3 = min3(c3, a[0][3], a[1][3]);
-                            }
-                        }
-                        if (BIDIR) {
-                            const float cc[4] = {c0, c1, c2, c3};
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) {
-                                const unsigned v = __float_as_uint(cc[t]);
-                                const unsigned m = __reduce_min_sync(0xffffffffu, v);
-                                const unsigned bal = __ballot_sync(0xffffffffu, v == m);
-                                if (lane == 0)
-                                    s_col[b][warp][off + jj + t] =
-                                        ((u64)m << 32) | (u64)(rg_base + (__ffs(bal) - 1));
-                            }
-                        }
-                    }
+                    sub_chunk<BIDIR>(&s_t[b][0][2 * off], &s_t[b][1][2 * off], &s_t[b][2][2 * off],
+                                     rx, ry, rz, cm, BIDIR ? &s_cv[b][warp][off] : nullptr,
+                                     BIDIR ? &s_cb[b][warp][off] : nullptr);
 #pragma unroll
                     for (int r = 0; r < ROWS_PER_THREAD; ++r)
-                        if (cm[r] < best[r]) {
-                            best[r] = cm[r];
-                            bidx[r] = (unsigned)sc;
+                        if (cm[r] < s_best[r][tid]) {
+                            s_best[r][tid] = cm[r];
+                            s_bidx[r][tid] = (unsigned)sc;
                         }
                 }
             }
             abort = __syncthreads_or(!ok) != 0;
             if (abort) break;
-            pending &= ~(1u << b);
-            // buffer b is free again: stage chunk c + 2 into it
-            if (tid == 0 && c + 2 <= c_hi) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&s_bar[b], 3 * CHUNK * sizeof(float));
-                for (int p = 0; p < 3; ++p)
-                    bulk_g2s(&s_t[b][p][0],
-                             TX + (long long)p * Mpad + (long long)(c + 2) * CHUNK,
-                             CHUNK * sizeof(float), &s_bar[b]);
-                pending |= 1u << b;
+            if (tid == 0) {
+                pending &= ~(1u << b);
+                // buffer b is free again: stage chunk c + 2 into it
+                if (c + 2 <= c_hi) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(&s_bar[b], 3 * PLANE_BYTES);
+                    for (int p = 0; p < 3; ++p)
+                        bulk_g2s(&s_t[b][p][0],
+                                 s_u.tx + 2LL * p * s_u.Mpad + 2LL * (c + 2) * CHUNK, PLANE_BYTES,
+                                 &s_bar[b]);
+                    pending |= 1u << b;
+                }
             }
             if (BIDIR) {
+                // CTA minimum of each target of the chunk over its active warps (the lowest
+                // warp and, within it, the lowest lane among equals), merged globally
+                const int n_active =
+                    min(WARPS, div_up(N - s_u.rb * ROWS_PER_UNIT, ROWS_PER_WARP));
+                const unsigned rg0 = (unsigned)(s_u.rb * ROWS_PER_UNIT / ROWS_PER_THREAD);
                 const int j0 = sc0 * SUB - c * CHUNK;
-                const int jend = min(sc1 * SUB, M) - c * CHUNK;
+                const int jend = min(sc1 * SUB, s_u.M) - c * CHUNK;
                 for (int j = j0 + tid; j < jend; j += THREADS) {
-                    u64 v = s_col[b][0][j];
-                    for (int q = 1; q < n_active; ++q) v = min(v, s_col[b][q][j]);
-                    atomicMin(&w.pba[col0 + c * CHUNK + j], v);
+                    unsigned bv = s_cv[b][0][j], bw = 0;
+                    for (int q = 1; q < n_active; ++q) {
+                        const unsigned v = s_cv[b][q][j];
+                        if (v < bv) {
+                            bv = v;
+                            bw = q;
+                        }
+                    }
+                    const unsigned lane_first = __ffs(s_cb[b][bw][j]) - 1;
+                    const unsigned rg = rg0 + bw * 32 + lane_first;
+                    atomicMin(&w.pba[s_u.col0 + c * CHUNK + j], ((u64)bv << 32) | (u64)rg);
                 }
             }
         }
@@ -284,11 +306,11 @@ __global__ void __launch_bounds__(THREADS, 4)
             for (int r = 0; r < ROWS_PER_THREAD; ++r) {
                 const int row = trow0 + r;
                 if (row < N)
-                    atomicMin(&w.pab[row0 + row],
-                              ((u64)__float_as_uint(best[r]) << 32) | (u64)bidx[r]);
+                    atomicMin(&w.pab[s_u.row0 + row],
+                              ((u64)__float_as_uint(s_best[r][tid]) << 32) | (u64)s_bidx[r][tid]);
             }
         }
-        s = unext;
+        s = min(s_end, w.unit_pre[u + 1]);
         ++u;
     }
 
@@ -301,127 +323,6 @@ __global__ void __launch_bounds__(THREADS, 4)
         }
         __syncthreads();
     }
-}
-
-// ---------------------------------------------------------------------------------------
-// argmin recovery: rows re-scan their winning sub-chunk, columns their winning row group
-// ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_finalize(Ws w, int n_frames, int rows, int cols,
-                                                  int bidir) {
-    const int total = rows + (bidir ? cols : 0);
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        if (g < rows) {
-            const int k = last_le(w.rowpre, n_frames, g);
-            const FrameDesc* fr = w.frames + k;
-            const int i = g - fr->row0;
-            if (i >= fr->N) continue;
-            const u64 p = w.pab[g];
-            int found = -1;
-            if (p != EMPTY) {
-                const unsigned d = (unsigned)(p >> 32);
-                const int j0 = (int)(p & 0xffffffffu) * SUB, j1 = min(j0 + SUB, fr->M);
-                const float4 x = w.x[g];
-                const float* X = w.tsoa + 3LL * fr->col0;
-                const float* Y = X + fr->Mpad;
-                const float* Z = Y + fr->Mpad;
-                for (int j = j0; j < j1; ++j)
-                    if (__float_as_uint(dist2(x.x, x.y, x.z, X[j], Y[j], Z[j])) == d) {
-                        found = j;
-                        break;
-                    }
-            }
-            if (found < 0) set_status(&w.hdr->status, DC_EDEVICE);
-            fr->nn_ab[i] = found;
-        } else {
-            const int gc = g - rows;
-            const int k = last_le(w.colpre, n_frames, gc);
-            const FrameDesc* fr = w.frames + k;
-            const int j = gc - fr->col0;
-            if (j >= fr->M) continue;
-            const u64 p = w.pba[gc];
-            int found = -1;
-            if (p != EMPTY) {
-                const unsigned d = (unsigned)(p >> 32);
-                const int r0 = (int)(p & 0xffffffffu) * ROWS_PER_THREAD;
-                const int r1 = min(r0 + ROWS_PER_THREAD, fr->N);
-                const float* X = w.tsoa + 3LL * fr->col0;
-                const float tx = X[j], ty = X[fr->Mpad + j], tz = X[2 * fr->Mpad + j];
-                for (int r = r0; r < r1; ++r) {
-                    const float4 x = w.x[fr->row0 + r];
-                    if (__float_as_uint(dist2(x.x, x.y, x.z, tx, ty, tz)) == d) {
-                        found = r;
-                        break;
-                    }
-                }
-            }
-            if (found < 0) set_status(&w.hdr->status, DC_EDEVICE);
-            fr->nn_ba[j] = found;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// per-frame loss (Eq. 1 / Eq. 2): fixed-order compensated sums of the minimum distances
-// ---------------------------------------------------------------------------------------
-constexpr int LOSS_THREADS = 256;
-
-__device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
-    const int tid = threadIdx.x;
-    s_red[tid] = v;
-    __syncthreads();
-    for (int o = LOSS_THREADS / 2; o > 0; o >>= 1) {
-        if (tid < o) s_red[tid] = __fadd_rn(s_red[tid], s_red[tid + o]);
-        __syncthreads();
-    }
-    const float r = s_red[0];
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
-    const float y = __fsub_rn(v, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
-__global__ void __launch_bounds__(LOSS_THREADS) k_loss(Ws w, int bidir) {
-    __shared__ float s_red[LOSS_THREADS];
-    const FrameDesc* fr = w.frames + blockIdx.x;
-    const int N = fr->N, M = fr->M;
-    float s = 0.f, c = 0.f;
-    for (int i = threadIdx.x; i < N; i += LOSS_THREADS)
-        kahan_add(s, c, __uint_as_float((unsigned)(w.pab[fr->row0 + i] >> 32)));
-    const float sab = block_sum_fixed(s, s_red);
-    float L = 0.f;
-    if (bidir) {
-        s = 0.f;
-        c = 0.f;
-        for (int j = threadIdx.x; j < M; j += LOSS_THREADS)
-            kahan_add(s, c, __uint_as_float((unsigned)(w.pba[fr->col0 + j] >> 32)));
-        const float sba = block_sum_fixed(s, s_red);
-        L = __fadd_rn(__fdiv_rn(sab, (float)N), __fdiv_rn(sba, (float)M));
-    } else {
-        L = sab;
-    }
-    if (threadIdx.x == 0) fr->loss[0] = L;
-}
-
-// total = sum_k w_k L_k in a fixed order (lane-strided partial sums, then a fixed tree)
-__global__ void k_total(Ws w, int n_frames, float* total) {
-    const int lane = threadIdx.x;
-    float s = 0.f, c = 0.f;
-    for (int k = lane; k < n_frames; k += 32) {
-        const FrameDesc* fr = w.frames + k;
-        kahan_add(s, c, __fmul_rn(fr->weight, fr->loss[0]));
-    }
-    for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
-    if (lane == 0) total[0] = s;
-}
-
-int grid_for(long long n, int threads) {
-    long long b = (n + threads - 1) / threads;
-    return (int)(b < 1 ? 1 : (b > 65535LL * 16 ? 65535LL * 16 : b));
 }
 
 int g_chamfer_ctas[64][2];  // per device, per mode: resident CTAs for the persistent grid
@@ -456,25 +357,6 @@ cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, cu
         k_chamfer<false><<<grid, THREADS, 0, s>>>(w, n_units, total_sub);
     prof_after(s);
     count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const Ws& w, int n_frames, int rows, int cols, int mode,
-                            cudaStream_t s) {
-    const int bidir = mode == DC_BIDIR_MEAN;
-    k_finalize<<<grid_for(rows + (bidir ? cols : 0), 256), 256, 0, s>>>(w, n_frames, rows, cols,
-                                                                         bidir);
-    count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_loss(const Ws& w, int n_frames, int mode, float* total, cudaStream_t s) {
-    k_loss<<<n_frames, LOSS_THREADS, 0, s>>>(w, mode == DC_BIDIR_MEAN);
-    count_launch();
-    if (total) {
-        k_total<<<1, 32, 0, s>>>(w, n_frames, total);
-        count_launch();
-    }
     return cudaGetLastError();
 }
 

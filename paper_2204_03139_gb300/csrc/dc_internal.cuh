@@ -10,21 +10,33 @@ namespace dc {
 
 // ---------------------------------------------------------------------------------------
 // Chamfer tiling. A CTA of WARPS warps owns one "unit": ROWS_PER_UNIT consecutive sim points
-// of one frame, ROWS_PER_THREAD per thread held in registers. Targets stream through shared
-// memory in chunks of CHUNK points (structure-of-arrays planes, bulk-copied); inside a
-// chunk the per-row minimum is tracked per sub-chunk of SUB targets, so that a row's
-// nearest neighbour can later be found again by re-scanning one sub-chunk.
+// of one frame, ROWS_PER_THREAD per thread held in registers as packed pairs {x_i, x_i+1}.
+// Targets stream through shared memory in chunks of CHUNK points: structure-of-arrays planes
+// holding every coordinate negated and twice, {-X_j, -X_j}, bulk-copied. The per-row minimum
+// is tracked per sub-chunk of SUB targets, so that a row's nearest neighbour can later be
+// found again by re-scanning one sub-chunk, and a target's by re-scanning one thread's rows.
 // ---------------------------------------------------------------------------------------
-constexpr int ROWS_PER_THREAD = 8;
-constexpr int WARPS = 4;
+#ifndef DC_ROWS_PER_THREAD
+#define DC_ROWS_PER_THREAD 16
+#endif
+#ifndef DC_WARPS
+#define DC_WARPS 4
+#endif
+#ifndef DC_CHAMFER_MIN_BLOCKS
+#define DC_CHAMFER_MIN_BLOCKS 3
+#endif
+constexpr int ROWS_PER_THREAD = DC_ROWS_PER_THREAD;  // even
+constexpr int WARPS = DC_WARPS;
 constexpr int THREADS = 32 * WARPS;
-constexpr int ROWS_PER_WARP = 32 * ROWS_PER_THREAD;       // 256
-constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * WARPS;      // 1024
+constexpr int ROWS_PER_WARP = 32 * ROWS_PER_THREAD;       // 512
+constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * WARPS;      // 2048
 constexpr int SUB = 64;                                   // targets per tracked sub-chunk
 constexpr int CHUNK = 256;                                // targets per staged chunk
 constexpr int SUBS_PER_CHUNK = CHUNK / SUB;
 constexpr int ROW_PAD = ROWS_PER_WARP;                    // sim points padded to this
 constexpr int COL_PAD = CHUNK;                            // target points padded to this
+constexpr int EPI_CTAS = 304;                             // epilogue CTAs to aim for
+constexpr int MAX_SLICES = 8;                             // epilogue slices per frame
 
 constexpr float COORD_MAX = 1e15f;
 constexpr unsigned long long EMPTY = ~0ull;
@@ -67,18 +79,27 @@ struct WsHeader {
     int planned;      // batch plan written
     int any_grad;
     int max_v;        // largest V among frames with a gradient
-    int pad[53];
+    int slices;       // epilogue slices per frame
+    int pad[52];
 };
 
 // Byte offsets of every region of a workspace (computed on the host).
 struct Layout {
     size_t hdr, frames, rowpre, colpre, unit_frame, unit_rb, unit_pre, cdf, x, fw, tsoa, pab,
-        pba, nnab, nnba, loss, total;
+        pba, nnab, nnba, loss, part, gscr, total;
 };
 
 struct Sizes {
     long long n_frames, n_units, sum_f, rows, cols;
+    long long slices;  // epilogue slices per frame
+    long long gscr;    // floats of per-slice gradient partials (0 when slices == 1)
 };
+
+// Epilogue slices per frame: enough CTAs to cover the GPU, at most MAX_SLICES.
+inline int epilogue_slices(long long n_frames) {
+    long long s = (EPI_CTAS + n_frames - 1) / n_frames;
+    return (int)(s < 1 ? 1 : (s > MAX_SLICES ? MAX_SLICES : s));
+}
 
 Layout make_layout(const Sizes& s);
 
@@ -94,12 +115,14 @@ struct Ws {
     float* cdf;        // [sum F]
     float4* x;         // [rows] sampled points (w lane unused), NaN beyond N
     int4* fw;          // [rows] (face, w0, w1, w2 bits)
-    float* tsoa;       // [3 * cols] per frame: X[Mpad], Y[Mpad], Z[Mpad], NaN beyond M
+    float* tsoa;       // [6 * cols] per frame: X2[2 Mpad], Y2, Z2 = {-v, -v} pairs, sentinel beyond M
     unsigned long long* pab;  // [rows] packed (d bits << 32 | sub-chunk)
     unsigned long long* pba;  // [cols] packed (d bits << 32 | row group)
     int* nnab;         // [rows] fallback neighbour buffers
     int* nnba;         // [cols]
     float* loss;       // [n_frames] fallback loss buffer
+    float* part;       // [n_frames][slices][2] loss partial sums
+    float* gscr;       // [n_frames][slices][3 max_v] gradient partials (slices > 1)
 };
 
 Ws make_ws(void* base, const Layout& L);
@@ -125,7 +148,7 @@ struct UniformArgs {
     float* out_bary;
     const float* weight;   // [T] nullable
     const float* gscale;   // [T] nullable: defaults to weight
-    int T, V, F, N, M, mode, units_per_frame, subs_per_unit;
+    int T, V, F, N, M, mode, units_per_frame, subs_per_unit, slices;
 };
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s);
@@ -134,10 +157,10 @@ cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s);
 cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s);
 cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s);
 cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, cudaStream_t s);
-cudaError_t launch_finalize(const Ws& w, int n_frames, int rows, int cols, int mode,
-                            cudaStream_t s);
-cudaError_t launch_loss(const Ws& w, int n_frames, int mode, float* total, cudaStream_t s);
-cudaError_t launch_bwd(const Ws& w, int n_frames, int max_v, int mode, cudaStream_t s);
+// epilogue: neighbour recovery (rescan), loss partials, gradient scatter
+enum : int { EPI_RESCAN = 1, EPI_LOSS = 2, EPI_GRAD = 4 };
+cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, int mode,
+                            int flags, float* total, cudaStream_t s);
 cudaError_t launch_chamfer_bwd_points(const float* a, const float* b, const int* nn_ab,
                                       const int* nn_ba, int T, int N, int M, int mode,
                                       const float* g, float* grad_a, cudaStream_t s);

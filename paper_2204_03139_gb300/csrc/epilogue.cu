@@ -1,0 +1,398 @@
+// After the Chamfer pass: nearest-neighbour recovery, the loss (Eq. 1 / Eq. 2) and the
+// adjoint -- dL/dx_i along the chosen neighbours scattered to the picked face's vertices with
+// the barycentric weights (Eq. 4).
+//
+// One CTA per (frame, slice): the frame's sim points and target points are cut into
+// `slices` equal ranges so that the whole GPU works even on few frames. Each CTA
+//   - re-scans the sub-chunk (rows) or 16-row group (targets) that the packed minimum
+//     points at, with the same float32 operations as the Chamfer kernel, to find the first
+//     index attaining it (ties go to the lowest index);
+//   - sums its minimum distances (fixed order) into a per-slice partial;
+//   - scatters the gradient into a shared-memory copy of the frame's V x 3 gradient, then
+//     writes it out (one slice) or to a per-slice partial that k_grad_reduce sums in order.
+#include "dc_internal.cuh"
+
+namespace dc {
+
+namespace {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, DC_OK, code); }
+
+// dx = a - b, d = fma(dz, dz, fma(dy, dy, dx * dx)): the scalar twin of the packed distance
+__device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, float by,
+                                       float bz) {
+    const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// G[v_c] += w_c * g for the three vertices of the face recorded in q = (f, w0, w1, w2)
+__device__ __forceinline__ void scatter(float* __restrict__ G, const int* __restrict__ faces,
+                                        int V, int4 q, float gx, float gy, float gz) {
+    const int f = q.x;
+    if (f < 0) return;
+    const float wc[3] = {__int_as_float(q.y), __int_as_float(q.z), __int_as_float(q.w)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int v = faces[3 * f + c];
+        if ((unsigned)v >= (unsigned)V) continue;
+        atomicAdd(&G[3 * v + 0], __fmul_rn(wc[c], gx));
+        atomicAdd(&G[3 * v + 1], __fmul_rn(wc[c], gy));
+        atomicAdd(&G[3 * v + 2], __fmul_rn(wc[c], gz));
+    }
+}
+
+constexpr int EPI_THREADS = 512;
+
+struct EpiArgs {
+    int slices;
+    int flags;     // EPI_RESCAN | EPI_LOSS | EPI_GRAD
+    int bidir;
+    int use_smem;  // the V x 3 accumulator fits in shared memory
+    int vstride;   // floats per slice in gscr (3 * max V)
+};
+
+__device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
+    // fixed-order tree: warp shuffles, then warp 0 over the per-warp sums
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    float r = 0.f;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) r = __fadd_rn(r, __shfl_down_sync(0xffffffffu, r, o));
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
+    extern __shared__ float s_acc[];
+    __shared__ float s_red[EPI_THREADS / 32];
+    const int k = blockIdx.x / e.slices, sl = blockIdx.x - k * e.slices;
+    const int tid = threadIdx.x;
+    const FrameDesc* fr = w.frames + k;
+    const int N = fr->N, M = fr->M, V = fr->V, row0 = fr->row0, col0 = fr->col0;
+    const bool grad = (e.flags & EPI_GRAD) && fr->grad && fr->verts;
+    const bool rescan = (e.flags & EPI_RESCAN) != 0, want_loss = (e.flags & EPI_LOSS) != 0;
+    const int* faces = fr->faces;
+    const float* tgt = fr->tgt;
+
+    float* G = nullptr;
+    if (grad) {
+        if (e.use_smem) {
+            G = s_acc;
+            for (int v = tid; v < 3 * V; v += EPI_THREADS) G[v] = 0.0f;
+        } else {
+            G = fr->grad;  // zeroed by the area kernel
+        }
+    }
+    __syncthreads();
+
+    const float gs = fr->gscale;
+    const float cab = e.bidir ? __fdiv_rn(__fmul_rn(2.0f, gs), (float)N) : __fmul_rn(2.0f, gs);
+    const float cba = __fdiv_rn(__fmul_rn(2.0f, gs), (float)M);
+
+    // ---- sim points of this slice, 32 per warp step ----
+    // Each row's minimum points at one sub-chunk of SUB targets; the warp re-scans the rows
+    // of its step one after another, each lane checking two candidates (coalesced loads), so
+    // that one L2 round trip serves a whole sub-chunk.
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = EPI_THREADS / 32;
+    const int i0 = (int)((long long)N * sl / e.slices);
+    const int i1 = (int)((long long)N * (sl + 1) / e.slices);
+    float sab = 0.f, cab_c = 0.f;
+    for (int base = i0 + warp * 32; base < i1; base += NW * 32) {
+        const int i = base + lane;
+        const bool valid = i < i1;
+        const int g = row0 + i;
+        u64 p = EMPTY;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 q = make_int4(-1, 0, 0, 0);
+        if (valid) {
+            x = w.x[g];
+            if (grad) q = w.fw[g];
+            if (rescan) p = w.pab[g];
+        }
+        int nn = -1;
+        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+        if (rescan) {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+                const u64 pr = __shfl_sync(0xffffffffu, p, r);
+                if (pr == EMPTY) continue;  // the same for every lane
+                const float qx = __shfl_sync(0xffffffffu, x.x, r);
+                const float qy = __shfl_sync(0xffffffffu, x.y, r);
+                const float qz = __shfl_sync(0xffffffffu, x.z, r);
+                const unsigned dq = (unsigned)(pr >> 32);
+                const int jb = (int)(pr & 0xffffffffu) * SUB;
+                const int ja = jb + lane, jc = ja + 32;
+                float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+                bool ma = false, mc = false;
+                if (ja < M) {
+                    const float* y = tgt + 3LL * ja;
+                    ax = y[0];
+                    ay = y[1];
+                    az = y[2];
+                    ma = __float_as_uint(dist2(qx, qy, qz, ax, ay, az)) == dq;
+                }
+                if (jc < M) {
+                    const float* y = tgt + 3LL * jc;
+                    cx = y[0];
+                    cy = y[1];
+                    cz = y[2];
+                    mc = __float_as_uint(dist2(qx, qy, qz, cx, cy, cz)) == dq;
+                }
+                const unsigned ba = __ballot_sync(0xffffffffu, ma);
+                const unsigned bc = __ballot_sync(0xffffffffu, mc);
+                // first candidate in target order: the lower half before the upper half
+                const int src = ba ? __ffs(ba) - 1 : (bc ? 31 + __ffs(bc) : -1);
+                const bool lo = src < 32;
+                const int from = src & 31;
+                const float mx = __shfl_sync(0xffffffffu, lo ? ax : cx, from);
+                const float my = __shfl_sync(0xffffffffu, lo ? ay : cy, from);
+                const float mz = __shfl_sync(0xffffffffu, lo ? az : cz, from);
+                if (lane == r) {
+                    nn = src < 0 ? -1 : jb + src;
+                    y0 = mx;
+                    y1 = my;
+                    y2 = mz;
+                }
+            }
+            if (valid) {
+                if (p != EMPTY && want_loss) kahan_add(sab, cab_c, __uint_as_float((unsigned)(p >> 32)));
+                if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
+                fr->nn_ab[i] = nn;
+            }
+        } else if (valid) {
+            nn = fr->nn_ab[i];
+            if ((unsigned)nn < (unsigned)M) {
+                const float* y = tgt + 3LL * nn;
+                y0 = y[0];
+                y1 = y[1];
+                y2 = y[2];
+            } else {
+                set_status(&w.hdr->status, DC_EINVAL);
+                nn = -1;
+            }
+        }
+        if (grad && valid && nn >= 0)
+            scatter(G, faces, V, q, __fmul_rn(cab, __fsub_rn(x.x, y0)),
+                    __fmul_rn(cab, __fsub_rn(x.y, y1)), __fmul_rn(cab, __fsub_rn(x.z, y2)));
+    }
+
+    // ---- target points of this slice (Eq. 1 only) ----
+    // A target's minimum points at one thread's group of ROWS_PER_THREAD sim points; the
+    // candidates are loaded eight at a time before any comparison.
+    float sba = 0.f, cba_c = 0.f;
+    if (e.bidir) {
+        const int j0 = (int)((long long)M * sl / e.slices);
+        const int j1 = (int)((long long)M * (sl + 1) / e.slices);
+        for (int j = j0 + tid; j < j1; j += EPI_THREADS) {
+            const float* y = tgt + 3LL * j;
+            const float y0 = y[0], y1 = y[1], y2 = y[2];
+            int nn = -1;
+            float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rescan) {
+                const u64 p = w.pba[col0 + j];
+                if (p != EMPTY) {
+                    const unsigned dq = (unsigned)(p >> 32);
+                    const int rb = (int)(p & 0xffffffffu) * ROWS_PER_THREAD;
+                    for (int h = 0; h < ROWS_PER_THREAD && nn < 0; h += 8) {
+                        float4 xr[8];
+#pragma unroll
+                        for (int t = 0; t < 8; ++t)
+                            xr[t] = h + t < ROWS_PER_THREAD && rb + h + t < N
+                                        ? w.x[row0 + rb + h + t]
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int t = 0; t < 8; ++t)
+                            if (nn < 0 && h + t < ROWS_PER_THREAD && rb + h + t < N &&
+                                __float_as_uint(dist2(xr[t].x, xr[t].y, xr[t].z, y0, y1, y2)) == dq) {
+                                nn = rb + h + t;
+                                xm = xr[t];
+                            }
+                    }
+                    if (want_loss) kahan_add(sba, cba_c, __uint_as_float(dq));
+                }
+                if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
+                fr->nn_ba[j] = nn;
+            } else {
+                nn = fr->nn_ba[j];
+                if ((unsigned)nn < (unsigned)N) {
+                    xm = w.x[row0 + nn];
+                } else {
+                    set_status(&w.hdr->status, DC_EINVAL);
+                    nn = -1;
+                }
+            }
+            if (grad && nn >= 0)
+                scatter(G, faces, V, w.fw[row0 + nn], __fmul_rn(cba, __fsub_rn(xm.x, y0)),
+                        __fmul_rn(cba, __fsub_rn(xm.y, y1)), __fmul_rn(cba, __fsub_rn(xm.z, y2)));
+        }
+    }
+
+    if (want_loss) {
+        const float a = block_sum_fixed(sab, s_red);
+        const float b = block_sum_fixed(sba, s_red);
+        if (tid == 0) {
+            w.part[2 * (k * e.slices + sl)] = a;
+            w.part[2 * (k * e.slices + sl) + 1] = b;
+        }
+    }
+    if (grad && e.use_smem) {
+        __syncthreads();
+        float* dst = e.slices == 1 ? fr->grad : w.gscr + (size_t)(k * e.slices + sl) * e.vstride;
+        for (int v = tid; v < 3 * V; v += EPI_THREADS) dst[v] = s_acc[v];
+    }
+}
+
+// gradient of frame k = sum over its slices, in slice order
+__global__ void __launch_bounds__(256) k_grad_reduce(Ws w, int n_frames, int slices, int vstride) {
+    const long long n = (long long)n_frames * vstride;
+    for (long long t = blockIdx.x * 256LL + threadIdx.x; t < n; t += (long long)gridDim.x * 256) {
+        const int k = (int)(t / vstride), v = (int)(t - (long long)k * vstride);
+        const FrameDesc* fr = w.frames + k;
+        if (!fr->grad || !fr->verts || v >= 3 * fr->V) continue;
+        const float* src = w.gscr + (size_t)k * slices * vstride + v;
+        float s = 0.f;
+        for (int q = 0; q < slices; ++q) s = __fadd_rn(s, src[(size_t)q * vstride]);
+        fr->grad[v] = s;
+    }
+}
+
+// L_k from its slice partials (Eq. 1: means, Eq. 2: sum) and the weighted total, all in a
+// fixed order
+constexpr int LOSS_THREADS = 1024;
+
+__global__ void __launch_bounds__(LOSS_THREADS) k_frame_loss(Ws w, int n_frames, int slices,
+                                                             int bidir, float* total) {
+    __shared__ float s_red[LOSS_THREADS / 32];
+    float t = 0.f, tc = 0.f;
+    for (int k = threadIdx.x; k < n_frames; k += LOSS_THREADS) {
+        const FrameDesc* fr = w.frames + k;
+        float sab = 0.f, sba = 0.f;
+        for (int q = 0; q < slices; ++q) {
+            sab = __fadd_rn(sab, w.part[2 * (k * slices + q)]);
+            sba = __fadd_rn(sba, w.part[2 * (k * slices + q) + 1]);
+        }
+        const float L = bidir ? __fadd_rn(__fdiv_rn(sab, (float)fr->N), __fdiv_rn(sba, (float)fr->M))
+                              : sab;
+        fr->loss[0] = L;
+        kahan_add(t, tc, __fmul_rn(fr->weight, L));
+    }
+    const float s = block_sum_fixed(t, s_red);
+    if (threadIdx.x == 0 && total) total[0] = s;
+}
+
+// ---- gradient with respect to given sim points (dc_chamfer_bwd) ----
+__global__ void __launch_bounds__(256) k_cbwd_rows(const float* a, const float* b,
+                                                   const int* nn_ab, int T, int N, int M,
+                                                   int bidir, const float* g, float* grad) {
+    const long long n = (long long)T * N;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+        const int t = (int)(e / N);
+        const int j = nn_ab[e];
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        if ((unsigned)j < (unsigned)M) {
+            const float c = bidir ? __fdiv_rn(__fmul_rn(2.0f, g[t]), (float)N)
+                                  : __fmul_rn(2.0f, g[t]);
+            const float* y = b + 3LL * ((long long)t * M + j);
+            gx = __fmul_rn(c, __fsub_rn(a[3 * e], y[0]));
+            gy = __fmul_rn(c, __fsub_rn(a[3 * e + 1], y[1]));
+            gz = __fmul_rn(c, __fsub_rn(a[3 * e + 2], y[2]));
+        }
+        grad[3 * e] = gx;
+        grad[3 * e + 1] = gy;
+        grad[3 * e + 2] = gz;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cbwd_cols(const float* a, const float* b,
+                                                   const int* nn_ba, int T, int N, int M,
+                                                   const float* g, float* grad) {
+    const long long n = (long long)T * M;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+        const int t = (int)(e / M);
+        const int i = nn_ba[e];
+        if ((unsigned)i >= (unsigned)N) continue;
+        const float c = __fdiv_rn(__fmul_rn(2.0f, g[t]), (float)M);
+        const long long ia = (long long)t * N + i;
+        const float* x = a + 3 * ia;
+        atomicAdd(&grad[3 * ia], __fmul_rn(c, __fsub_rn(x[0], b[3 * e])));
+        atomicAdd(&grad[3 * ia + 1], __fmul_rn(c, __fsub_rn(x[1], b[3 * e + 1])));
+        atomicAdd(&grad[3 * ia + 2], __fmul_rn(c, __fsub_rn(x[2], b[3 * e + 2])));
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > 65535LL * 16 ? 65535LL * 16 : b));
+}
+
+int g_smem_limit[64];
+
+}  // namespace
+
+cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, int mode,
+                            int flags, float* total, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (g_smem_limit[dev] == 0) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (optin <= 0) optin = 48 * 1024;
+        optin -= 1024;  // room for the static reduction buffer
+        cudaError_t e = cudaFuncSetAttribute(k_epilogue,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return e;
+        g_smem_limit[dev] = optin;
+    }
+    EpiArgs a;
+    a.slices = slices;
+    a.flags = flags;
+    a.bidir = mode == DC_BIDIR_MEAN;
+    const bool grad = (flags & EPI_GRAD) && max_v > 0;
+    const size_t need = (size_t)max_v * 3 * sizeof(float);
+    a.use_smem = grad && need <= (size_t)g_smem_limit[dev];
+    a.vstride = 3 * max_v;
+    k_epilogue<<<n_frames * slices, EPI_THREADS, a.use_smem ? need : 0, s>>>(w, a);
+    count_launch();
+    if (flags & EPI_LOSS) {
+        k_frame_loss<<<1, LOSS_THREADS, 0, s>>>(w, n_frames, slices, a.bidir, total);
+        count_launch();
+    }
+    if (a.use_smem && slices > 1) {
+        k_grad_reduce<<<grid_for((long long)n_frames * a.vstride, 256), 256, 0, s>>>(
+            w, n_frames, slices, a.vstride);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chamfer_bwd_points(const float* a, const float* b, const int* nn_ab,
+                                      const int* nn_ba, int T, int N, int M, int mode,
+                                      const float* g, float* grad_a, cudaStream_t s) {
+    const int bidir = mode == DC_BIDIR_MEAN;
+    k_cbwd_rows<<<grid_for((long long)T * N, 256), 256, 0, s>>>(a, b, nn_ab, T, N, M, bidir, g,
+                                                                 grad_a);
+    count_launch();
+    if (bidir) {
+        k_cbwd_cols<<<grid_for((long long)T * M, 256), 256, 0, s>>>(a, b, nn_ba, T, N, M, g,
+                                                                     grad_a);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dc

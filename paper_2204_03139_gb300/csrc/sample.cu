@@ -48,6 +48,7 @@ __global__ void k_build_uniform(UniformArgs a, Ws w) {
         h->planned = 0;
         h->any_grad = a.grad != nullptr;
         h->max_v = a.V;
+        h->slices = a.slices;
     }
     if (g <= a.T) {
         w.rowpre[g] = g * Npad;
@@ -193,6 +194,9 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
         cdf[f] = run.hi;
     }
     if (bad_idx || bad_val) set_status(&w.hdr->status, DC_EINVAL);
+    // the gradient of this frame starts from zero (accumulated by the epilogue)
+    if (fr->grad)
+        for (int e = tid; e < 3 * V; e += CDF_THREADS) fr->grad[e] = 0.0f;
     if (f1 == F && f0 < f1) {
         const float A = run.hi;
         if (!(A > 0.0f) || !isfinite(A)) set_status(&w.hdr->status, DC_EDEGENERATE);
@@ -289,10 +293,12 @@ __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
             if (!coord_ok(vx) || !coord_ok(vy) || !coord_ok(vz))
                 set_status(&w.hdr->status, DC_EINVAL);
         }
-        float* X = w.tsoa + 3LL * fr->col0;
-        X[j] = vx;
-        X[fr->Mpad + j] = vy;
-        X[2 * fr->Mpad + j] = vz;
+        // planes of negated {-v, -v} pairs: X2 [2 Mpad], Y2 [2 Mpad], Z2 [2 Mpad]; the Chamfer
+        // kernel forms x - v as x + (-v), which rounds identically
+        float2* P = reinterpret_cast<float2*>(w.tsoa + 6LL * fr->col0);
+        P[j] = make_float2(-vx, -vx);
+        P[fr->Mpad + j] = make_float2(-vy, -vy);
+        P[2 * fr->Mpad + j] = make_float2(-vz, -vz);
         w.pba[g] = EMPTY;
     }
 }

@@ -1,0 +1,64 @@
+"""Batched frames of uneven sizes in one launch sequence (and its CUDA-graph replay) against
+the FP64 oracle and against the plain per-frame form (GB300 only)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def trajs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    tr = W.batched_uneven(n_traj=4, grid=(12, 30), T=(3, 5), m=(300, 3000))
+    return [parity.nudge_draws(t)[0] for t in tr]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_matches_oracle(trajs, graph, mode):
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
+
+    dts = [DeviceTrajectory.from_host(t, DEV) for t in trajs]
+    weights = [np.linspace(0.5, 1.5, t.T) for t in trajs]
+    b = BatchedLoss(dts, mode=mode, weights=weights, grad=True, graph=graph, nn=True)
+    for _ in range(2):  # replays give the same answer
+        total = b.run(check=True)
+        torch.cuda.synchronize()
+    ref_total = 0.0
+    for k, t in enumerate(trajs):
+        ref = oracle.loss_traj(t, mode=mode, weights=weights[k])
+        parity.check_loss(b.loss_frames[k].cpu().numpy(), ref["loss_frames"])
+        parity.check_grad(b.grad_verts[k].cpu().numpy(), ref["grad_verts"])
+        for f in range(t.T):
+            n0, n1 = t.n_off[f], t.n_off[f + 1]
+            per = ref["frames"][f]
+            nba = None
+            if mode == 0:
+                nba = b.nn_ba[k][t.m_off[f]:t.m_off[f + 1]].cpu().numpy()
+            parity.check_nn(b.nn_ab[k][n0:n1].cpu().numpy(), per["nn_ab"], nba,
+                            per["nn_ba"] if mode == 0 else None)
+        ref_total += ref["loss_total"]
+    parity.check_loss([float(total[0])], [ref_total], what="batch total")
+
+
+def test_batch_equals_per_frame_form(trajs):
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory, per_frame_loss
+
+    dts = [DeviceTrajectory.from_host(t, DEV) for t in trajs]
+    b = BatchedLoss(dts, grad=True, graph=True)
+    b.run(check=True)
+    lf, gv = per_frame_loss(dts)
+    torch.cuda.synchronize()
+    for k in range(len(dts)):
+        # the same kernels; the loss partial sums may be cut into different slices
+        np.testing.assert_allclose(b.loss_frames[k].cpu().numpy(), lf[k].cpu().numpy(),
+                                   rtol=1e-6)
+        assert parity.rel_l2(b.grad_verts[k].cpu().numpy(), gv[k].cpu().numpy()) < 1e-6
