@@ -171,6 +171,30 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
  */
 int dc_ws_status(const void* ws, dc_stream_t stream);
 
+/*
+ * dc_loss_traj_noalloc -- dc_loss_traj for callers that cannot allocate device memory when
+ * they need the loss (a plug-in whose host framework owns all device memory, a real-time
+ * loop that forbids allocator calls after start-up). The paper has no counterpart: this is
+ * an interface convenience.
+ *   Arguments and outputs as in dc_loss_traj; instead of a workspace it uses a built-in
+ *   16 MiB scratch array in device memory, which every GPU that loads the library holds
+ *   until the process exits.
+ *   status [1] device, nullable: receives the device-side error code of this call
+ *   (DC_OK, DC_EINVAL, DC_EDEGENERATE, ...), since the scratch is not visible to the caller.
+ *   Returns DC_ENOSPC, without launching anything, when dc_workspace_size(T, V, F, N, M)
+ *   exceeds 16 MiB (about fifteen frames of 10 000 samples against 10 000 targets on a
+ *   2 500-vertex mesh).
+ *   It calls no allocator. Its first call on a device looks up the scratch array's device
+ *   address with that device current; make that first call before any stream capture.
+ *   All calls on a device share the one array and each overwrites it: calls that may overlap
+ *   on the GPU (different streams, or threads without ordering) race and must not be issued.
+ */
+int dc_loss_traj_noalloc(const float* verts, const int32_t* faces, const float* draws,
+                         const float* targets, int T, int V, int F, int N, int M, int mode,
+                         const float* frame_w, float* loss_total, float* loss_frames,
+                         float* grad_verts, int32_t* nn_ab, int32_t* nn_ba, int32_t* status,
+                         dc_stream_t stream);
+
 /* Description of the last failure on the calling thread ("" if none). */
 const char* dc_last_error(void);
 

@@ -70,6 +70,8 @@ def lib() -> ctypes.CDLL:
                 "dc_launch_count": (ctypes.c_longlong, []),
                 "dc_prof_start": (I, [I]),
                 "dc_prof_stop": (I, [ctypes.POINTER(F), ctypes.POINTER(I)]),
+                "dc_loss_traj_noalloc": (I, [P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P,
+                                             P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -266,3 +268,29 @@ def prof_stop() -> tuple[float, int]:
     n = ctypes.c_int(0)
     _check(lib().dc_prof_stop(ctypes.byref(ms), ctypes.byref(n)))
     return float(ms.value), int(n.value)
+
+
+def dc_loss_traj_noalloc(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None,
+                         grad=True, check=False):
+    """dc_loss_traj on the library's built-in 16 MiB scratch array instead of a workspace,
+    for callers that cannot allocate device memory when they need the loss. The outputs are
+    allocated here for convenience; a caller that cannot allocate passes its own buffers to
+    the C function directly. check=True reads the device-side status the call wrote."""
+    dev = _dev(verts)
+    _f32(verts, "verts"), _i32(faces, "faces"), _f32(draws, "draws"), _f32(targets, "targets")
+    T, V, F, N, M = (verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1],
+                     targets.shape[1])
+    lt = torch.empty(1, dtype=torch.float32, device=dev)
+    lf = torch.empty(T, dtype=torch.float32, device=dev)
+    gv = torch.empty((T, V, 3), dtype=torch.float32, device=dev) if grad else None
+    nab = torch.empty((T, N), dtype=torch.int32, device=dev)
+    nba = torch.empty((T, M), dtype=torch.int32, device=dev) if mode == BIDIR_MEAN else None
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(lib().dc_loss_traj_noalloc(_ptr(verts), _ptr(faces), _ptr(draws), _ptr(targets), T, V,
+                                      F, N, M, mode, _ptr(frame_w), _ptr(lt), _ptr(lf), _ptr(gv),
+                                      _ptr(nab), _ptr(nba), _ptr(st), _stream(dev)))
+    if check:
+        code = int(st.item())
+        if code != DC_OK:
+            raise DCError(code, "device-side error reported by dc_loss_traj_noalloc")
+    return {"loss_total": lt, "loss_frames": lf, "grad_verts": gv, "nn_ab": nab, "nn_ba": nba}

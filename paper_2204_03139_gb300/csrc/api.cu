@@ -538,3 +538,67 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// dc_loss_traj_noalloc: dc_loss_traj with built-in scratch memory instead of a workspace
+// ---------------------------------------------------------------------------------------
+// Some callers cannot call cudaMalloc at the point where they need the loss: a plug-in inside
+// a host framework whose memory pool owns all device memory, or a real-time control loop that
+// forbids allocator calls after start-up (an allocation can synchronise the device and take
+// unbounded time). For them the scratch lives in this file-scope device array, reserved once
+// when the library's module is loaded on a GPU and held until the process exits.
+#define DC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64];  // device address of g_noalloc_scratch, per device
+}  // namespace
+
+extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
+                                    const float* draws, const float* targets, int T, int V, int F,
+                                    int N, int M, int mode, const float* frame_w,
+                                    float* loss_total, float* loss_frames, float* grad_verts,
+                                    int32_t* nn_ab, int32_t* nn_ba, int32_t* status,
+                                    dc_stream_t stream) {
+    int rc = check_common(T, N, M, mode);
+    if (rc) return rc;
+    if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
+    rc = check_ptrs({verts, faces, draws, targets, loss_frames}, "dc_loss_traj_noalloc");
+    if (rc) return rc;
+    const size_t need = dc_workspace_size(T, V, F, N, M);
+    if (need == 0) return fail(DC_EINVAL, "problem too large for 32-bit offsets");
+    if (need > DC_NOALLOC_SCRATCH_BYTES)
+        return fail(DC_ENOSPC,
+                    "dc_loss_traj_noalloc: this problem needs %zu bytes of scratch; the built-in "
+                    "scratch holds %u bytes (use dc_loss_traj with a workspace)",
+                    need, DC_NOALLOC_SCRATCH_BYTES);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(DC_EINVAL, "device index %d out of range", dev);
+    void* ws = nullptr;
+    {
+        // first call on this device (with it current): look up the array's device address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+            g_noalloc_ptr[dev] = p;
+        }
+        ws = g_noalloc_ptr[dev];
+    }
+    // Every region of the scratch that a call reads is written earlier in the same call (the
+    // status word included), so nothing needs clearing between calls.
+    rc = dc_loss_traj(verts, faces, draws, targets, T, V, F, N, M, mode, frame_w, loss_total,
+                      loss_frames, grad_verts, nn_ab, nn_ba, ws, DC_NOALLOC_SCRATCH_BYTES, stream);
+    if (rc) return rc;
+    if (status) {
+        e = cudaMemcpyAsync(status, &static_cast<const WsHeader*>(ws)->status, sizeof(int32_t),
+                            cudaMemcpyDeviceToDevice, stream);
+        if (e) return cuda_fail(e, "status copy");
+    }
+    return DC_OK;
+}
