@@ -56,6 +56,7 @@ Layout make_layout(const Sizes& s) {
     L.x = take(s.rows * 16);
     L.fw = take(s.rows * 16);
     L.tsoa = take(6 * s.cols * 4);
+    L.tpl = take(3 * s.cols * 4);
     L.pab = take(s.rows * 8);
     L.pba = take(s.cols * 8);
     L.nnab = take(s.rows * 4);
@@ -81,6 +82,7 @@ Ws make_ws(void* base, const Layout& L) {
     w.x = reinterpret_cast<float4*>(p + L.x);
     w.fw = reinterpret_cast<int4*>(p + L.fw);
     w.tsoa = reinterpret_cast<float*>(p + L.tsoa);
+    w.tpl = reinterpret_cast<float*>(p + L.tpl);
     w.pab = reinterpret_cast<unsigned long long*>(p + L.pab);
     w.pba = reinterpret_cast<unsigned long long*>(p + L.pba);
     w.nnab = reinterpret_cast<int*>(p + L.nnab);
@@ -161,8 +163,9 @@ int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total
     const int T = a.T, rows = (int)sz.rows, cols = (int)sz.cols;
     cudaError_t e = launch_build_uniform(a, w, st);
     if (!e && (phases & PH_AREA)) e = launch_area_cdf(w, T, st);
-    if (!e && (phases & PH_SAMPLE)) e = launch_sample(w, T, rows, st);
-    if (!e && (phases & PH_TARGETS) && cols > 0) e = launch_targets(w, T, cols, st);
+    if (!e && (phases & (PH_SAMPLE | PH_TARGETS)))
+        e = launch_stage(w, T, (int)sz.slices, a.pts ? 0 : a.F, (phases & PH_SAMPLE) ? rows : 0,
+                         (phases & PH_TARGETS) ? cols : 0, st);
     if (!e && (phases & PH_CHAMFER))
         e = launch_chamfer(w, (int)sz.n_units, (int)(sz.n_units * spu), a.mode, st);
     if (!e && epi_flags)
@@ -189,7 +192,7 @@ int check_ptrs(std::initializer_list<const void*> ps, const char* what) {
 // ---- batch plans (host copy of what dc_batch_run needs to launch) ----
 struct Plan {
     Sizes sz;
-    int mode, any_grad, max_v, total_sub;
+    int mode, any_grad, max_v, max_f, total_sub;
     size_t bytes;
 };
 std::mutex g_plan_mu;
@@ -441,7 +444,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     int* ufr = reinterpret_cast<int*>(img.data() + L.unit_frame);
     int* urb = reinterpret_cast<int*>(img.data() + L.unit_rb);
     int* upre = reinterpret_cast<int*>(img.data() + L.unit_pre);
-    int row0 = 0, col0 = 0, cdf0 = 0, unit = 0, sub = 0, any_grad = 0, max_v = 0;
+    int row0 = 0, col0 = 0, cdf0 = 0, unit = 0, sub = 0, any_grad = 0, max_v = 0, max_f = 0;
     for (int k = 0; k < n_frames; ++k) {
         const dc_frame& f = frames[k];
         FrameDesc d{};
@@ -475,6 +478,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
             upre[unit] = sub;
             sub += spu;
         }
+        if (f.F > max_f) max_f = f.F;
         if (f.grad_verts) {
             any_grad = 1;
             if (f.V > max_v) max_v = f.V;
@@ -506,6 +510,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     p.mode = mode;
     p.any_grad = any_grad;
     p.max_v = max_v;
+    p.max_f = max_f;
     p.total_sub = sub;
     p.bytes = L.total;
     std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -526,8 +531,7 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
     const int n = (int)p.sz.n_frames, rows = (int)p.sz.rows, cols = (int)p.sz.cols;
     cudaError_t e = launch_reset(w, stream);
     if (!e) e = launch_area_cdf(w, n, stream);
-    if (!e) e = launch_sample(w, n, rows, stream);
-    if (!e) e = launch_targets(w, n, cols, stream);
+    if (!e) e = launch_stage(w, n, (int)p.sz.slices, p.max_f, rows, cols, stream);
     if (!e) e = launch_chamfer(w, (int)p.sz.n_units, p.total_sub, p.mode, stream);
     if (!e)
         e = launch_epilogue(w, n, (int)p.sz.slices, p.any_grad ? p.max_v : 0, p.mode,

@@ -30,13 +30,14 @@ constexpr int WARPS = DC_WARPS;
 constexpr int THREADS = 32 * WARPS;
 constexpr int ROWS_PER_WARP = 32 * ROWS_PER_THREAD;       // 512
 constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * WARPS;      // 2048
-constexpr int SUB = 64;                                   // targets per tracked sub-chunk
+constexpr int SUB = 32;                                   // targets per tracked sub-chunk
 constexpr int CHUNK = 256;                                // targets per staged chunk
 constexpr int SUBS_PER_CHUNK = CHUNK / SUB;
 constexpr int ROW_PAD = ROWS_PER_WARP;                    // sim points padded to this
 constexpr int COL_PAD = CHUNK;                            // target points padded to this
-constexpr int EPI_CTAS = 304;                             // epilogue CTAs to aim for
-constexpr int MAX_SLICES = 8;                             // epilogue slices per frame
+constexpr int EPI_THREADS = 256;                          // epilogue CTA size
+constexpr int EPI_CTAS = 608;                             // epilogue CTAs resident at once
+constexpr int MAX_SLICES = 16;                            // epilogue slices per frame
 
 constexpr float COORD_MAX = 1e15f;
 constexpr unsigned long long EMPTY = ~0ull;
@@ -85,8 +86,8 @@ struct WsHeader {
 
 // Byte offsets of every region of a workspace (computed on the host).
 struct Layout {
-    size_t hdr, frames, rowpre, colpre, unit_frame, unit_rb, unit_pre, cdf, x, fw, tsoa, pab,
-        pba, nnab, nnba, loss, part, gscr, total;
+    size_t hdr, frames, rowpre, colpre, unit_frame, unit_rb, unit_pre, cdf, x, fw, tsoa, tpl,
+        pab, pba, nnab, nnba, loss, part, gscr, total;
 };
 
 struct Sizes {
@@ -95,9 +96,10 @@ struct Sizes {
     long long gscr;    // floats of per-slice gradient partials (0 when slices == 1)
 };
 
-// Epilogue slices per frame: enough CTAs to cover the GPU, at most MAX_SLICES.
+// Epilogue slices per frame: as many as keep all (frame, slice) CTAs in one wave, at most
+// MAX_SLICES.
 inline int epilogue_slices(long long n_frames) {
-    long long s = (EPI_CTAS + n_frames - 1) / n_frames;
+    long long s = EPI_CTAS / n_frames;
     return (int)(s < 1 ? 1 : (s > MAX_SLICES ? MAX_SLICES : s));
 }
 
@@ -116,6 +118,7 @@ struct Ws {
     float4* x;         // [rows] sampled points (w lane unused), NaN beyond N
     int4* fw;          // [rows] (face, w0, w1, w2 bits)
     float* tsoa;       // [6 * cols] per frame: X2[2 Mpad], Y2, Z2 = {-v, -v} pairs, sentinel beyond M
+    float* tpl;        // [3 * cols] per frame: X[Mpad], Y, Z (the targets as given), 0 beyond M
     unsigned long long* pab;  // [rows] packed (d bits << 32 | sub-chunk)
     unsigned long long* pba;  // [cols] packed (d bits << 32 | row group)
     int* nnab;         // [rows] fallback neighbour buffers
@@ -156,6 +159,10 @@ cudaError_t launch_reset(const Ws& w, cudaStream_t s);
 cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s);
 cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s);
 cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s);
+// sampling + target staging in one (frame, slice) launch when the largest CDF (max_f
+// floats) fits in shared memory, else launch_sample + launch_targets
+cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
+                         cudaStream_t s);
 cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, cudaStream_t s);
 // epilogue: neighbour recovery (rescan), loss partials, gradient scatter
 enum : int { EPI_RESCAN = 1, EPI_LOSS = 2, EPI_GRAD = 4 };

@@ -4,7 +4,7 @@
 //
 // One CTA per (frame, slice): the frame's sim points and target points are cut into
 // `slices` equal ranges so that the whole GPU works even on few frames. Each CTA
-//   - re-scans the sub-chunk (rows) or 16-row group (targets) that the packed minimum
+//   - re-scans the sub-chunk (rows) or the thread's row group (targets) that the packed minimum
 //     points at, with the same float32 operations as the Chamfer kernel, to find the first
 //     index attaining it (ties go to the lowest index);
 //   - sums its minimum distances (fixed order) into a per-slice partial;
@@ -49,8 +49,6 @@ __device__ __forceinline__ void scatter(float* __restrict__ G, const int* __rest
         atomicAdd(&G[3 * v + 2], __fmul_rn(wc[c], gz));
     }
 }
-
-constexpr int EPI_THREADS = 512;
 
 struct EpiArgs {
     int slices;
@@ -102,78 +100,53 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
     const float cab = e.bidir ? __fdiv_rn(__fmul_rn(2.0f, gs), (float)N) : __fmul_rn(2.0f, gs);
     const float cba = __fdiv_rn(__fmul_rn(2.0f, gs), (float)M);
 
-    // ---- sim points of this slice, 32 per warp step ----
-    // Each row's minimum points at one sub-chunk of SUB targets; the warp re-scans the rows
-    // of its step one after another, each lane checking two candidates (coalesced loads), so
-    // that one L2 round trip serves a whole sub-chunk.
-    const int lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = EPI_THREADS / 32;
+    // ---- sim points of this slice ----
+    // Each row's minimum points at one sub-chunk of SUB targets; the thread re-scans that
+    // window from the compact target planes, eight candidates per round of loads.
     const int i0 = (int)((long long)N * sl / e.slices);
     const int i1 = (int)((long long)N * (sl + 1) / e.slices);
+    const float* PX = w.tpl + 3LL * col0;
+    const float* PY = PX + fr->Mpad;
+    const float* PZ = PY + fr->Mpad;
     float sab = 0.f, cab_c = 0.f;
-    for (int base = i0 + warp * 32; base < i1; base += NW * 32) {
-        const int i = base + lane;
-        const bool valid = i < i1;
+    for (int i = i0 + tid; i < i1; i += EPI_THREADS) {
         const int g = row0 + i;
-        u64 p = EMPTY;
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        int4 q = make_int4(-1, 0, 0, 0);
-        if (valid) {
-            x = w.x[g];
-            if (grad) q = w.fw[g];
-            if (rescan) p = w.pab[g];
-        }
+        const float4 x = w.x[g];
         int nn = -1;
         float y0 = 0.f, y1 = 0.f, y2 = 0.f;
         if (rescan) {
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r) {
-                const u64 pr = __shfl_sync(0xffffffffu, p, r);
-                if (pr == EMPTY) continue;  // the same for every lane
-                const float qx = __shfl_sync(0xffffffffu, x.x, r);
-                const float qy = __shfl_sync(0xffffffffu, x.y, r);
-                const float qz = __shfl_sync(0xffffffffu, x.z, r);
-                const unsigned dq = (unsigned)(pr >> 32);
-                const int jb = (int)(pr & 0xffffffffu) * SUB;
-                const int ja = jb + lane, jc = ja + 32;
-                float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-                bool ma = false, mc = false;
-                if (ja < M) {
-                    const float* y = tgt + 3LL * ja;
-                    ax = y[0];
-                    ay = y[1];
-                    az = y[2];
-                    ma = __float_as_uint(dist2(qx, qy, qz, ax, ay, az)) == dq;
+            const u64 p = w.pab[g];
+            if (p != EMPTY) {
+                const unsigned dq = (unsigned)(p >> 32);
+                const int jb = (int)(p & 0xffffffffu) * SUB, je = min(jb + SUB, M);
+                for (int h = 0; h < SUB && nn < 0; h += 8) {
+                    // the window is 16-byte aligned: col0 and jb are multiples of 8 floats
+                    const float4 xa = *reinterpret_cast<const float4*>(PX + jb + h);
+                    const float4 xb = *reinterpret_cast<const float4*>(PX + jb + h + 4);
+                    const float4 ya = *reinterpret_cast<const float4*>(PY + jb + h);
+                    const float4 yb = *reinterpret_cast<const float4*>(PY + jb + h + 4);
+                    const float4 za = *reinterpret_cast<const float4*>(PZ + jb + h);
+                    const float4 zb = *reinterpret_cast<const float4*>(PZ + jb + h + 4);
+                    const float cx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                    const float cy[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                    const float cz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int j = jb + h + t;
+                        if (nn < 0 && j < je &&
+                            __float_as_uint(dist2(x.x, x.y, x.z, cx[t], cy[t], cz[t])) == dq) {
+                            nn = j;
+                            y0 = cx[t];
+                            y1 = cy[t];
+                            y2 = cz[t];
+                        }
+                    }
                 }
-                if (jc < M) {
-                    const float* y = tgt + 3LL * jc;
-                    cx = y[0];
-                    cy = y[1];
-                    cz = y[2];
-                    mc = __float_as_uint(dist2(qx, qy, qz, cx, cy, cz)) == dq;
-                }
-                const unsigned ba = __ballot_sync(0xffffffffu, ma);
-                const unsigned bc = __ballot_sync(0xffffffffu, mc);
-                // first candidate in target order: the lower half before the upper half
-                const int src = ba ? __ffs(ba) - 1 : (bc ? 31 + __ffs(bc) : -1);
-                const bool lo = src < 32;
-                const int from = src & 31;
-                const float mx = __shfl_sync(0xffffffffu, lo ? ax : cx, from);
-                const float my = __shfl_sync(0xffffffffu, lo ? ay : cy, from);
-                const float mz = __shfl_sync(0xffffffffu, lo ? az : cz, from);
-                if (lane == r) {
-                    nn = src < 0 ? -1 : jb + src;
-                    y0 = mx;
-                    y1 = my;
-                    y2 = mz;
-                }
+                if (want_loss) kahan_add(sab, cab_c, __uint_as_float(dq));
             }
-            if (valid) {
-                if (p != EMPTY && want_loss) kahan_add(sab, cab_c, __uint_as_float((unsigned)(p >> 32)));
-                if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
-                fr->nn_ab[i] = nn;
-            }
-        } else if (valid) {
+            if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
+            fr->nn_ab[i] = nn;
+        } else {
             nn = fr->nn_ab[i];
             if ((unsigned)nn < (unsigned)M) {
                 const float* y = tgt + 3LL * nn;
@@ -185,8 +158,8 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
                 nn = -1;
             }
         }
-        if (grad && valid && nn >= 0)
-            scatter(G, faces, V, q, __fmul_rn(cab, __fsub_rn(x.x, y0)),
+        if (grad && nn >= 0)
+            scatter(G, faces, V, w.fw[g], __fmul_rn(cab, __fsub_rn(x.x, y0)),
                     __fmul_rn(cab, __fsub_rn(x.y, y1)), __fmul_rn(cab, __fsub_rn(x.z, y2)));
     }
 

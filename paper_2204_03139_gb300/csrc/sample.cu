@@ -206,102 +206,140 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
 // ---------------------------------------------------------------------------------------
 // sampling: face pick by inverse CDF (Sec. III-B) and barycentric point (Eq. 3)
 // ---------------------------------------------------------------------------------------
+// Row g (frame-local index i) of frame fr, with the frame's CDF at `cdf` (global or shared).
+__device__ __forceinline__ void sample_row(const Ws& w, const FrameDesc* fr, int i, int g,
+                                           const float* cdf) {
+    float4 x = make_float4(ROW_SENTINEL, ROW_SENTINEL, ROW_SENTINEL, 0.0f);
+    int4 q = make_int4(-1, 0, 0, 0);
+    if (i < fr->N) {
+        if (fr->pts) {
+            const float* p = fr->pts + 3LL * i;
+            x = make_float4(p[0], p[1], p[2], 0.0f);
+            if (!coord_ok(x.x) || !coord_ok(x.y) || !coord_ok(x.z))
+                set_status(&w.hdr->status, DC_EINVAL);
+        } else {
+            const float* r = fr->draws + 3LL * i;
+            const float rf = r[0], r1 = r[1], r2 = r[2];
+            if (!(rf >= 0.0f && rf <= 1.0f && r1 >= 0.0f && r1 <= 1.0f && r2 >= 0.0f &&
+                  r2 <= 1.0f))
+                set_status(&w.hdr->status, DC_EINVAL);
+            const int F = fr->F;
+            const float t = __fmul_rn(rf, cdf[F - 1]);
+            int lo = 0, hi = F;  // first f with cdf[f] > t
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (cdf[mid] > t)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            const int f = min(lo, F - 1);
+            const int i0 = fr->faces[3 * f], i1 = fr->faces[3 * f + 1], i2 = fr->faces[3 * f + 2];
+            const int V = fr->V;
+            if ((unsigned)i0 < (unsigned)V && (unsigned)i1 < (unsigned)V &&
+                (unsigned)i2 < (unsigned)V) {
+                const float* p0 = fr->verts + 3LL * i0;
+                const float* p1 = fr->verts + 3LL * i1;
+                const float* p2 = fr->verts + 3LL * i2;
+                const float s = __fsqrt_rn(r1);
+                const float w0 = __fsub_rn(1.0f, s);
+                const float w1 = __fmul_rn(s, __fsub_rn(1.0f, r2));
+                const float w2 = __fmul_rn(s, r2);
+                x.x = __fmaf_rn(w2, p2[0], __fmaf_rn(w1, p1[0], __fmul_rn(w0, p0[0])));
+                x.y = __fmaf_rn(w2, p2[1], __fmaf_rn(w1, p1[1], __fmul_rn(w0, p0[1])));
+                x.z = __fmaf_rn(w2, p2[2], __fmaf_rn(w1, p1[2], __fmul_rn(w0, p0[2])));
+                q = make_int4(f, __float_as_int(w0), __float_as_int(w1), __float_as_int(w2));
+                if (fr->out_face) fr->out_face[i] = f;
+                if (fr->out_bary) {
+                    fr->out_bary[3LL * i] = w0;
+                    fr->out_bary[3LL * i + 1] = w1;
+                    fr->out_bary[3LL * i + 2] = w2;
+                }
+            } else {
+                set_status(&w.hdr->status, DC_EINVAL);
+                x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            if (fr->out_pts) {
+                fr->out_pts[3LL * i] = x.x;
+                fr->out_pts[3LL * i + 1] = x.y;
+                fr->out_pts[3LL * i + 2] = x.z;
+            }
+        }
+    }
+    w.x[g] = x;
+    w.fw[g] = q;
+    w.pab[g] = EMPTY;
+}
+
+// Target j (frame-local) of frame fr at padded column g: the negated duplicated planes the
+// Chamfer kernel stages, the compact planes the epilogue re-scans, and the column minimum.
+__device__ __forceinline__ void stage_target(const Ws& w, const FrameDesc* fr, int j, int g) {
+    float vx = COL_SENTINEL, vy = COL_SENTINEL, vz = COL_SENTINEL;
+    const bool real = j < fr->M;
+    if (real) {
+        const float* p = fr->tgt + 3LL * j;
+        vx = p[0];
+        vy = p[1];
+        vz = p[2];
+        if (!coord_ok(vx) || !coord_ok(vy) || !coord_ok(vz)) set_status(&w.hdr->status, DC_EINVAL);
+    }
+    // planes of negated {-v, -v} pairs: X2 [2 Mpad], Y2 [2 Mpad], Z2 [2 Mpad]; the Chamfer
+    // kernel forms x - v as x + (-v), which rounds identically
+    float2* P = reinterpret_cast<float2*>(w.tsoa + 6LL * fr->col0);
+    P[j] = make_float2(-vx, -vx);
+    P[fr->Mpad + j] = make_float2(-vy, -vy);
+    P[2 * fr->Mpad + j] = make_float2(-vz, -vz);
+    // compact planes as given (0 beyond M) for the epilogue's re-scans
+    float* Q = w.tpl + 3LL * fr->col0;
+    Q[j] = real ? vx : 0.0f;
+    Q[fr->Mpad + j] = real ? vy : 0.0f;
+    Q[2 * fr->Mpad + j] = real ? vz : 0.0f;
+    w.pba[g] = EMPTY;
+}
+
 __global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.rowpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
-        const int i = g - fr->row0;
-        float4 x = make_float4(ROW_SENTINEL, ROW_SENTINEL, ROW_SENTINEL, 0.0f);
-        int4 q = make_int4(-1, 0, 0, 0);
-        if (i < fr->N) {
-            if (fr->pts) {
-                const float* p = fr->pts + 3LL * i;
-                x = make_float4(p[0], p[1], p[2], 0.0f);
-                if (!coord_ok(x.x) || !coord_ok(x.y) || !coord_ok(x.z))
-                    set_status(&w.hdr->status, DC_EINVAL);
-            } else {
-                const float* r = fr->draws + 3LL * i;
-                const float rf = r[0], r1 = r[1], r2 = r[2];
-                if (!(rf >= 0.0f && rf <= 1.0f && r1 >= 0.0f && r1 <= 1.0f && r2 >= 0.0f &&
-                      r2 <= 1.0f))
-                    set_status(&w.hdr->status, DC_EINVAL);
-                const float* cdf = w.cdf + fr->cdf0;
-                const int F = fr->F;
-                const float t = __fmul_rn(rf, cdf[F - 1]);
-                int lo = 0, hi = F;  // first f with cdf[f] > t
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cdf[mid] > t)
-                        hi = mid;
-                    else
-                        lo = mid + 1;
-                }
-                const int f = min(lo, F - 1);
-                const int i0 = fr->faces[3 * f], i1 = fr->faces[3 * f + 1],
-                          i2 = fr->faces[3 * f + 2];
-                const int V = fr->V;
-                if ((unsigned)i0 < (unsigned)V && (unsigned)i1 < (unsigned)V &&
-                    (unsigned)i2 < (unsigned)V) {
-                    const float* p0 = fr->verts + 3LL * i0;
-                    const float* p1 = fr->verts + 3LL * i1;
-                    const float* p2 = fr->verts + 3LL * i2;
-                    const float s = __fsqrt_rn(r1);
-                    const float w0 = __fsub_rn(1.0f, s);
-                    const float w1 = __fmul_rn(s, __fsub_rn(1.0f, r2));
-                    const float w2 = __fmul_rn(s, r2);
-                    x.x = __fmaf_rn(w2, p2[0], __fmaf_rn(w1, p1[0], __fmul_rn(w0, p0[0])));
-                    x.y = __fmaf_rn(w2, p2[1], __fmaf_rn(w1, p1[1], __fmul_rn(w0, p0[1])));
-                    x.z = __fmaf_rn(w2, p2[2], __fmaf_rn(w1, p1[2], __fmul_rn(w0, p0[2])));
-                    q = make_int4(f, __float_as_int(w0), __float_as_int(w1), __float_as_int(w2));
-                    if (fr->out_face) fr->out_face[i] = f;
-                    if (fr->out_bary) {
-                        fr->out_bary[3LL * i] = w0;
-                        fr->out_bary[3LL * i + 1] = w1;
-                        fr->out_bary[3LL * i + 2] = w2;
-                    }
-                } else {
-                    set_status(&w.hdr->status, DC_EINVAL);
-                    x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                }
-                if (fr->out_pts) {
-                    fr->out_pts[3LL * i] = x.x;
-                    fr->out_pts[3LL * i + 1] = x.y;
-                    fr->out_pts[3LL * i + 2] = x.z;
-                }
-            }
-        }
-        w.x[g] = x;
-        w.fw[g] = q;
-        w.pab[g] = EMPTY;
+        sample_row(w, fr, g - fr->row0, g, w.cdf + fr->cdf0);
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// targets: [M][3] -> X/Y/Z planes padded to Mpad (sentinel beyond M); reset column minima
-// ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < cols; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.colpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
-        const int j = g - fr->col0;
-        float vx = COL_SENTINEL, vy = COL_SENTINEL, vz = COL_SENTINEL;
-        if (j < fr->M) {
-            const float* p = fr->tgt + 3LL * j;
-            vx = p[0];
-            vy = p[1];
-            vz = p[2];
-            if (!coord_ok(vx) || !coord_ok(vy) || !coord_ok(vz))
-                set_status(&w.hdr->status, DC_EINVAL);
-        }
-        // planes of negated {-v, -v} pairs: X2 [2 Mpad], Y2 [2 Mpad], Z2 [2 Mpad]; the Chamfer
-        // kernel forms x - v as x + (-v), which rounds identically
-        float2* P = reinterpret_cast<float2*>(w.tsoa + 6LL * fr->col0);
-        P[j] = make_float2(-vx, -vx);
-        P[fr->Mpad + j] = make_float2(-vy, -vy);
-        P[2 * fr->Mpad + j] = make_float2(-vz, -vz);
-        w.pba[g] = EMPTY;
+        stage_target(w, fr, g - fr->col0, g);
     }
 }
+
+// Sampling and target staging in one launch: one CTA per (frame, slice), the frame's CDF
+// copied to shared memory so that the binary searches stay on chip.
+constexpr int STAGE_THREADS = 256;
+
+__global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int rows, int cols) {
+    extern __shared__ float s_cdf[];
+    const int k = blockIdx.x / slices, sl = blockIdx.x - k * slices;
+    const FrameDesc* fr = w.frames + k;
+    const bool sampled = fr->verts && !fr->pts;
+    if (sampled)
+        for (int f = threadIdx.x; f < fr->F; f += STAGE_THREADS) s_cdf[f] = w.cdf[fr->cdf0 + f];
+    __syncthreads();
+    if (rows) {
+        const int a = (int)((long long)fr->Npad * sl / slices);
+        const int b = (int)((long long)fr->Npad * (sl + 1) / slices);
+        for (int i = a + threadIdx.x; i < b; i += STAGE_THREADS)
+            sample_row(w, fr, i, fr->row0 + i, s_cdf);
+    }
+    if (cols) {
+        const int a = (int)((long long)fr->Mpad * sl / slices);
+        const int b = (int)((long long)fr->Mpad * (sl + 1) / slices);
+        for (int j = a + threadIdx.x; j < b; j += STAGE_THREADS)
+            stage_target(w, fr, j, fr->col0 + j);
+    }
+}
+
+int g_stage_smem[64];
 
 int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
@@ -336,6 +374,33 @@ cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s) {
 
 cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s) {
     k_targets<<<grid_for(cols, 256), 256, 0, s>>>(w, n_frames, cols);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
+                         cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (g_stage_smem[dev] == 0) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (optin <= 0) optin = 48 * 1024;
+        cudaError_t e = cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             optin);
+        if (e != cudaSuccess) return e;
+        g_stage_smem[dev] = optin;
+    }
+    const size_t need = (size_t)max_f * sizeof(float);
+    if (need > (size_t)g_stage_smem[dev]) {
+        // the CDF does not fit on chip: one kernel per step, searching the CDF in global memory
+        cudaError_t e = cudaSuccess;
+        if (rows) e = launch_sample(w, n_frames, rows, s);
+        if (!e && cols) e = launch_targets(w, n_frames, cols, s);
+        return e;
+    }
+    k_stage<<<n_frames * slices, STAGE_THREADS, need, s>>>(w, slices, rows > 0, cols > 0);
     count_launch();
     return cudaGetLastError();
 }
