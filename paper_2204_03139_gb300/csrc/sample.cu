@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
 
 // Sampling and target staging in one launch: one CTA per (frame, slice), the frame's CDF
 // copied to shared memory so that the binary searches stay on chip.
-constexpr int STAGE_THREADS = 256;
+constexpr int STAGE_THREADS = 512;
 
 __global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int rows, int cols) {
     extern __shared__ float s_cdf[];
