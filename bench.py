@@ -41,20 +41,26 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--workload", default="trajectory_50x50")
+    p.add_argument("--workload", default="trajectory_50x50",
+                   choices=["trajectory_50x50", "trajectory_100x100", "single_frame",
+                            "batched_uneven", "serving"])
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--frames", type=int, default=None,
+                   help="use only the first FRAMES frames of the trajectory (profiling runs)")
     return p.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, frames=None):
     if name == "trajectory_50x50":
-        return workloads.trajectory_50x50()
+        return workloads.trajectory_50x50(T=frames or 40)
     if name == "trajectory_100x100":
-        return workloads.trajectory_100x100()
+        return workloads.trajectory_100x100(T=frames or 100)
     if name == "single_frame":
         return workloads.single_frame()
+    if name == "batched_uneven":
+        return workloads.batched_uneven()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -197,7 +203,7 @@ def run_gpu(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    tr = make_workload(args.workload)
+    tr = make_workload(args.workload, args.frames)
     pairs = tr.pairs()
     T, V, F, N, M = tr.T, tr.V, tr.F, tr.n(0), tr.m(0)
 
@@ -329,6 +335,185 @@ def run_gpu(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, rank, world, dist):
+    """64 trajectories of uneven sizes: the batched form (one planned launch sequence replayed
+    from a CUDA graph) against the plain per-frame form (one dc_loss_traj call per frame)."""
+    import torch
+
+    from paper_2204_03139_gb300 import _lib
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory, per_frame_loss
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    trajs = workloads.batched_uneven()
+    pairs = sum(t.pairs() for t in trajs)
+    frames = sum(t.T for t in trajs)
+    dts = [DeviceTrajectory.from_host(t, dev) for t in trajs]
+    b = BatchedLoss(dts, grad=True, graph=True)
+    b.run(check=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local)
+    for _ in range(max(3, args.warmup)):
+        b.run()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    stream = torch.cuda.current_stream(dev)
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        b.run()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    # graph replays launch nothing from the host: count and time the Chamfer kernel on the
+    # same launch sequence issued eagerly
+    launches0 = _lib.launch_count()
+    _lib.prof_start(3)
+    for _ in range(3):
+        b._launch()
+    torch.cuda.synchronize()
+    chamfer_ms, chamfer_n = _lib.prof_stop()
+    launches = (_lib.launch_count() - launches0) // 3 * steps
+    per = [a.elapsed_time(c) for a, c in ev]
+    ms = statistics.mean(per)
+    # the plain per-frame form on the same inputs
+    per_frame_loss(dts)
+    torch.cuda.synchronize()
+    pf_steps = 2
+    t0 = time.perf_counter()
+    for _ in range(pf_steps):
+        per_frame_loss(dts)
+    torch.cuda.synchronize()
+    pf_ms = 1e3 * (time.perf_counter() - t0) / pf_steps
+    # end to end: the batch's inputs from pinned host memory each step, gradients back
+    host = [(torch.from_numpy(t.verts).pin_memory(), torch.from_numpy(t.draws).pin_memory(),
+             torch.from_numpy(t.targets).pin_memory()) for t in trajs]
+    hg = [torch.empty(tuple(d.verts.shape), dtype=torch.float32).pin_memory() for d in dts]
+    h2d = sum(v.numel() * 4 + d.numel() * 4 + y.numel() * 4 for v, d, y in host)
+    d2h = sum(g.numel() * 4 for g in hg) + 4
+    e2e = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for (hv, hd, hy), d in zip(host, dts):
+            d.verts.copy_(hv, non_blocking=True)
+            d.draws.copy_(hd, non_blocking=True)
+            d.targets.copy_(hy, non_blocking=True)
+        tot = b.run()
+        for g, gv in zip(hg, b.grad_verts):
+            g.copy_(gv, non_blocking=True)
+        float(tot[0])
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t1)
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clk.get("sm_mhz") or 0.0
+    peak = 2 * FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6 / 1e12 if sm_mhz else None
+    ck = chamfer_ms / max(1, chamfer_n) / 1e3
+    ach = FLOP_PER_PAIR * pairs / ck / 1e12 if chamfer_n else None
+    line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s", "value": world * pairs / (ms / 1e3),
+            "unit": "pairs/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_uneven_64traj", "trajectories": len(trajs),
+                       "frames": frames, "pairs_per_step": pairs,
+                       "form": "one planned launch sequence replayed from a CUDA graph",
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)"},
+            "comparison": {"plain_per_frame_ms_per_step": pf_ms,
+                           "plain_per_frame_pairs_per_s": pairs / (pf_ms / 1e3),
+                           "batched_over_plain": pf_ms / ms},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak if (ach and peak) else None, "traffic": None,
+                         "kernel": "k_chamfer<true>", "kernel_ms": ck * 1e3},
+            "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": world * pairs / statistics.mean(e2e), "unit": "pairs/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args, rank, world, dist):
+    """Poisson stream of loss+gradient requests: 90% at the 50x50 / 10 000-point size, 10% at
+    the 100x100 / 32 768-point size, served with continuous batching under a 120 GB budget.
+    Each rate runs a fixed arrival window; latencies include queueing."""
+    import threading
+
+    import torch
+
+    from paper_2204_03139_gb300.serve import Server, serve_plain
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    small = [workloads.lift_trajectory(workloads.SEED_BASE + 50 + k, 50, 40, 10_000, 10_000,
+                                       name=f"small{k}") for k in range(4)]
+    big = [workloads.trajectory_100x100(seed=workloads.SEED_BASE + 60)]
+    window = float(os.environ.get("DC_SERVE_WINDOW_S", "1.0"))
+
+    def arrivals(rate, seed):
+        rng = workloads.rng_for(seed)
+        t, out = 0.0, []
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t > window:
+                return out
+            is_big = rng.random() < 0.1
+            pool = big if is_big else small
+            out.append((t, pool[int(rng.integers(len(pool)))]))
+
+    def run_rate(rate, seed):
+        reqs = arrivals(rate, seed)
+        srv = Server(dev, hbm_budget=120 << 30)
+        futs = []
+        t0 = time.perf_counter()
+        for at, tr in reqs:
+            now = time.perf_counter() - t0
+            if now < at:
+                time.sleep(at - now)
+            futs.append(srv.submit(tr))
+        res = [f.result(timeout=600) for f in futs]
+        t_end = time.perf_counter() - t0
+        srv.close()
+        lat = np.array([r.latency_s for r in res])
+        pairs = sum(tr.pairs() for _, tr in reqs)
+        return {"rate_hz": rate, "requests": len(reqs), "window_s": window,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "throughput_pairs_per_s": pairs / t_end,
+                "mean_batch_requests": float(np.mean([r.batch_requests for r in res]))}
+
+    # warm-up: build pinned copies, first launches
+    w = Server(dev, hbm_budget=120 << 30)
+    for tr in small + big:
+        w.submit(tr).result(timeout=600)
+    w.close()
+    rates = [500, 300, 200, 100]
+    results = [run_rate(r, 1000 + r) for r in rates]
+    plain_rate = 100
+    preqs = arrivals(plain_rate, 1000 + plain_rate)
+    serve_plain(preqs[:3], dev)  # warm-up
+    plat = np.array(serve_plain(preqs, dev))
+    if rank != 0:
+        return
+    head = results[0]
+    line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s",
+            "value": head["throughput_pairs_per_s"], "unit": "pairs/s", "n_gpus": world,
+            "steps": head["requests"], "warmup": len(small) + len(big),
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_poisson", "mix": "90% 50x50 T40 10k x 10k, "
+                       "10% 100x100 T100 32768 x 32768", "hbm_budget_gb": 120,
+                       "latency": "from arrival to the result on the host, queueing included"},
+            "serving": results,
+            "plain_per_request": {"rate_hz": plain_rate, "requests": len(preqs),
+                                  "p50_ms": float(np.percentile(plat, 50) * 1e3),
+                                  "p99_ms": float(np.percentile(plat, 99) * 1e3)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -342,6 +527,10 @@ def main():
     if args.impl == "reference":
         # the oracle pool runs before any GPU work (forking after CUDA init is unsafe)
         run_reference(args, rank, world)
+    elif args.workload == "batched_uneven":
+        run_batched(args, rank, world, dist)
+    elif args.workload == "serving":
+        run_serving(args, rank, world, dist)
     else:
         run_gpu(args, rank, world, dist)
     if dist is not None:

@@ -56,11 +56,22 @@ class BatchedLoss:
     """
 
     def __init__(self, trajs, mode=_lib.BIDIR_MEAN, weights=None, grad=True, graph=False,
-                 nn=False):
+                 nn=False, stream=None):
         self.trajs = list(trajs)
         self.mode = mode
         dev = self.trajs[0].verts.device
         self.device = dev
+        # the stream the plan is uploaded on and the batch runs on (default: current stream)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        # outputs and workspace belong to the batch's stream (the caching allocator reuses
+        # memory per stream)
+        with torch.cuda.stream(self.stream):
+            self._build(mode, weights, grad, nn)
+        if graph:
+            self._capture()
+
+    def _build(self, mode, weights, grad, nn):
+        dev = self.device
         nfr = sum(t.T for t in self.trajs)
         self.frames = (_lib.dc_frame * nfr)()
         self.loss_frames, self.grad_verts, self.nn_ab, self.nn_ba = [], [], [], []
@@ -99,34 +110,39 @@ class BatchedLoss:
             raise _lib.DCError(_lib.DC_EINVAL, "bad batch sizes")
         self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
         self.total = torch.empty(1, dtype=torch.float32, device=dev)
+        self.workspace_bytes = nb
         self.n_frames = nfr
         _lib._check(L.dc_batch_plan(self.frames, nfr, mode, ctypes.c_void_p(self.ws.data_ptr()),
-                                    nb, _lib._stream(dev)))
+                                    nb, ctypes.c_void_p(self.stream.cuda_stream)))
         self.graph = None
-        if graph:
-            self._capture()
 
     def _launch(self):
         _lib._check(_lib.lib().dc_batch_run(ctypes.c_void_p(self.ws.data_ptr()),
                                             ctypes.c_void_p(self.total.data_ptr()),
-                                            _lib._stream(self.device)))
+                                            ctypes.c_void_p(self.stream.cuda_stream)))
 
     def _capture(self):
         # one eager run first: per-device one-time set-up happens outside the capture
         self._launch()
         torch.cuda.synchronize(self.device)
         s = torch.cuda.Stream(self.device)
-        s.wait_stream(torch.cuda.current_stream(self.device))
+        s.wait_stream(self.stream)
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(g, stream=s):
-                self._launch()
-        torch.cuda.current_stream(self.device).wait_stream(s)
+        launch_stream = self.stream
+        self.stream = s
+        try:
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    self._launch()
+        finally:
+            self.stream = launch_stream
+        self.stream.wait_stream(s)
         self.graph = g
 
     def run(self, check: bool = False) -> torch.Tensor:
         if self.graph is not None:
-            self.graph.replay()
+            with torch.cuda.stream(self.stream):
+                self.graph.replay()
         else:
             self._launch()
         if check:

@@ -1,0 +1,291 @@
+"""Serving loss-and-gradient requests from many concurrent parameter-inference optimisations.
+
+Each request is one trajectory (its own mesh resolution, frame count and cloud sizes) whose
+loss and vertex gradient a caller's optimiser needs (the inner step of Sec. III-C, repeated by
+every optimisation). The server batches continuously:
+
+  - admission: requests wait in arrival order until their device memory (inputs, outputs and
+    their share of a batch workspace) fits in the HBM budget; their inputs are then copied to
+    the device once, on a copy stream, and stay resident until the result is delivered;
+  - batching: whenever one of the compute streams is free, every admitted request of the
+    same mode (up to a size cap) goes into one planned launch sequence (dc_batch_plan /
+    dc_batch_run): one persistent Chamfer launch covers all their frames, whatever their sizes;
+  - overlap: batches on different streams run at the same time while new requests are
+    admitted and copied in; finished batches resolve their requests' futures and release their
+    memory, which admits the next requests.
+
+Every result equals the one the request gets alone (same kernels; only the order of the
+per-slice loss partial sums may differ, within float32 rounding).
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib
+from .batch import BatchedLoss, DeviceTrajectory
+
+
+@dataclass
+class Result:
+    loss_frames: np.ndarray          # [T] L_t
+    loss_total: float                # sum_t w_t L_t
+    grad_verts: np.ndarray | None    # [T, V, 3] gradient of sum_t w_t L_t
+    latency_s: float                 # completion - arrival
+    batch_id: int
+    batch_requests: int
+
+
+@dataclass
+class _Request:
+    rid: int
+    traj: object
+    mode: int
+    weights: np.ndarray | None
+    grad: bool
+    arrival: float
+    nbytes: int
+    future: Future
+    dev: DeviceTrajectory | None = None
+    ready: torch.cuda.Event | None = None
+    host: tuple = field(default_factory=tuple)
+
+
+def _frames_of(traj):
+    """dc_frame array with sizes only (no pointers): enough for dc_batch_workspace_size."""
+    n = np.diff(np.asarray(traj.n_off))
+    m = np.diff(np.asarray(traj.m_off))
+    fr = (_lib.dc_frame * traj.T)()
+    for t in range(traj.T):
+        fr[t].V, fr[t].F, fr[t].N, fr[t].M = traj.V, traj.F, int(n[t]), int(m[t])
+        fr[t].grad_verts = 1  # counted as having a gradient
+    return fr
+
+
+def request_bytes(traj, grad: bool = True) -> int:
+    """Device bytes a request holds while admitted: inputs, outputs, workspace share."""
+    inputs = (traj.verts.nbytes + traj.faces.nbytes + traj.draws.nbytes + traj.targets.nbytes)
+    outputs = 4 * traj.T + (traj.verts.nbytes if grad else 0)
+    ws = int(_lib.lib().dc_batch_workspace_size(_frames_of(traj), traj.T))
+    if ws == 0:
+        raise _lib.DCError(_lib.DC_EINVAL, "request sizes are invalid")
+    return inputs + outputs + ws + 64 * 1024
+
+
+class Server:
+    """Continuous-batching loss+gradient server on one GPU."""
+
+    def __init__(self, device="cuda:0", hbm_budget: int = 120 << 30, streams: int = 2,
+                 max_batch_requests: int = 256, max_batch_pairs: int = 2 * 10**12):
+        self.device = torch.device(device)
+        self.budget = int(hbm_budget)
+        self.max_batch_requests = max_batch_requests
+        self.max_batch_pairs = max_batch_pairs
+        self._copy = torch.cuda.Stream(self.device)
+        self._streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
+        self._busy = [None] * streams
+        self._cv = threading.Condition()
+        self._waiting: collections.deque = collections.deque()
+        self._admitted: list = []
+        self._used = 0
+        self._next_id = 0
+        self._next_batch = 0
+        self._closing = False
+        self.completed: list[tuple[int, float, int, int]] = []  # (rid, latency, pairs, batch)
+        self.batch_sizes: list[int] = []
+        self._thread = threading.Thread(target=self._loop, name="diffcloud-serve", daemon=True)
+        self._thread.start()
+
+    # ---- client side ----
+    def submit(self, traj, mode: int = _lib.BIDIR_MEAN, weights=None, grad: bool = True) -> Future:
+        """Queue one trajectory (workloads.Trajectory or anything with verts, faces, draws,
+        targets, n_off, m_off as numpy arrays). Returns a Future of Result."""
+        fut: Future = Future()
+        try:
+            nbytes = request_bytes(traj, grad)
+        except Exception as e:  # invalid sizes
+            fut.set_exception(e)
+            return fut
+        if nbytes > self.budget:
+            fut.set_exception(_lib.DCError(
+                _lib.DC_ENOSPC, f"request needs {nbytes} bytes, the HBM budget is {self.budget}"))
+            return fut
+        w = None if weights is None else np.asarray(weights, np.float32)
+        with self._cv:
+            if self._closing:
+                fut.set_exception(RuntimeError("server is closed"))
+                return fut
+            r = _Request(self._next_id, traj, mode, w, grad, time.perf_counter(), nbytes, fut)
+            self._next_id += 1
+            self._waiting.append(r)
+            self._cv.notify()
+        return fut
+
+    def close(self, wait: bool = True):
+        with self._cv:
+            self._closing = True
+            self._cv.notify()
+        if wait:
+            self._thread.join()
+
+    def stats(self) -> dict:
+        lat = np.array([c[1] for c in self.completed]) if self.completed else np.zeros(0)
+        return {"requests": len(self.completed),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+                "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+                "mean_batch_requests": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0,
+                "batches": len(self.batch_sizes)}
+
+    # ---- scheduler thread ----
+    def _loop(self):
+        torch.cuda.set_device(self.device)
+        while True:
+            with self._cv:
+                idle = (not self._waiting and not self._admitted
+                        and all(b is None for b in self._busy))
+                if idle and self._closing:
+                    return
+                if idle:
+                    self._cv.wait(timeout=0.05)
+                    continue
+            try:
+                self._admit()
+                self._launch()
+                progressed = self._complete()
+            except Exception as e:  # fail the affected requests, keep serving
+                self._fail_all(e)
+                progressed = True
+            if not progressed:
+                time.sleep(5e-5)
+
+    def _admit(self):
+        while True:
+            with self._cv:
+                if not self._waiting or self._used + self._waiting[0].nbytes > self.budget:
+                    return
+                r = self._waiting.popleft()
+                self._used += r.nbytes
+            tr = r.traj
+            # pinned host copies, kept on the trajectory object for repeated submissions
+            host = getattr(tr, "_dc_pinned", None)
+            if host is None:
+                host = tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                             for a in (tr.verts, tr.faces, tr.draws, tr.targets))
+                try:
+                    tr._dc_pinned = host
+                except AttributeError:
+                    pass
+            with torch.cuda.stream(self._copy):
+                dv = [h.to(self.device, non_blocking=True) for h in host]
+                r.ready = torch.cuda.Event()
+                r.ready.record(self._copy)
+            r.host = host  # pinned buffers live until the copy has finished
+            r.dev = DeviceTrajectory(dv[0], dv[1], dv[2], dv[3], np.asarray(tr.n_off, np.int64),
+                                     np.asarray(tr.m_off, np.int64))
+            self._admitted.append(r)
+
+    def _launch(self):
+        for s_idx, busy in enumerate(self._busy):
+            if busy is not None or not self._admitted:
+                continue
+            mode = self._admitted[0].mode
+            take, pairs = [], 0
+            for r in self._admitted:
+                if r.mode != mode:
+                    continue
+                p = r.dev.pairs()
+                if take and (len(take) >= self.max_batch_requests
+                             or pairs + p > self.max_batch_pairs):
+                    break
+                take.append(r)
+                pairs += p
+            for r in take:
+                self._admitted.remove(r)
+            stream = self._streams[s_idx]
+            for r in take:
+                stream.wait_event(r.ready)
+            b = BatchedLoss([r.dev for r in take], mode=mode,
+                            weights=[r.weights if r.weights is not None
+                                     else np.ones(r.dev.T, np.float32) for r in take],
+                            grad=any(r.grad for r in take), stream=stream)
+            b.run()
+            done = torch.cuda.Event()
+            done.record(stream)
+            self._busy[s_idx] = (b, done, take, self._next_batch, pairs)
+            self.batch_sizes.append(len(take))
+            self._next_batch += 1
+
+    def _complete(self) -> bool:
+        progressed = False
+        for s_idx, busy in enumerate(self._busy):
+            if busy is None:
+                continue
+            b, done, take, bid, _ = busy
+            if not done.query():
+                continue
+            status = _lib.ws_status(b.ws)
+            now = time.perf_counter()
+            for i, r in enumerate(take):
+                if status != _lib.DC_OK:
+                    r.future.set_exception(_lib.DCError(status, "device-side error in batch"))
+                else:
+                    lf = b.loss_frames[i].cpu().numpy()
+                    w = r.weights if r.weights is not None else np.ones_like(lf)
+                    gv = b.grad_verts[i].cpu().numpy() if (r.grad and b.grad_verts[i]
+                                                           is not None) else None
+                    lat = time.perf_counter() - r.arrival
+                    r.future.set_result(Result(lf, float(np.sum(w.astype(np.float64) * lf)), gv,
+                                               lat, bid, len(take)))
+                    self.completed.append((r.rid, lat, r.dev.pairs(), bid))
+                r.dev = None
+                r.host = ()
+            with self._cv:
+                self._used -= sum(r.nbytes for r in take)
+            self._busy[s_idx] = None
+            progressed = True
+        return progressed
+
+    def _fail_all(self, e):
+        for s_idx, busy in enumerate(self._busy):
+            if busy is not None:
+                for r in busy[2]:
+                    if not r.future.done():
+                        r.future.set_exception(e)
+                with self._cv:
+                    self._used -= sum(r.nbytes for r in busy[2])
+                self._busy[s_idx] = None
+        for r in self._admitted:
+            if not r.future.done():
+                r.future.set_exception(e)
+            with self._cv:
+                self._used -= r.nbytes
+        self._admitted.clear()
+
+
+def serve_plain(requests, device="cuda:0", mode: int = _lib.BIDIR_MEAN):
+    """The plain per-request form, for comparison: each request in arrival order, copied in,
+    computed with dc_loss_traj (uniform trajectories) on one stream, copied out. Requests are
+    (arrival_s, traj) pairs; returns the per-request latencies (s) measured from arrival."""
+    dev = torch.device(device)
+    t0 = time.perf_counter()
+    lat = []
+    for arrival, tr in requests:
+        now = time.perf_counter() - t0
+        if now < arrival:
+            time.sleep(arrival - now)
+        v = torch.from_numpy(tr.verts).to(dev)
+        f = torch.from_numpy(tr.faces).to(dev)
+        d = torch.from_numpy(np.ascontiguousarray(tr.draws_tn3())).to(dev)
+        y = torch.from_numpy(np.ascontiguousarray(tr.targets_tm3())).to(dev)
+        r = _lib.dc_loss_traj(v, f, d, y, mode=mode)
+        r["grad_verts"].cpu()
+        float(r["loss_total"][0])
+        lat.append(time.perf_counter() - t0 - arrival)
+    return lat

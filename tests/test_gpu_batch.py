@@ -62,3 +62,30 @@ def test_batch_equals_per_frame_form(trajs):
         np.testing.assert_allclose(b.loss_frames[k].cpu().numpy(), lf[k].cpu().numpy(),
                                    rtol=1e-6)
         assert parity.rel_l2(b.grad_verts[k].cpu().numpy(), gv[k].cpu().numpy()) < 1e-6
+
+
+@pytest.mark.slow
+def test_batched_uneven_full_size_sampled_frames():
+    """All 64 trajectories of the uneven workload (grids 15x15..80x80, 20..100 frames, 2 000 to
+    30 000 points per frame) in one batch, as the bench runs it; the oracle checks the first,
+    middle and last frame of three trajectories."""
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    trajs = [parity.nudge_draws(t)[0] for t in W.batched_uneven()]
+    dts = [DeviceTrajectory.from_host(t, DEV) for t in trajs]
+    b = BatchedLoss(dts, grad=True, graph=True, nn=True)
+    b.run(check=True)
+    torch.cuda.synchronize()
+    for k in (0, 31, 63):
+        t = trajs[k]
+        frames = sorted({0, t.T // 2, t.T - 1})
+        ref = oracle.loss_traj(t, frames=frames)
+        parity.check_loss(b.loss_frames[k].cpu().numpy()[frames], ref["loss_frames"][frames])
+        parity.check_grad(b.grad_verts[k].cpu().numpy()[frames], ref["grad_verts"][frames])
+        for f in frames:
+            n0, n1 = t.n_off[f], t.n_off[f + 1]
+            m0, m1 = t.m_off[f], t.m_off[f + 1]
+            parity.check_nn(b.nn_ab[k][n0:n1].cpu().numpy(), ref["frames"][f]["nn_ab"],
+                            b.nn_ba[k][m0:m1].cpu().numpy(), ref["frames"][f]["nn_ba"])
