@@ -129,8 +129,10 @@ def workspace(nbytes: int, device) -> torch.Tensor:
     return ws
 
 
-def ws_status(ws: torch.Tensor) -> int:
-    return int(lib().dc_ws_status(_ptr(ws), _stream(ws.device)))
+def ws_status(ws: torch.Tensor, stream=None) -> int:
+    """Device-side status of the calls issued on `stream` (default: current) with ws."""
+    s = _stream(ws.device) if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    return int(lib().dc_ws_status(_ptr(ws), s))
 
 
 def check_ws(ws: torch.Tensor):

@@ -47,6 +47,16 @@ class DeviceTrajectory:
         return int(np.sum(np.diff(self.n_off) * np.diff(self.m_off)))
 
 
+# numpy view of the C struct dc_frame (include/diffcloud.h), 88 bytes per frame
+FRAME_DTYPE = np.dtype([("verts", "u8"), ("faces", "u8"), ("draws", "u8"), ("targets", "u8"),
+                        ("V", "i4"), ("F", "i4"), ("N", "i4"), ("M", "i4"), ("weight", "f4"),
+                        ("tag", "i4"), ("loss", "u8"), ("grad_verts", "u8"), ("nn_ab", "u8"),
+                        ("nn_ba", "u8")])
+assert FRAME_DTYPE.itemsize == ctypes.sizeof(_lib.dc_frame)
+for _name, _ in _lib.dc_frame._fields_:
+    assert FRAME_DTYPE.fields[_name][1] == getattr(_lib.dc_frame, _name).offset
+
+
 class BatchedLoss:
     """Loss (and vertex gradients) of a list of trajectories in one planned launch sequence.
 
@@ -73,7 +83,8 @@ class BatchedLoss:
     def _build(self, mode, weights, grad, nn):
         dev = self.device
         nfr = sum(t.T for t in self.trajs)
-        self.frames = (_lib.dc_frame * nfr)()
+        # the dc_frame table, filled column by column (one row per frame)
+        tab = np.zeros(nfr, dtype=FRAME_DTYPE)
         self.loss_frames, self.grad_verts, self.nn_ab, self.nn_ba = [], [], [], []
         k = 0
         for i, tr in enumerate(self.trajs):
@@ -87,23 +98,29 @@ class BatchedLoss:
             self.grad_verts.append(gv)
             self.nn_ab.append(nab)
             self.nn_ba.append(nba)
-            w = None if weights is None else weights[i]
-            for t in range(T):
-                fr = self.frames[k]
-                n0, n1 = int(tr.n_off[t]), int(tr.n_off[t + 1])
-                m0, m1 = int(tr.m_off[t]), int(tr.m_off[t + 1])
-                fr.verts = tr.verts.data_ptr() + 4 * 3 * V * t
-                fr.faces = tr.faces.data_ptr()
-                fr.draws = tr.draws.data_ptr() + 4 * 3 * n0
-                fr.targets = tr.targets.data_ptr() + 4 * 3 * m0
-                fr.V, fr.F, fr.N, fr.M = V, F, n1 - n0, m1 - m0
-                fr.weight = 1.0 if w is None else float(w[t])
-                fr.tag = i
-                fr.loss = lf.data_ptr() + 4 * t
-                fr.grad_verts = gv.data_ptr() + 4 * 3 * V * t if grad else None
-                fr.nn_ab = nab.data_ptr() + 4 * n0 if nn else None
-                fr.nn_ba = nba.data_ptr() + 4 * m0 if nba is not None else None
-                k += 1
+            n_off = np.asarray(tr.n_off, np.int64)
+            m_off = np.asarray(tr.m_off, np.int64)
+            t = np.arange(T, dtype=np.int64)
+            row = tab[k:k + T]
+            row["verts"] = tr.verts.data_ptr() + 12 * V * t
+            row["faces"] = tr.faces.data_ptr()
+            row["draws"] = tr.draws.data_ptr() + 12 * n_off[:-1]
+            row["targets"] = tr.targets.data_ptr() + 12 * m_off[:-1]
+            row["V"], row["F"] = V, F
+            row["N"] = np.diff(n_off)
+            row["M"] = np.diff(m_off)
+            row["weight"] = 1.0 if weights is None or weights[i] is None else weights[i]
+            row["tag"] = i
+            row["loss"] = lf.data_ptr() + 4 * t
+            if grad:
+                row["grad_verts"] = gv.data_ptr() + 12 * V * t
+            if nab is not None:
+                row["nn_ab"] = nab.data_ptr() + 4 * n_off[:-1]
+            if nba is not None:
+                row["nn_ba"] = nba.data_ptr() + 4 * m_off[:-1]
+            k += T
+        self._table = tab
+        self.frames = tab.ctypes.data_as(ctypes.POINTER(_lib.dc_frame))
         L = _lib.lib()
         nb = int(L.dc_batch_workspace_size(self.frames, nfr))
         if nb == 0:

@@ -7,9 +7,13 @@ every optimisation). The server batches continuously:
   - admission: requests wait in arrival order until their device memory (inputs, outputs and
     their share of a batch workspace) fits in the HBM budget; their inputs are then copied to
     the device once, on a copy stream, and stay resident until the result is delivered;
-  - batching: whenever one of the compute streams is free, every admitted request of the
-    same mode (up to a size cap) goes into one planned launch sequence (dc_batch_plan /
-    dc_batch_run): one persistent Chamfer launch covers all their frames, whatever their sizes;
+  - time slicing: an admitted request is cut into items of consecutive frames of at most
+    `item_pairs` point pairs, so that a long request cannot hold the GPU for its whole
+    duration (one persistent Chamfer launch occupies every SM until it ends);
+  - batching: whenever one of the compute streams is free, admitted items of the same mode,
+    oldest first, up to `max_batch_pairs`, go into one planned launch sequence
+    (dc_batch_plan / dc_batch_run): one persistent Chamfer launch covers all their frames,
+    whatever their sizes;
   - overlap: batches on different streams run at the same time while new requests are
     admitted and copied in; finished batches resolve their requests' futures and release their
     memory, which admits the next requests.
@@ -43,7 +47,7 @@ class Result:
     batch_requests: int
 
 
-@dataclass
+@dataclass(eq=False)  # identity comparison: the fields hold arrays and tensors
 class _Request:
     rid: int
     traj: object
@@ -56,6 +60,28 @@ class _Request:
     dev: DeviceTrajectory | None = None
     ready: torch.cuda.Event | None = None
     host: tuple = field(default_factory=tuple)
+    loss: np.ndarray | None = None     # [T] filled item by item
+    gradv: np.ndarray | None = None    # [T, V, 3]
+    left: int = 0                      # items not finished yet
+    batches: set = field(default_factory=set)
+    failed: bool = False
+
+
+@dataclass(eq=False)
+class _Item:
+    req: _Request
+    a: int             # first frame
+    b: int             # one past the last frame
+    dev: DeviceTrajectory
+    pairs: int
+
+
+def _slice(d: DeviceTrajectory, a: int, b: int) -> DeviceTrajectory:
+    """Frames [a, b) of a device trajectory (views, no copies)."""
+    n0, n1 = int(d.n_off[a]), int(d.n_off[b])
+    m0, m1 = int(d.m_off[a]), int(d.m_off[b])
+    return DeviceTrajectory(d.verts[a:b], d.faces, d.draws[n0:n1], d.targets[m0:m1],
+                            d.n_off[a:b + 1] - n0, d.m_off[a:b + 1] - m0)
 
 
 def _frames_of(traj):
@@ -83,11 +109,15 @@ class Server:
     """Continuous-batching loss+gradient server on one GPU."""
 
     def __init__(self, device="cuda:0", hbm_budget: int = 120 << 30, streams: int = 2,
-                 max_batch_requests: int = 256, max_batch_pairs: int = 2 * 10**12):
+                 max_batch_items: int = 512, max_batch_pairs: int = 8 * 10**9,
+                 item_pairs: int = 4 * 10**9):
+        """max_batch_pairs: batch size when the queue is short; under load batches grow up
+        to 8x that. item_pairs: the time slice a long request is cut into."""
         self.device = torch.device(device)
         self.budget = int(hbm_budget)
-        self.max_batch_requests = max_batch_requests
+        self.max_batch_items = max_batch_items
         self.max_batch_pairs = max_batch_pairs
+        self.item_pairs = item_pairs
         self._copy = torch.cuda.Stream(self.device)
         self._streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
         self._busy = [None] * streams
@@ -146,6 +176,9 @@ class Server:
     # ---- scheduler thread ----
     def _loop(self):
         torch.cuda.set_device(self.device)
+        # the scheduler's own allocations and copies go on the copy stream, never on the
+        # legacy default stream
+        torch.cuda.set_stream(self._copy)
         while True:
             with self._cv:
                 idle = (not self._waiting and not self._admitted
@@ -189,32 +222,60 @@ class Server:
             r.host = host  # pinned buffers live until the copy has finished
             r.dev = DeviceTrajectory(dv[0], dv[1], dv[2], dv[3], np.asarray(tr.n_off, np.int64),
                                      np.asarray(tr.m_off, np.int64))
-            self._admitted.append(r)
+            r.loss = np.empty(tr.T, np.float32)
+            r.gradv = np.empty(tr.verts.shape, np.float32) if r.grad else None
+            # cut into items of consecutive frames of at most item_pairs pairs
+            per = np.diff(r.dev.n_off) * np.diff(r.dev.m_off)
+            a = 0
+            items = []
+            while a < tr.T:
+                b, acc = a, 0
+                while b < tr.T and (b == a or acc + per[b] <= self.item_pairs):
+                    acc += int(per[b])
+                    b += 1
+                items.append(_Item(r, a, b, _slice(r.dev, a, b), acc))
+                a = b
+            r.left = len(items)
+            self._admitted.extend(items)
 
     def _launch(self):
         for s_idx, busy in enumerate(self._busy):
             if busy is not None or not self._admitted:
                 continue
-            mode = self._admitted[0].mode
-            take, pairs = [], 0
-            for r in self._admitted:
-                if r.mode != mode:
-                    continue
-                p = r.dev.pairs()
-                if take and (len(take) >= self.max_batch_requests
-                             or pairs + p > self.max_batch_pairs):
+            mode = self._admitted[0].req.mode
+            # small batches while few requests wait (latency), larger ones when many do
+            # (fewer launches per pair)
+            waiting = len({id(it.req) for it in self._admitted})
+            cap = self.max_batch_pairs * max(1, min(8, waiting // 8))
+            # round robin over requests in arrival order: at most one item of each request
+            # per pass, so a short request is not queued behind a long one's items
+            take, taken, pairs, full = [], set(), 0, False
+            while not full:
+                seen, added = set(), False
+                for it in self._admitted:
+                    if it.req.mode != mode or id(it.req) in seen or id(it) in taken:
+                        continue
+                    seen.add(id(it.req))
+                    if take and (len(take) >= self.max_batch_items or pairs + it.pairs > cap):
+                        full = True
+                        break
+                    take.append(it)
+                    taken.add(id(it))
+                    pairs += it.pairs
+                    added = True
+                if not added:
                     break
-                take.append(r)
-                pairs += p
-            for r in take:
-                self._admitted.remove(r)
+            for it in take:
+                self._admitted.remove(it)
             stream = self._streams[s_idx]
-            for r in take:
+            for r in {id(it.req): it.req for it in take}.values():
                 stream.wait_event(r.ready)
-            b = BatchedLoss([r.dev for r in take], mode=mode,
-                            weights=[r.weights if r.weights is not None
-                                     else np.ones(r.dev.T, np.float32) for r in take],
-                            grad=any(r.grad for r in take), stream=stream)
+            weights = []
+            for it in take:
+                w = it.req.weights
+                weights.append(w[it.a:it.b] if w is not None else np.ones(it.b - it.a, np.float32))
+            b = BatchedLoss([it.dev for it in take], mode=mode, weights=weights,
+                            grad=any(it.req.grad for it in take), stream=stream)
             b.run()
             done = torch.cuda.Event()
             done.record(stream)
@@ -230,43 +291,55 @@ class Server:
             b, done, take, bid, _ = busy
             if not done.query():
                 continue
-            status = _lib.ws_status(b.ws)
-            now = time.perf_counter()
-            for i, r in enumerate(take):
-                if status != _lib.DC_OK:
+            finished = []
+            # status and results are read on the batch's own stream, which is done: nothing
+            # here waits for the batch running on the other stream
+            with torch.cuda.stream(b.stream):
+                status = _lib.ws_status(b.ws, b.stream)
+                for i, it in enumerate(take):
+                    r = it.req
+                    if status != _lib.DC_OK:
+                        r.failed = True
+                    else:
+                        r.loss[it.a:it.b] = b.loss_frames[i].cpu().numpy()
+                        if r.grad and b.grad_verts[i] is not None:
+                            r.gradv[it.a:it.b] = b.grad_verts[i].cpu().numpy()
+                    r.batches.add(bid)
+                    r.left -= 1
+                    if r.left == 0:
+                        finished.append(r)
+            for r in finished:
+                if r.failed:
                     r.future.set_exception(_lib.DCError(status, "device-side error in batch"))
                 else:
-                    lf = b.loss_frames[i].cpu().numpy()
-                    w = r.weights if r.weights is not None else np.ones_like(lf)
-                    gv = b.grad_verts[i].cpu().numpy() if (r.grad and b.grad_verts[i]
-                                                           is not None) else None
+                    w = r.weights if r.weights is not None else np.ones_like(r.loss)
                     lat = time.perf_counter() - r.arrival
-                    r.future.set_result(Result(lf, float(np.sum(w.astype(np.float64) * lf)), gv,
-                                               lat, bid, len(take)))
+                    r.future.set_result(Result(r.loss, float(np.sum(w.astype(np.float64) * r.loss)),
+                                               r.gradv, lat, max(r.batches), len(take)))
                     self.completed.append((r.rid, lat, r.dev.pairs(), bid))
                 r.dev = None
                 r.host = ()
-            with self._cv:
-                self._used -= sum(r.nbytes for r in take)
+                with self._cv:
+                    self._used -= r.nbytes
             self._busy[s_idx] = None
             progressed = True
         return progressed
 
     def _fail_all(self, e):
+        reqs = {}
         for s_idx, busy in enumerate(self._busy):
             if busy is not None:
-                for r in busy[2]:
-                    if not r.future.done():
-                        r.future.set_exception(e)
-                with self._cv:
-                    self._used -= sum(r.nbytes for r in busy[2])
+                for it in busy[2]:
+                    reqs[id(it.req)] = it.req
                 self._busy[s_idx] = None
-        for r in self._admitted:
+        for it in self._admitted:
+            reqs[id(it.req)] = it.req
+        self._admitted.clear()
+        for r in reqs.values():
             if not r.future.done():
                 r.future.set_exception(e)
             with self._cv:
                 self._used -= r.nbytes
-        self._admitted.clear()
 
 
 def serve_plain(requests, device="cuda:0", mode: int = _lib.BIDIR_MEAN):
