@@ -166,6 +166,22 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
 int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
 
 /*
+ * Tuning of the Chamfer kernel's tile shape. A CTA of w warps (w = 1, 2 or 4) holds
+ * w * 512 sim points in registers while target chunks stream through it: wide CTAs amortise
+ * the target staging and the column merges over more points, narrow ones split small
+ * problems into enough work items to fill the GPU. warps_per_cta = 0 (the default) picks the
+ * widest width that still gives every resident CTA several work items. dc_tune_set sets the
+ * width for every later call in the process (an autotuner times the widths per problem size
+ * and sets the winner before its calls); batch plans keep the width they were planned with.
+ */
+typedef struct dc_tune {
+    int32_t warps_per_cta; /* 0: automatic, else 1, 2 or 4 */
+} dc_tune;
+
+int dc_tune_set(const dc_tune* tune); /* NULL restores automatic */
+int dc_tune_get(dc_tune* tune);
+
+/*
  * dc_ws_status -- synchronise `stream` and return the first device-side error recorded in
  * ws by the calls issued so far (DC_OK if none). The next call on ws clears it.
  */

@@ -31,6 +31,10 @@ class DCError(RuntimeError):
         self.code = code
 
 
+class dc_tune(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32)]
+
+
 class dc_frame(ctypes.Structure):
     _fields_ = [("verts", ctypes.c_void_p), ("faces", ctypes.c_void_p),
                 ("draws", ctypes.c_void_p), ("targets", ctypes.c_void_p),
@@ -72,6 +76,8 @@ def lib() -> ctypes.CDLL:
                 "dc_prof_stop": (I, [ctypes.POINTER(F), ctypes.POINTER(I)]),
                 "dc_loss_traj_noalloc": (I, [P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P,
                                              P]),
+                "dc_tune_set": (I, [P]),
+                "dc_tune_get": (I, [P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -296,3 +302,15 @@ def dc_loss_traj_noalloc(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=
         if code != DC_OK:
             raise DCError(code, "device-side error reported by dc_loss_traj_noalloc")
     return {"loss_total": lt, "loss_frames": lf, "grad_verts": gv, "nn_ab": nab, "nn_ba": nba}
+
+
+def tune_set(warps_per_cta: int = 0):
+    """Chamfer CTA width (1, 2 or 4 warps; 0: automatic) for every later call."""
+    t = dc_tune(int(warps_per_cta))
+    _check(lib().dc_tune_set(ctypes.byref(t)))
+
+
+def tune_get() -> int:
+    t = dc_tune(0)
+    _check(lib().dc_tune_get(ctypes.byref(t)))
+    return int(t.warps_per_cta)

@@ -113,22 +113,24 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 constexpr long long INT_LIMIT = 0x7fffffffLL;
 
-// Sizes of a uniform trajectory; false if any derived count overflows int32.
-bool uniform_sizes(int T, int V, int F, int N, int M, Sizes& s, int& upf, int& spu) {
+// Sizes of a uniform trajectory; false if any derived count overflows int32. The unit
+// arrays are sized for the narrowest CTA (the most units); sub[w] is the Chamfer work
+// (sub-chunks) at CTA width 1, 2 and 4 (indices 0, 1, 2).
+bool uniform_sizes(int T, int V, int F, int N, int M, Sizes& s, long long sub[3], int& spu) {
     const long long Npad = (long long)div_up(N, ROW_PAD) * ROW_PAD;
     const long long Mpad = M > 0 ? (long long)div_up(M, COL_PAD) * COL_PAD : 0;
-    upf = div_up(N, ROWS_PER_UNIT);
     spu = M > 0 ? div_up(M, SUB) : 0;
+    for (int i = 0; i < 3; ++i)
+        sub[i] = (long long)T * div_up(N, ROWS_PER_WARP << i) * spu;
     s.n_frames = T;
-    s.n_units = (long long)T * upf;
+    s.n_units = (long long)T * div_up(N, ROWS_PER_WARP);
     s.sum_f = (long long)T * F;
     s.rows = (long long)T * Npad;
     s.cols = (long long)T * Mpad;
     s.slices = epilogue_slices(T);
     s.gscr = s.slices > 1 ? (long long)T * s.slices * 3 * V : 0;
-    const long long total_sub = s.n_units * spu;
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
-           total_sub < INT_LIMIT && s.rows * 3 < INT_LIMIT * 16 && s.cols * 6 < INT_LIMIT * 16 &&
+           sub[0] < INT_LIMIT && s.rows * 3 < INT_LIMIT * 16 && s.cols * 6 < INT_LIMIT * 16 &&
            s.gscr < INT_LIMIT * 4;
 }
 
@@ -150,10 +152,13 @@ int check_ws(void* ws, size_t ws_bytes, size_t need) {
 int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total, void* ws,
                 size_t ws_bytes, cudaStream_t st) {
     Sizes sz;
-    int upf = 0, spu = 0;
-    if (!uniform_sizes(a.T, a.V, a.F, a.N, a.M, sz, upf, spu))
+    long long sub[3];
+    int spu = 0;
+    if (!uniform_sizes(a.T, a.V, a.F, a.N, a.M, sz, sub, spu))
         return fail(DC_EINVAL, "problem too large for 32-bit offsets");
-    a.units_per_frame = upf;
+    const int warps = (phases & PH_CHAMFER) ? choose_warps(a.mode, sub[2], sub[1], sub[0]) : 1;
+    a.warps = warps;
+    a.units_per_frame = div_up(a.N, ROWS_PER_WARP * warps);
     a.subs_per_unit = spu;
     a.slices = (int)sz.slices;
     const Layout L = make_layout(sz);
@@ -166,8 +171,10 @@ int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total
     if (!e && (phases & (PH_SAMPLE | PH_TARGETS)))
         e = launch_stage(w, T, (int)sz.slices, a.pts ? 0 : a.F, (phases & PH_SAMPLE) ? rows : 0,
                          (phases & PH_TARGETS) ? cols : 0, st);
-    if (!e && (phases & PH_CHAMFER))
-        e = launch_chamfer(w, (int)sz.n_units, (int)(sz.n_units * spu), a.mode, st);
+    if (!e && (phases & PH_CHAMFER)) {
+        const long long units = (long long)T * a.units_per_frame;
+        e = launch_chamfer(w, (int)units, (int)(units * spu), a.mode, warps, st);
+    }
     if (!e && epi_flags)
         e = launch_epilogue(w, T, (int)sz.slices, a.grad ? a.V : 0, a.mode, epi_flags,
                             loss_total, st);
@@ -192,7 +199,7 @@ int check_ptrs(std::initializer_list<const void*> ps, const char* what) {
 // ---- batch plans (host copy of what dc_batch_run needs to launch) ----
 struct Plan {
     Sizes sz;
-    int mode, any_grad, max_v, max_f, total_sub;
+    int mode, any_grad, max_v, max_f, total_sub, n_units, warps;
     size_t bytes;
 };
 std::mutex g_plan_mu;
@@ -241,11 +248,26 @@ int dc_prof_stop(float* total_ms, int* launches) {
     return DC_OK;
 }
 
+int dc_tune_set(const dc_tune* tune) {
+    const int w = tune ? tune->warps_per_cta : 0;
+    if (w != 0 && w != 1 && w != 2 && w != 4)
+        return fail(DC_EINVAL, "warps_per_cta must be 0 (automatic), 1, 2 or 4");
+    set_tuned_warps(w);
+    return DC_OK;
+}
+
+int dc_tune_get(dc_tune* tune) {
+    if (!tune) return fail(DC_EINVAL, "tune is NULL");
+    tune->warps_per_cta = tuned_warps();
+    return DC_OK;
+}
+
 size_t dc_workspace_size(int T, int V, int F, int N, int M) {
     if (T <= 0 || V <= 0 || F <= 0 || N <= 0 || M < 0) return 0;
     Sizes sz;
-    int upf, spu;
-    if (!uniform_sizes(T, V, F, N, M, sz, upf, spu)) return 0;
+    long long sub[3];
+    int spu;
+    if (!uniform_sizes(T, V, F, N, M, sz, sub, spu)) return 0;
     return make_layout(sz).total;
 }
 
@@ -382,22 +404,22 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draw
 // ---------------------------------------------------------------------------------------
 // batches
 // ---------------------------------------------------------------------------------------
-static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long& total_sub) {
+static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long sub[3]) {
     s = Sizes{n, 0, 0, 0, 0, epilogue_slices(n), 0};
-    total_sub = 0;
+    sub[0] = sub[1] = sub[2] = 0;
     long long max_v = 0;
     for (int k = 0; k < n; ++k) {
-        const long long upf = div_up(fr[k].N, ROWS_PER_UNIT);
-        s.n_units += upf;
+        const long long spu = div_up(fr[k].M, SUB);
+        s.n_units += div_up(fr[k].N, ROWS_PER_WARP);
+        for (int i = 0; i < 3; ++i) sub[i] += (long long)div_up(fr[k].N, ROWS_PER_WARP << i) * spu;
         s.sum_f += fr[k].F;
         s.rows += (long long)div_up(fr[k].N, ROW_PAD) * ROW_PAD;
         s.cols += (long long)div_up(fr[k].M, COL_PAD) * COL_PAD;
-        total_sub += upf * div_up(fr[k].M, SUB);
         if (fr[k].grad_verts && fr[k].V > max_v) max_v = fr[k].V;
     }
     s.gscr = s.slices > 1 ? (long long)n * s.slices * 3 * max_v : 0;
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
-           total_sub < INT_LIMIT && s.n_units < INT_LIMIT && s.cols * 6 < INT_LIMIT * 16 &&
+           sub[0] < INT_LIMIT && s.n_units < INT_LIMIT && s.cols * 6 < INT_LIMIT * 16 &&
            s.gscr < INT_LIMIT * 4;
 }
 
@@ -407,8 +429,8 @@ size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames) {
         if (frames[k].N <= 0 || frames[k].M <= 0 || frames[k].F <= 0 || frames[k].V <= 0)
             return 0;
     Sizes sz;
-    long long ts;
-    if (!batch_sizes(frames, n_frames, sz, ts)) return 0;
+    long long sub[3];
+    if (!batch_sizes(frames, n_frames, sz, sub)) return 0;
     return make_layout(sz).total;
 }
 
@@ -427,9 +449,10 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
             return fail(DC_EINVAL, "frame %d: pointers must be 4-byte aligned", k);
     }
     Sizes sz;
-    long long total_sub;
-    if (!batch_sizes(frames, n_frames, sz, total_sub))
+    long long sub[3];
+    if (!batch_sizes(frames, n_frames, sz, sub))
         return fail(DC_EINVAL, "batch too large for 32-bit offsets");
+    const int warps = choose_warps(mode, sub[2], sub[1], sub[0]);
     const Layout L = make_layout(sz);
     int rc = check_ws(ws, ws_bytes, L.total);
     if (rc) return rc;
@@ -444,7 +467,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     int* ufr = reinterpret_cast<int*>(img.data() + L.unit_frame);
     int* urb = reinterpret_cast<int*>(img.data() + L.unit_rb);
     int* upre = reinterpret_cast<int*>(img.data() + L.unit_pre);
-    int row0 = 0, col0 = 0, cdf0 = 0, unit = 0, sub = 0, any_grad = 0, max_v = 0, max_f = 0;
+    int row0 = 0, col0 = 0, cdf0 = 0, unit = 0, subc = 0, any_grad = 0, max_v = 0, max_f = 0;
     for (int k = 0; k < n_frames; ++k) {
         const dc_frame& f = frames[k];
         FrameDesc d{};
@@ -471,12 +494,12 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
         fd[k] = d;
         rowpre[k] = row0;
         colpre[k] = col0;
-        const int upf = div_up(f.N, ROWS_PER_UNIT), spu = div_up(f.M, SUB);
+        const int upf = div_up(f.N, ROWS_PER_WARP * warps), spu = div_up(f.M, SUB);
         for (int r = 0; r < upf; ++r, ++unit) {
             ufr[unit] = k;
             urb[unit] = r;
-            upre[unit] = sub;
-            sub += spu;
+            upre[unit] = subc;
+            subc += spu;
         }
         if (f.F > max_f) max_f = f.F;
         if (f.grad_verts) {
@@ -489,11 +512,11 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     }
     rowpre[n_frames] = row0;
     colpre[n_frames] = col0;
-    upre[unit] = sub;
+    upre[unit] = subc;
     h->status = DC_OK;
     h->n_frames = n_frames;
     h->n_units = unit;
-    h->total_sub = sub;
+    h->total_sub = subc;
     h->total_rows = row0;
     h->total_cols = col0;
     h->sum_f = cdf0;
@@ -502,6 +525,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     h->any_grad = any_grad;
     h->max_v = max_v;
     h->slices = (int)sz.slices;
+    h->warps = warps;
     cudaError_t e = cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, stream);
     if (!e) e = cudaStreamSynchronize(stream);
     if (e) return cuda_fail(e, "dc_batch_plan copy");
@@ -511,7 +535,9 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     p.any_grad = any_grad;
     p.max_v = max_v;
     p.max_f = max_f;
-    p.total_sub = sub;
+    p.total_sub = subc;
+    p.n_units = unit;
+    p.warps = warps;
     p.bytes = L.total;
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_plans[ws] = p;
@@ -532,7 +558,7 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
     cudaError_t e = launch_reset(w, stream);
     if (!e) e = launch_area_cdf(w, n, stream);
     if (!e) e = launch_stage(w, n, (int)p.sz.slices, p.max_f, rows, cols, stream);
-    if (!e) e = launch_chamfer(w, (int)p.sz.n_units, p.total_sub, p.mode, stream);
+    if (!e) e = launch_chamfer(w, p.n_units, p.total_sub, p.mode, p.warps, stream);
     if (!e)
         e = launch_epilogue(w, n, (int)p.sz.slices, p.any_grad ? p.max_v : 0, p.mode,
                             EPI_RESCAN | EPI_LOSS | (p.any_grad ? EPI_GRAD : 0), loss_total,

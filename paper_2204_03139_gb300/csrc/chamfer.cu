@@ -149,9 +149,18 @@ __device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const fl
     }
 }
 
-template <bool BIDIR>
-__global__ void __launch_bounds__(THREADS, DC_CHAMFER_MIN_BLOCKS)
+// resident CTAs per SM the register budget is sized for, per CTA width
+template <int W>
+struct MinBlocks {
+    static constexpr int value = W == 4 ? 3 : (W == 2 ? 6 : 12);
+};
+
+template <bool BIDIR, int W>
+__global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
     k_chamfer(Ws w, int n_units, int total_sub) {
+    constexpr int THREADS = 32 * W;
+    constexpr int WARPS = W;
+    constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * W;
     // targets of two chunks, each coordinate negated and twice: [buffer][plane][2 * CHUNK]
     __shared__ __align__(128) float s_t[2][3][2 * CHUNK];
     // per-warp column minima of the chunk and the ballot of the lanes that hold them
@@ -325,39 +334,72 @@ __global__ void __launch_bounds__(THREADS, DC_CHAMFER_MIN_BLOCKS)
     }
 }
 
-int g_chamfer_ctas[64][2];  // per device, per mode: resident CTAs for the persistent grid
+int g_chamfer_ctas[64][2][3];  // per device, mode and width: resident CTAs of the grid
 
-int chamfer_ctas(int mode) {
+template <bool BIDIR, int W>
+int occupancy() {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chamfer<BIDIR, W>, 32 * W, 0);
+    return occ;
+}
+
+int width_index(int warps) { return warps == 4 ? 2 : (warps == 2 ? 1 : 0); }
+
+int g_tuned_warps = 0;  // process-wide CTA width set by dc_tune_set (0: automatic)
+
+}  // namespace
+
+int chamfer_grid(int mode, int warps) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    int& n = g_chamfer_ctas[dev][mode == DC_BIDIR_MEAN ? 0 : 1];
+    const int b = mode == DC_BIDIR_MEAN ? 0 : 1, wi = width_index(warps);
+    int& n = g_chamfer_ctas[dev][b][wi];
     if (n == 0) {
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (mode == DC_BIDIR_MEAN)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chamfer<true>, THREADS, 0);
+        if (b == 0)
+            occ = wi == 2 ? occupancy<true, 4>() : (wi == 1 ? occupancy<true, 2>()
+                                                             : occupancy<true, 1>());
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chamfer<false>, THREADS, 0);
+            occ = wi == 2 ? occupancy<false, 4>() : (wi == 1 ? occupancy<false, 2>()
+                                                              : occupancy<false, 1>());
         n = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
     }
     return n;
 }
 
-}  // namespace
+int choose_warps(int mode, long long sub_w4, long long sub_w2, long long sub_w1) {
+    if (g_tuned_warps == 1 || g_tuned_warps == 2 || g_tuned_warps == 4) return g_tuned_warps;
+    // at least 8 sub-chunks per resident CTA keeps the per-unit set-up small
+    if (sub_w4 >= 8LL * chamfer_grid(mode, 4)) return 4;
+    if (sub_w2 >= 8LL * chamfer_grid(mode, 2)) return 2;
+    return 1;
+}
 
-cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, cudaStream_t s) {
+cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, int warps,
+                           cudaStream_t s) {
     if (total_sub <= 0) return cudaSuccess;
-    int grid = chamfer_ctas(mode);
+    int grid = chamfer_grid(mode, warps);
     if (grid > total_sub) grid = total_sub;
     prof_before(s);
-    if (mode == DC_BIDIR_MEAN)
-        k_chamfer<true><<<grid, THREADS, 0, s>>>(w, n_units, total_sub);
-    else
-        k_chamfer<false><<<grid, THREADS, 0, s>>>(w, n_units, total_sub);
+    const bool bi = mode == DC_BIDIR_MEAN;
+    if (warps == 4) {
+        if (bi) k_chamfer<true, 4><<<grid, 128, 0, s>>>(w, n_units, total_sub);
+        else k_chamfer<false, 4><<<grid, 128, 0, s>>>(w, n_units, total_sub);
+    } else if (warps == 2) {
+        if (bi) k_chamfer<true, 2><<<grid, 64, 0, s>>>(w, n_units, total_sub);
+        else k_chamfer<false, 2><<<grid, 64, 0, s>>>(w, n_units, total_sub);
+    } else {
+        if (bi) k_chamfer<true, 1><<<grid, 32, 0, s>>>(w, n_units, total_sub);
+        else k_chamfer<false, 1><<<grid, 32, 0, s>>>(w, n_units, total_sub);
+    }
     prof_after(s);
     count_launch();
     return cudaGetLastError();
 }
+
+void set_tuned_warps(int warps) { g_tuned_warps = warps; }
+int tuned_warps() { return g_tuned_warps; }
 
 }  // namespace dc

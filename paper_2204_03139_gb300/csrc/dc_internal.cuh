@@ -19,17 +19,12 @@ namespace dc {
 #ifndef DC_ROWS_PER_THREAD
 #define DC_ROWS_PER_THREAD 16
 #endif
-#ifndef DC_WARPS
-#define DC_WARPS 4
-#endif
-#ifndef DC_CHAMFER_MIN_BLOCKS
-#define DC_CHAMFER_MIN_BLOCKS 3
-#endif
 constexpr int ROWS_PER_THREAD = DC_ROWS_PER_THREAD;  // even
-constexpr int WARPS = DC_WARPS;
-constexpr int THREADS = 32 * WARPS;
 constexpr int ROWS_PER_WARP = 32 * ROWS_PER_THREAD;       // 512
-constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * WARPS;      // 2048
+// A Chamfer CTA has 1, 2 or 4 warps (units of 512, 1024 or 2048 sim points): wide CTAs
+// amortise the target staging and the column merges over more rows, narrow ones give
+// small problems enough work items to fill the GPU.
+constexpr int MAX_WARPS = 4;
 constexpr int SUB = 32;                                   // targets per tracked sub-chunk
 constexpr int CHUNK = 256;                                // targets per staged chunk
 constexpr int SUBS_PER_CHUNK = CHUNK / SUB;
@@ -81,7 +76,8 @@ struct WsHeader {
     int any_grad;
     int max_v;        // largest V among frames with a gradient
     int slices;       // epilogue slices per frame
-    int pad[52];
+    int warps;        // warps per Chamfer CTA (units of warps * ROWS_PER_WARP sim points)
+    int pad[51];
 };
 
 // Byte offsets of every region of a workspace (computed on the host).
@@ -151,7 +147,7 @@ struct UniformArgs {
     float* out_bary;
     const float* weight;   // [T] nullable
     const float* gscale;   // [T] nullable: defaults to weight
-    int T, V, F, N, M, mode, units_per_frame, subs_per_unit, slices;
+    int T, V, F, N, M, mode, units_per_frame, subs_per_unit, slices, warps;
 };
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s);
@@ -163,7 +159,15 @@ cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s);
 // floats) fits in shared memory, else launch_sample + launch_targets
 cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
                          cudaStream_t s);
-cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, cudaStream_t s);
+cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, int warps,
+                           cudaStream_t s);
+// resident Chamfer CTAs on the current device for a CTA width (persistent grid size)
+int chamfer_grid(int mode, int warps);
+// CTA width for a problem: the tuned default if one is set, else the widest width that gives
+// every resident CTA at least a few sub-chunks; sub_w4 is the work at width 4
+int choose_warps(int mode, long long sub_w4, long long sub_w2, long long sub_w1);
+void set_tuned_warps(int warps);  // 0: automatic
+int tuned_warps();
 // epilogue: neighbour recovery (rescan), loss partials, gradient scatter
 enum : int { EPI_RESCAN = 1, EPI_LOSS = 2, EPI_GRAD = 4 };
 cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, int mode,

@@ -49,6 +49,7 @@ __global__ void k_build_uniform(UniformArgs a, Ws w) {
         h->any_grad = a.grad != nullptr;
         h->max_v = a.V;
         h->slices = a.slices;
+        h->warps = a.warps;
     }
     if (g <= a.T) {
         w.rowpre[g] = g * Npad;

@@ -102,11 +102,12 @@ def test_trajectory_100x100_full_size_sampled_frames():
 
 
 # ---------------------------------------------------------------------------------------------
-# ragged sizes: tails of every tile level (8-row groups, 256-row warps, 1024-row units,
-# 64-target sub-chunks, 256-target chunks)
+# ragged sizes: tails of every tile level (16-row thread groups, 512-row warps, units of
+# 512 / 1024 / 2048 rows, 32-target sub-chunks, 256-target chunks)
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("n,m", [(1, 1), (1, 300), (300, 1), (2, 3), (63, 65), (255, 257),
-                                 (1023, 1025), (1025, 511), (2049, 4097), (3000, 64)])
+@pytest.mark.parametrize("n,m", [(1, 1), (1, 300), (300, 1), (2, 3), (31, 33), (63, 65),
+                                 (255, 257), (511, 513), (1023, 1025), (1025, 511),
+                                 (2049, 4097), (3000, 64)])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_ragged_sizes(n, m, mode):
     tr = W.lift_trajectory(7 + n + 3 * m, 9, 2, n, m, name="ragged")
@@ -266,6 +267,29 @@ def test_device_errors_are_reported():
     # the next good call clears the status
     r = L().dc_loss_traj(v2, f, d, y, check=True)
     assert torch.isfinite(r["loss_frames"]).all()
+
+
+@pytest.mark.parametrize("shape", [(2, 2048, 2048), (3, 5000, 7000)])
+def test_every_cta_width_gives_identical_results(shape):
+    """The three Chamfer tile shapes (1, 2, 4 warps per CTA) split the same pairs differently;
+    minima, neighbours and losses must not change by a single bit."""
+    from paper_2204_03139_gb300 import autotune
+
+    T, n, m = shape
+    tr = W.trajectory_50x50(T=T, n=n, m=m)
+    v, f, d, y = to_dev(tr)
+    outs = {}
+    for wd in (1, 2, 4):
+        with autotune.tuned(wd):
+            r = L().dc_loss_traj(v, f, d, y, check=True)
+        torch.cuda.synchronize()
+        outs[wd] = {k: x.cpu().numpy() for k, x in r.items() if x is not None}
+    for wd in (1, 2):
+        for k in ("loss_frames", "loss_total", "nn_ab", "nn_ba"):
+            np.testing.assert_array_equal(outs[wd][k], outs[4][k])
+        assert parity.rel_l2(outs[wd]["grad_verts"], outs[4]["grad_verts"]) < 1e-6
+    res = autotune.tune(v, f, d, y, reps=1, save=False)
+    assert res["best"] in (1, 2, 4) and all(t > 0 for t in res["ms"].values())
 
 
 def test_loss_is_deterministic():
