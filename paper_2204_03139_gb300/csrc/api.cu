@@ -398,7 +398,9 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draw
     a.N = N;
     a.M = M;
     a.mode = mode;
-    return run_uniform(a, PH_AREA | PH_SAMPLE, EPI_GRAD, nullptr, ws, ws_bytes, stream);
+    // targets are staged too: the gradient reads them from the compact planes
+    return run_uniform(a, PH_AREA | PH_SAMPLE | PH_TARGETS, EPI_GRAD, nullptr, ws, ws_bytes,
+                       stream);
 }
 
 // ---------------------------------------------------------------------------------------

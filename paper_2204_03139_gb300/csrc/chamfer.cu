@@ -100,6 +100,11 @@ struct UnitState {
     int N, M, Mpad, row0, col0, rb, sub_lo, sub_hi;
 };
 
+#ifndef DC_TARGETS_PER_STEP
+#define DC_TARGETS_PER_STEP 2
+#endif
+constexpr int TPS = DC_TARGETS_PER_STEP;  // targets per inner step (2 or 4)
+
 // one sub-chunk: SUB targets against this thread's rows; row minima into cm, per-target warp
 // minima and the ballot of the lanes holding them into smv / smb
 template <bool BIDIR>
@@ -108,43 +113,58 @@ __device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const fl
                                           const float2 (&ry)[PAIRS], const float2 (&rz)[PAIRS],
                                           float (&cm)[ROWS_PER_THREAD], unsigned* __restrict__ smv,
                                           unsigned* __restrict__ smb) {
-#pragma unroll 2
-    for (int jj = 0; jj < SUB; jj += 2) {
-        // targets j, j+1 as {-X_j, -X_j} and {-X_j+1, -X_j+1}
-        const float4 xq = *reinterpret_cast<const float4*>(tx + 2 * jj);
-        const float4 yq = *reinterpret_cast<const float4*>(ty + 2 * jj);
-        const float4 zq = *reinterpret_cast<const float4*>(tz + 2 * jj);
-        const float2 X0 = make_float2(xq.x, xq.y), X1 = make_float2(xq.z, xq.w);
-        const float2 Y0 = make_float2(yq.x, yq.y), Y1 = make_float2(yq.z, yq.w);
-        const float2 Z0 = make_float2(zq.x, zq.y), Z1 = make_float2(zq.z, zq.w);
-        float c0 = INFINITY, c1 = INFINITY;
+#pragma unroll(TPS == 2 ? 2 : 1)
+    for (int jj = 0; jj < SUB; jj += TPS) {
+        // targets jj..jj+TPS-1 as {-X_j, -X_j} pairs
+        float2 X[TPS], Y[TPS], Z[TPS];
+#pragma unroll
+        for (int t = 0; t < TPS; t += 2) {
+            const float4 xq = *reinterpret_cast<const float4*>(tx + 2 * (jj + t));
+            const float4 yq = *reinterpret_cast<const float4*>(ty + 2 * (jj + t));
+            const float4 zq = *reinterpret_cast<const float4*>(tz + 2 * (jj + t));
+            X[t] = make_float2(xq.x, xq.y);
+            X[t + 1] = make_float2(xq.z, xq.w);
+            Y[t] = make_float2(yq.x, yq.y);
+            Y[t + 1] = make_float2(yq.z, yq.w);
+            Z[t] = make_float2(zq.x, zq.y);
+            Z[t + 1] = make_float2(zq.z, zq.w);
+        }
+        float c[TPS];
+#pragma unroll
+        for (int t = 0; t < TPS; ++t) c[t] = INFINITY;
 #pragma unroll
         for (int p = 0; p < PAIRS; ++p) {
-            // x + (-X) rounds exactly like x - X
-            float2 dx = __fadd2_rn(rx[p], X0), dy = __fadd2_rn(ry[p], Y0),
-                   dz = __fadd2_rn(rz[p], Z0);
-            const float2 d0 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            dx = __fadd2_rn(rx[p], X1);
-            dy = __fadd2_rn(ry[p], Y1);
-            dz = __fadd2_rn(rz[p], Z1);
-            const float2 d1 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            cm[2 * p] = min3(cm[2 * p], d0.x, d1.x);
-            cm[2 * p + 1] = min3(cm[2 * p + 1], d0.y, d1.y);
+            float2 d[TPS];
+#pragma unroll
+            for (int t = 0; t < TPS; ++t) {
+                // x + (-X) rounds exactly like x - X
+                const float2 dx = __fadd2_rn(rx[p], X[t]), dy = __fadd2_rn(ry[p], Y[t]),
+                             dz = __fadd2_rn(rz[p], Z[t]);
+                d[t] = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            }
+#pragma unroll
+            for (int t = 0; t < TPS; t += 2) {
+                cm[2 * p] = min3(cm[2 * p], d[t].x, d[t + 1].x);
+                cm[2 * p + 1] = min3(cm[2 * p + 1], d[t].y, d[t + 1].y);
+            }
             if (BIDIR) {
-                c0 = min3(c0, d0.x, d0.y);
-                c1 = min3(c1, d1.x, d1.y);
+#pragma unroll
+                for (int t = 0; t < TPS; ++t) c[t] = min3(c[t], d[t].x, d[t].y);
             }
         }
         if (BIDIR) {
             // warp minimum of each target and the lanes holding it; every lane stores the
             // same value (no divergent branch); the first lane is taken later
-            const unsigned v0 = __float_as_uint(c0), v1 = __float_as_uint(c1);
-            const unsigned m0 = __reduce_min_sync(0xffffffffu, v0);
-            const unsigned m1 = __reduce_min_sync(0xffffffffu, v1);
-            const unsigned q0 = __ballot_sync(0xffffffffu, v0 == m0);
-            const unsigned q1 = __ballot_sync(0xffffffffu, v1 == m1);
-            *reinterpret_cast<uint2*>(smv + jj) = make_uint2(m0, m1);
-            *reinterpret_cast<uint2*>(smb + jj) = make_uint2(q0, q1);
+#pragma unroll
+            for (int t = 0; t < TPS; t += 2) {
+                const unsigned v0 = __float_as_uint(c[t]), v1 = __float_as_uint(c[t + 1]);
+                const unsigned m0 = __reduce_min_sync(0xffffffffu, v0);
+                const unsigned m1 = __reduce_min_sync(0xffffffffu, v1);
+                const unsigned q0 = __ballot_sync(0xffffffffu, v0 == m0);
+                const unsigned q1 = __ballot_sync(0xffffffffu, v1 == m1);
+                *reinterpret_cast<uint2*>(smv + jj + t) = make_uint2(m0, m1);
+                *reinterpret_cast<uint2*>(smb + jj + t) = make_uint2(q0, q1);
+            }
         }
     }
 }

@@ -34,22 +34,6 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
     s = t;
 }
 
-// G[v_c] += w_c * g for the three vertices of the face recorded in q = (f, w0, w1, w2)
-__device__ __forceinline__ void scatter(float* __restrict__ G, const int* __restrict__ faces,
-                                        int V, int4 q, float gx, float gy, float gz) {
-    const int f = q.x;
-    if (f < 0) return;
-    const float wc[3] = {__int_as_float(q.y), __int_as_float(q.z), __int_as_float(q.w)};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int v = faces[3 * f + c];
-        if ((unsigned)v >= (unsigned)V) continue;
-        atomicAdd(&G[3 * v + 0], __fmul_rn(wc[c], gx));
-        atomicAdd(&G[3 * v + 1], __fmul_rn(wc[c], gy));
-        atomicAdd(&G[3 * v + 2], __fmul_rn(wc[c], gz));
-    }
-}
-
 struct EpiArgs {
     int slices;
     int flags;     // EPI_RESCAN | EPI_LOSS | EPI_GRAD
@@ -83,8 +67,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
     const bool grad = (e.flags & EPI_GRAD) && fr->grad && fr->verts;
     const bool rescan = (e.flags & EPI_RESCAN) != 0, want_loss = (e.flags & EPI_LOSS) != 0;
     const int* faces = fr->faces;
-    const float* tgt = fr->tgt;
-
+    
     float* G = nullptr;
     if (grad) {
         if (e.use_smem) {
@@ -100,117 +83,139 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
     const float cab = e.bidir ? __fdiv_rn(__fmul_rn(2.0f, gs), (float)N) : __fmul_rn(2.0f, gs);
     const float cba = __fdiv_rn(__fmul_rn(2.0f, gs), (float)M);
 
-    // ---- sim points of this slice ----
-    // Each row's minimum points at one sub-chunk of SUB targets; the thread re-scans that
-    // window from the compact target planes, eight candidates per round of loads.
-    const int i0 = (int)((long long)N * sl / e.slices);
-    const int i1 = (int)((long long)N * (sl + 1) / e.slices);
-    const float* PX = w.tpl + 3LL * col0;
+    // ---- sim points of this slice, 8 rows per warp step, 4 lanes per row ----
+    // A row's minimum points at one sub-chunk of SUB (= 32) targets; lane q of the row's
+    // group checks candidates 8q..8q+7 with contiguous loads, and two xor-shuffles give the
+    // group the first candidate that matches. The three vertices of the gradient scatter go
+    // to lanes 0..2 of the group.
+    static_assert(SUB == 32, "four lanes of eight re-scan candidates per row");
+    const int lane = tid & 31, warp = tid >> 5, grp = lane >> 2, q = lane & 3;
+    constexpr int NW = EPI_THREADS / 32;
+    const float* PX = w.tpl + 3LL * col0;  // compact target planes X[Mpad], Y, Z
     const float* PY = PX + fr->Mpad;
     const float* PZ = PY + fr->Mpad;
+    const int i0 = (int)((long long)N * sl / e.slices);
+    const int i1 = (int)((long long)N * (sl + 1) / e.slices);
     float sab = 0.f, cab_c = 0.f;
-    for (int i = i0 + tid; i < i1; i += EPI_THREADS) {
-        const int g = row0 + i;
+    for (int base = i0 + warp * 8; base < i1; base += NW * 8) {
+        const int i = base + grp;
+        const bool valid = i < i1;
+        const int g = row0 + (valid ? i : i0);
         const float4 x = w.x[g];
         int nn = -1;
-        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+        float dmin = 0.f;
         if (rescan) {
-            const u64 p = w.pab[g];
+            const u64 p = valid ? w.pab[g] : EMPTY;
+            int first = 0x7fffffff;
             if (p != EMPTY) {
                 const unsigned dq = (unsigned)(p >> 32);
-                const int jb = (int)(p & 0xffffffffu) * SUB, je = min(jb + SUB, M);
-                for (int h = 0; h < SUB && nn < 0; h += 8) {
-                    // the window is 16-byte aligned: col0 and jb are multiples of 8 floats
-                    const float4 xa = *reinterpret_cast<const float4*>(PX + jb + h);
-                    const float4 xb = *reinterpret_cast<const float4*>(PX + jb + h + 4);
-                    const float4 ya = *reinterpret_cast<const float4*>(PY + jb + h);
-                    const float4 yb = *reinterpret_cast<const float4*>(PY + jb + h + 4);
-                    const float4 za = *reinterpret_cast<const float4*>(PZ + jb + h);
-                    const float4 zb = *reinterpret_cast<const float4*>(PZ + jb + h + 4);
-                    const float cx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-                    const float cy[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
-                    const float cz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+                dmin = __uint_as_float(dq);
+                const int jb = (int)(p & 0xffffffffu) * SUB + 8 * q;
+                const float4 xa = *reinterpret_cast<const float4*>(PX + jb);
+                const float4 xb = *reinterpret_cast<const float4*>(PX + jb + 4);
+                const float4 ya = *reinterpret_cast<const float4*>(PY + jb);
+                const float4 yb = *reinterpret_cast<const float4*>(PY + jb + 4);
+                const float4 za = *reinterpret_cast<const float4*>(PZ + jb);
+                const float4 zb = *reinterpret_cast<const float4*>(PZ + jb + 4);
+                const float cx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                const float cy[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                const float cz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const int j = jb + h + t;
-                        if (nn < 0 && j < je &&
-                            __float_as_uint(dist2(x.x, x.y, x.z, cx[t], cy[t], cz[t])) == dq) {
-                            nn = j;
-                            y0 = cx[t];
-                            y1 = cy[t];
-                            y2 = cz[t];
-                        }
-                    }
-                }
-                if (want_loss) kahan_add(sab, cab_c, __uint_as_float(dq));
+                for (int t = 7; t >= 0; --t)
+                    if (jb + t < M &&
+                        __float_as_uint(dist2(x.x, x.y, x.z, cx[t], cy[t], cz[t])) == dq)
+                        first = jb + t;
             }
-            if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
-            fr->nn_ab[i] = nn;
-        } else {
+            first = min(first, __shfl_xor_sync(0xffffffffu, first, 1));
+            first = min(first, __shfl_xor_sync(0xffffffffu, first, 2));
+            if (valid && p != EMPTY) nn = first == 0x7fffffff ? -1 : first;
+            if (valid && q == 0) {
+                if (p != EMPTY && want_loss) kahan_add(sab, cab_c, dmin);
+                if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
+                fr->nn_ab[i] = nn;
+            }
+        } else if (valid) {
             nn = fr->nn_ab[i];
-            if ((unsigned)nn < (unsigned)M) {
-                const float* y = tgt + 3LL * nn;
-                y0 = y[0];
-                y1 = y[1];
-                y2 = y[2];
-            } else {
-                set_status(&w.hdr->status, DC_EINVAL);
+            if ((unsigned)nn >= (unsigned)M) {
+                if (q == 0) set_status(&w.hdr->status, DC_EINVAL);
                 nn = -1;
             }
         }
-        if (grad && nn >= 0)
-            scatter(G, faces, V, w.fw[g], __fmul_rn(cab, __fsub_rn(x.x, y0)),
-                    __fmul_rn(cab, __fsub_rn(x.y, y1)), __fmul_rn(cab, __fsub_rn(x.z, y2)));
+        if (grad && valid && nn >= 0 && q < 3) {
+            const float y0 = PX[nn], y1 = PY[nn], y2 = PZ[nn];
+            const int4 fq = w.fw[g];
+            if (fq.x >= 0) {
+                const int v = faces[3 * fq.x + q];
+                const float wq = __int_as_float(q == 0 ? fq.y : (q == 1 ? fq.z : fq.w));
+                if ((unsigned)v < (unsigned)V) {
+                    atomicAdd(&G[3 * v + 0], __fmul_rn(wq, __fmul_rn(cab, __fsub_rn(x.x, y0))));
+                    atomicAdd(&G[3 * v + 1], __fmul_rn(wq, __fmul_rn(cab, __fsub_rn(x.y, y1))));
+                    atomicAdd(&G[3 * v + 2], __fmul_rn(wq, __fmul_rn(cab, __fsub_rn(x.z, y2))));
+                }
+            }
+        }
     }
 
-    // ---- target points of this slice (Eq. 1 only) ----
-    // A target's minimum points at one thread's group of ROWS_PER_THREAD sim points; the
-    // candidates are loaded eight at a time before any comparison.
+    // ---- target points of this slice (Eq. 1 only), 8 per warp step, 4 lanes per target ----
+    // A target's minimum points at one thread's group of ROWS_PER_THREAD (= 16) sim points:
+    // lane q of the target's group checks rows 4q..4q+3 of it.
+    static_assert(ROWS_PER_THREAD == 16, "four lanes of four re-scan candidates per target");
     float sba = 0.f, cba_c = 0.f;
     if (e.bidir) {
         const int j0 = (int)((long long)M * sl / e.slices);
         const int j1 = (int)((long long)M * (sl + 1) / e.slices);
-        for (int j = j0 + tid; j < j1; j += EPI_THREADS) {
-            const float* y = tgt + 3LL * j;
-            const float y0 = y[0], y1 = y[1], y2 = y[2];
+        for (int base = j0 + warp * 8; base < j1; base += NW * 8) {
+            const int j = base + grp;
+            const bool valid = j < j1;
+            const int jj = valid ? j : j0;
+            const float tx = PX[jj], ty = PY[jj], tz = PZ[jj];
             int nn = -1;
-            float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
+            float dmin = 0.f;
             if (rescan) {
-                const u64 p = w.pba[col0 + j];
+                const u64 p = valid ? w.pba[col0 + jj] : EMPTY;
+                int first = 0x7fffffff;
                 if (p != EMPTY) {
                     const unsigned dq = (unsigned)(p >> 32);
-                    const int rb = (int)(p & 0xffffffffu) * ROWS_PER_THREAD;
-                    for (int h = 0; h < ROWS_PER_THREAD && nn < 0; h += 8) {
-                        float4 xr[8];
+                    dmin = __uint_as_float(dq);
+                    const int rb = (int)(p & 0xffffffffu) * ROWS_PER_THREAD + 4 * q;
+                    float4 xr[4];
 #pragma unroll
-                        for (int t = 0; t < 8; ++t)
-                            xr[t] = h + t < ROWS_PER_THREAD && rb + h + t < N
-                                        ? w.x[row0 + rb + h + t]
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int t = 0; t < 4; ++t)
+                        xr[t] = w.x[row0 + min(rb + t, N - 1)];
 #pragma unroll
-                        for (int t = 0; t < 8; ++t)
-                            if (nn < 0 && h + t < ROWS_PER_THREAD && rb + h + t < N &&
-                                __float_as_uint(dist2(xr[t].x, xr[t].y, xr[t].z, y0, y1, y2)) == dq) {
-                                nn = rb + h + t;
-                                xm = xr[t];
-                            }
-                    }
-                    if (want_loss) kahan_add(sba, cba_c, __uint_as_float(dq));
+                    for (int t = 3; t >= 0; --t)
+                        if (rb + t < N &&
+                            __float_as_uint(dist2(xr[t].x, xr[t].y, xr[t].z, tx, ty, tz)) == dq)
+                            first = rb + t;
                 }
-                if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
-                fr->nn_ba[j] = nn;
-            } else {
+                first = min(first, __shfl_xor_sync(0xffffffffu, first, 1));
+                first = min(first, __shfl_xor_sync(0xffffffffu, first, 2));
+                if (valid && p != EMPTY) nn = first == 0x7fffffff ? -1 : first;
+                if (valid && q == 0) {
+                    if (p != EMPTY && want_loss) kahan_add(sba, cba_c, dmin);
+                    if (nn < 0) set_status(&w.hdr->status, DC_EDEVICE);
+                    fr->nn_ba[j] = nn;
+                }
+            } else if (valid) {
                 nn = fr->nn_ba[j];
-                if ((unsigned)nn < (unsigned)N) {
-                    xm = w.x[row0 + nn];
-                } else {
-                    set_status(&w.hdr->status, DC_EINVAL);
+                if ((unsigned)nn >= (unsigned)N) {
+                    if (q == 0) set_status(&w.hdr->status, DC_EINVAL);
                     nn = -1;
                 }
             }
-            if (grad && nn >= 0)
-                scatter(G, faces, V, w.fw[row0 + nn], __fmul_rn(cba, __fsub_rn(xm.x, y0)),
-                        __fmul_rn(cba, __fsub_rn(xm.y, y1)), __fmul_rn(cba, __fsub_rn(xm.z, y2)));
+            if (grad && valid && nn >= 0 && q < 3) {
+                const float4 xm = w.x[row0 + nn];
+                const int4 fq = w.fw[row0 + nn];
+                if (fq.x >= 0) {
+                    const int v = faces[3 * fq.x + q];
+                    const float wq = __int_as_float(q == 0 ? fq.y : (q == 1 ? fq.z : fq.w));
+                    if ((unsigned)v < (unsigned)V) {
+                        atomicAdd(&G[3 * v + 0], __fmul_rn(wq, __fmul_rn(cba, __fsub_rn(xm.x, tx))));
+                        atomicAdd(&G[3 * v + 1], __fmul_rn(wq, __fmul_rn(cba, __fsub_rn(xm.y, ty))));
+                        atomicAdd(&G[3 * v + 2], __fmul_rn(wq, __fmul_rn(cba, __fsub_rn(xm.z, tz))));
+                    }
+                }
+            }
         }
     }
 
