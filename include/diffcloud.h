@@ -103,7 +103,9 @@ int dc_chamfer_bwd(const float* a, const float* b, const int32_t* nn_ab, const i
 /*
  * dc_loss_traj -- the whole loss over a trajectory, and optionally its vertex gradient
  * (Sec. III-B, Eq. 1-4; the per-frame loss of Sec. III-C).
- *   frame_w     [T] nullable (all ones): weights w_t.
+ *   frame_w     [T] nullable (all ones): weights w_t. A frame whose weight is 0 is skipped:
+ *               no sampling, Chamfer or gradient work is done for it, its L_t is reported as
+ *               0 and its gradient rows are 0 (the paper mostly optimises one frame, Sec. III-C).
  *   loss_total  [1] out, nullable: sum_t w_t L_t (fixed summation order).
  *   loss_frames [T] out: L_t.
  *   grad_verts  [T][V][3] out, nullable: w_t dL_t/dverts_t (overwritten). When NULL only
@@ -121,7 +123,8 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
  * dc_loss_traj_bwd -- vertex gradient of sum_t g_t L_t given the neighbours a previous
  * dc_loss_traj returned. The sampled points are recomputed from the draws (nothing from
  * the forward is stored but nn_ab / nn_ba).
- *   grad_frames [T]: g_t = dObjective/dL_t.   grad_verts [T][V][3] out, overwritten.
+ *   grad_frames [T]: g_t = dObjective/dL_t; frames with g_t = 0 are skipped (zero rows).
+ *   grad_verts [T][V][3] out, overwritten.
  */
 int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draws,
                      const float* targets, int T, int V, int F, int N, int M, int mode,
@@ -138,7 +141,8 @@ typedef struct dc_frame {
     const float* draws;   /* [N][3] */
     const float* targets; /* [M][3] */
     int32_t V, F, N, M;
-    float weight;         /* w: weight of L in loss_total and multiplier of its gradient */
+    float weight;         /* w: weight of L in loss_total and multiplier of its gradient;
+                             0 skips the frame (L reported as 0, gradient 0) */
     int32_t tag;          /* caller's label (e.g. trajectory id); not read by the library */
     float* loss;          /* [1] out: L */
     float* grad_verts;    /* [V][3] out, overwritten; NULL: no gradient for this frame */

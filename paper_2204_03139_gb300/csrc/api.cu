@@ -489,6 +489,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
         d.M = f.M;
         d.weight = f.weight;
         d.gscale = f.weight;
+        d.skip = f.weight == 0.0f;
         d.row0 = row0;
         d.col0 = col0;
         d.cdf0 = cdf0;
@@ -496,7 +497,8 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
         fd[k] = d;
         rowpre[k] = row0;
         colpre[k] = col0;
-        const int upf = div_up(f.N, ROWS_PER_WARP * warps), spu = div_up(f.M, SUB);
+        const int upf = div_up(f.N, ROWS_PER_WARP * warps);
+        const int spu = d.skip ? 0 : div_up(f.M, SUB);  // a skipped frame carries no work
         for (int r = 0; r < upf; ++r, ++unit) {
             ufr[unit] = k;
             urb[unit] = r;

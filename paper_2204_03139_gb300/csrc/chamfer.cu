@@ -177,7 +177,7 @@ struct MinBlocks {
 
 template <bool BIDIR, int W>
 __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
-    k_chamfer(Ws w, int n_units, int total_sub) {
+    k_chamfer(Ws w) {
     constexpr int THREADS = 32 * W;
     constexpr int WARPS = W;
     constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * W;
@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
     __shared__ __align__(8) u64 s_bar[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the work (units, and their sub-chunks without those of skipped frames) was laid out on
+    // the device or by the plan
+    const int n_units = w.hdr->n_units, total_sub = w.hdr->total_sub;
     const int per = (total_sub + gridDim.x - 1) / gridDim.x;
     int s = blockIdx.x * per;
     const int s_end = min(total_sub, s + per);
@@ -399,20 +402,22 @@ int choose_warps(int mode, long long sub_w4, long long sub_w2, long long sub_w1)
 
 cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, int warps,
                            cudaStream_t s) {
-    if (total_sub <= 0) return cudaSuccess;
+    // total_sub is an upper bound here (frames skipped on the device carry no work); CTAs
+    // beyond the work exit at once
+    if (n_units <= 0 || total_sub <= 0) return cudaSuccess;
     int grid = chamfer_grid(mode, warps);
     if (grid > total_sub) grid = total_sub;
     prof_before(s);
     const bool bi = mode == DC_BIDIR_MEAN;
     if (warps == 4) {
-        if (bi) k_chamfer<true, 4><<<grid, 128, 0, s>>>(w, n_units, total_sub);
-        else k_chamfer<false, 4><<<grid, 128, 0, s>>>(w, n_units, total_sub);
+        if (bi) k_chamfer<true, 4><<<grid, 128, 0, s>>>(w);
+        else k_chamfer<false, 4><<<grid, 128, 0, s>>>(w);
     } else if (warps == 2) {
-        if (bi) k_chamfer<true, 2><<<grid, 64, 0, s>>>(w, n_units, total_sub);
-        else k_chamfer<false, 2><<<grid, 64, 0, s>>>(w, n_units, total_sub);
+        if (bi) k_chamfer<true, 2><<<grid, 64, 0, s>>>(w);
+        else k_chamfer<false, 2><<<grid, 64, 0, s>>>(w);
     } else {
-        if (bi) k_chamfer<true, 1><<<grid, 32, 0, s>>>(w, n_units, total_sub);
-        else k_chamfer<false, 1><<<grid, 32, 0, s>>>(w, n_units, total_sub);
+        if (bi) k_chamfer<true, 1><<<grid, 32, 0, s>>>(w);
+        else k_chamfer<false, 1><<<grid, 32, 0, s>>>(w);
     }
     prof_after(s);
     count_launch();

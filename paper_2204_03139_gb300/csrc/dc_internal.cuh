@@ -60,6 +60,7 @@ struct FrameDesc {
     int col0;             // offset of this frame's targets in the padded column buffers
     int cdf0;             // offset of this frame's CDF
     int unit0;            // first Chamfer unit of this frame
+    int skip;             // weight (or gradient multiplier) 0: no work, L reported as 0
 };
 
 // Header at the start of every workspace.

@@ -63,6 +63,13 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
     const int k = blockIdx.x / e.slices, sl = blockIdx.x - k * e.slices;
     const int tid = threadIdx.x;
     const FrameDesc* fr = w.frames + k;
+    if (fr->skip) {  // weight 0: nothing to recover, L reported as 0, gradient left at 0
+        if (tid == 0 && (e.flags & EPI_LOSS)) {
+            w.part[2 * (k * e.slices + sl)] = 0.0f;
+            w.part[2 * (k * e.slices + sl) + 1] = 0.0f;
+        }
+        return;
+    }
     const int N = fr->N, M = fr->M, V = fr->V, row0 = fr->row0, col0 = fr->col0;
     const bool grad = (e.flags & EPI_GRAD) && fr->grad && fr->verts;
     const bool rescan = (e.flags & EPI_RESCAN) != 0, want_loss = (e.flags & EPI_LOSS) != 0;
@@ -240,7 +247,7 @@ __global__ void __launch_bounds__(256) k_grad_reduce(Ws w, int n_frames, int sli
     for (long long t = blockIdx.x * 256LL + threadIdx.x; t < n; t += (long long)gridDim.x * 256) {
         const int k = (int)(t / vstride), v = (int)(t - (long long)k * vstride);
         const FrameDesc* fr = w.frames + k;
-        if (!fr->grad || !fr->verts || v >= 3 * fr->V) continue;
+        if (!fr->grad || !fr->verts || fr->skip || v >= 3 * fr->V) continue;
         const float* src = w.gscr + (size_t)k * slices * vstride + v;
         float s = 0.f;
         for (int q = 0; q < slices; ++q) s = __fadd_rn(s, src[(size_t)q * vstride]);

@@ -28,19 +28,78 @@ __device__ __forceinline__ int last_le(const int* pre, int n, int g) {
 __device__ __forceinline__ bool coord_ok(float v) { return fabsf(v) <= COORD_MAX; }
 
 // ---------------------------------------------------------------------------------------
-// uniform trajectory -> frame table, row/column prefixes and Chamfer units
+// uniform trajectory -> frame table, row/column prefixes and Chamfer units. One block: the
+// Chamfer work of a frame whose weight (or gradient multiplier) is 0 is left out, which
+// needs a prefix count of the live frames.
 // ---------------------------------------------------------------------------------------
-__global__ void k_build_uniform(UniformArgs a, Ws w) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int BUILD_THREADS = 1024;
+
+__global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, Ws w) {
+    __shared__ int s_warp[BUILD_THREADS / 32];
+    __shared__ int s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Npad = ((a.N + ROW_PAD - 1) / ROW_PAD) * ROW_PAD;
     const int Mpad = ((a.M + COL_PAD - 1) / COL_PAD) * COL_PAD;
-    const int n_units = a.T * a.units_per_frame;
-    if (g == 0) {
+    const int upf = a.units_per_frame, spu = a.subs_per_unit;
+    const int n_units = a.T * upf;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    // frames, in chunks of BUILD_THREADS, with a running count of live frames
+    for (int k0 = 0; k0 < a.T; k0 += BUILD_THREADS) {
+        const int k = k0 + tid;
+        bool live = false;
+        if (k < a.T) {
+            FrameDesc f;
+            f.verts = a.verts ? a.verts + 3LL * k * a.V : nullptr;
+            f.faces = a.faces;
+            f.draws = a.draws ? a.draws + 3LL * k * a.N : nullptr;
+            f.pts = a.pts ? a.pts + 3LL * k * a.N : nullptr;
+            f.tgt = a.tgt ? a.tgt + 3LL * k * a.M : nullptr;
+            f.loss = a.loss ? a.loss + k : w.loss + k;
+            f.nn_ab = a.nn_ab ? a.nn_ab + (long long)k * a.N : w.nnab + (long long)k * Npad;
+            f.nn_ba = a.nn_ba ? a.nn_ba + (long long)k * a.M : w.nnba + (long long)k * Mpad;
+            f.grad = a.grad ? a.grad + 3LL * k * a.V : nullptr;
+            f.out_pts = a.out_pts ? a.out_pts + 3LL * k * a.N : nullptr;
+            f.out_face = a.out_face ? a.out_face + (long long)k * a.N : nullptr;
+            f.out_bary = a.out_bary ? a.out_bary + 3LL * k * a.N : nullptr;
+            f.V = a.V;
+            f.F = a.F;
+            f.N = a.N;
+            f.M = a.M;
+            f.Npad = Npad;
+            f.Mpad = Mpad;
+            f.weight = a.weight ? a.weight[k] : 1.0f;
+            f.gscale = a.gscale ? a.gscale[k] : f.weight;
+            f.skip = f.weight == 0.0f || f.gscale == 0.0f;
+            live = !f.skip;
+            f.row0 = k * Npad;
+            f.col0 = k * Mpad;
+            f.cdf0 = k * a.F;
+            f.unit0 = 0;  // set below: live frames before this one
+            w.frames[k] = f;
+            w.rowpre[k] = k * Npad;
+            w.colpre[k] = k * Mpad;
+        }
+        // exclusive prefix of live flags over the chunk
+        const unsigned bal = __ballot_sync(0xffffffffu, live);
+        const int in_warp = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        int before = s_carry;
+        for (int q = 0; q < warp; ++q) before += s_warp[q];
+        if (k < a.T) w.frames[k].unit0 = before + in_warp;
+        __syncthreads();
+        if (tid == BUILD_THREADS - 1) s_carry = before + in_warp + (live ? 1 : 0);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        w.rowpre[a.T] = a.T * Npad;
+        w.colpre[a.T] = a.T * Mpad;
         WsHeader* h = w.hdr;
         h->status = DC_OK;
         h->n_frames = a.T;
         h->n_units = n_units;
-        h->total_sub = n_units * a.subs_per_unit;
+        h->total_sub = s_carry * upf * spu;
         h->total_rows = a.T * Npad;
         h->total_cols = a.T * Mpad;
         h->sum_f = a.T * a.F;
@@ -51,44 +110,22 @@ __global__ void k_build_uniform(UniformArgs a, Ws w) {
         h->slices = a.slices;
         h->warps = a.warps;
     }
-    if (g <= a.T) {
-        w.rowpre[g] = g * Npad;
-        w.colpre[g] = g * Mpad;
+    __syncthreads();  // the frames' live counts are written
+    // units: a skipped frame's units carry no sub-chunks
+    for (int u = tid; u <= n_units; u += BUILD_THREADS) {
+        if (u == n_units) {
+            w.unit_pre[u] = s_carry * upf * spu;
+            continue;
+        }
+        const int k = u / upf, rb = u - k * upf;
+        const FrameDesc* f = w.frames + k;
+        w.unit_frame[u] = k;
+        w.unit_rb[u] = rb;
+        w.unit_pre[u] = (f->unit0 * upf + (f->skip ? 0 : rb)) * spu;
     }
-    if (g < a.T) {
-        const int k = g;
-        FrameDesc f;
-        f.verts = a.verts ? a.verts + 3LL * k * a.V : nullptr;
-        f.faces = a.faces;
-        f.draws = a.draws ? a.draws + 3LL * k * a.N : nullptr;
-        f.pts = a.pts ? a.pts + 3LL * k * a.N : nullptr;
-        f.tgt = a.tgt ? a.tgt + 3LL * k * a.M : nullptr;
-        f.loss = a.loss ? a.loss + k : w.loss + k;
-        f.nn_ab = a.nn_ab ? a.nn_ab + (long long)k * a.N : w.nnab + (long long)k * Npad;
-        f.nn_ba = a.nn_ba ? a.nn_ba + (long long)k * a.M : w.nnba + (long long)k * Mpad;
-        f.grad = a.grad ? a.grad + 3LL * k * a.V : nullptr;
-        f.out_pts = a.out_pts ? a.out_pts + 3LL * k * a.N : nullptr;
-        f.out_face = a.out_face ? a.out_face + (long long)k * a.N : nullptr;
-        f.out_bary = a.out_bary ? a.out_bary + 3LL * k * a.N : nullptr;
-        f.V = a.V;
-        f.F = a.F;
-        f.N = a.N;
-        f.M = a.M;
-        f.Npad = Npad;
-        f.Mpad = Mpad;
-        f.weight = a.weight ? a.weight[k] : 1.0f;
-        f.gscale = a.gscale ? a.gscale[k] : f.weight;
-        f.row0 = k * Npad;
-        f.col0 = k * Mpad;
-        f.cdf0 = k * a.F;
-        f.unit0 = k * a.units_per_frame;
-        w.frames[k] = f;
-    }
-    if (g <= n_units) w.unit_pre[g] = g * a.subs_per_unit;
-    if (g < n_units) {
-        w.unit_frame[g] = g / a.units_per_frame;
-        w.unit_rb[g] = g % a.units_per_frame;
-    }
+    // unit0 now holds "live frames before"; restore its documented meaning
+    __syncthreads();
+    for (int k = tid; k < a.T; k += BUILD_THREADS) w.frames[k].unit0 = k * upf;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -157,6 +194,11 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
     const FrameDesc* fr = w.frames + blockIdx.x;
     const float* verts = fr->verts;
     if (!verts) return;
+    if (fr->skip) {  // no sampling for this frame: only its gradient (zero) is written
+        if (fr->grad)
+            for (int e = threadIdx.x; e < 3 * fr->V; e += CDF_THREADS) fr->grad[e] = 0.0f;
+        return;
+    }
     const int* faces = fr->faces;
     const int F = fr->F, V = fr->V;
     float* cdf = w.cdf + fr->cdf0;
@@ -302,7 +344,7 @@ __global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.rowpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
-        sample_row(w, fr, g - fr->row0, g, w.cdf + fr->cdf0);
+        if (!fr->skip) sample_row(w, fr, g - fr->row0, g, w.cdf + fr->cdf0);
     }
 }
 
@@ -310,7 +352,7 @@ __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < cols; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.colpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
-        stage_target(w, fr, g - fr->col0, g);
+        if (!fr->skip) stage_target(w, fr, g - fr->col0, g);
     }
 }
 
@@ -322,6 +364,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int r
     extern __shared__ float s_cdf[];
     const int k = blockIdx.x / slices, sl = blockIdx.x - k * slices;
     const FrameDesc* fr = w.frames + k;
+    if (fr->skip) return;
     const bool sampled = fr->verts && !fr->pts;
     if (sampled)
         for (int f = threadIdx.x; f < fr->F; f += STAGE_THREADS) s_cdf[f] = w.cdf[fr->cdf0 + f];
@@ -350,9 +393,7 @@ int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s) {
-    const long long n = 1 + (long long)(a.T > a.T * a.units_per_frame ? a.T
-                                                                        : a.T * a.units_per_frame);
-    k_build_uniform<<<grid_for(n, 256), 256, 0, s>>>(a, w);
+    k_build_uniform<<<1, BUILD_THREADS, 0, s>>>(a, w);
     count_launch();
     return cudaGetLastError();
 }

@@ -49,6 +49,25 @@ def test_batch_matches_oracle(trajs, graph, mode):
     parity.check_loss([float(total[0])], [ref_total], what="batch total")
 
 
+def test_batch_skips_zero_weight_frames(trajs):
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
+
+    dts = [DeviceTrajectory.from_host(t, DEV) for t in trajs]
+    weights = [np.where(np.arange(t.T) % 2 == 0, 0.0, 1.0) for t in trajs]
+    b = BatchedLoss(dts, weights=weights, grad=True)
+    b.run(check=True)
+    torch.cuda.synchronize()
+    for k, t in enumerate(trajs):
+        live = [f for f in range(t.T) if weights[k][f] != 0.0]
+        dead = [f for f in range(t.T) if weights[k][f] == 0.0]
+        ref = oracle.loss_traj(t, weights=weights[k], frames=live)
+        lf = b.loss_frames[k].cpu().numpy()
+        gv = b.grad_verts[k].cpu().numpy()
+        parity.check_loss(lf[live], ref["loss_frames"][live])
+        parity.check_grad(gv[live], ref["grad_verts"][live])
+        assert np.all(lf[dead] == 0.0) and np.all(gv[dead] == 0.0)
+
+
 def test_batch_equals_per_frame_form(trajs):
     from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory, per_frame_loss
 

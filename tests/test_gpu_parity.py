@@ -85,10 +85,39 @@ def test_trajectory_50x50_full_size_sampled_frames():
 
 def test_trajectory_50x50_weights_total():
     tr, _ = parity.nudge_draws(W.trajectory_50x50(T=4, n=3000, m=2500))
-    w = [0.0, 0.5, 1.0, 2.0]
+    w = [0.25, 0.5, 1.0, 2.0]
     g = run_traj(tr, frame_w=w)
     ref = oracle.loss_traj(tr, weights=w)
     compare_traj(tr, g, ref, list(range(tr.T)), weights=w)
+
+
+@pytest.mark.parametrize("w", [[0.0, 0.0, 0.0, 1.0], [0.0, 1.5, 0.0, 0.5], [1.0, 0.0, 2.0, 0.0]])
+def test_zero_weight_frames_are_skipped(w):
+    """Frames of weight 0 (e.g. last-frame-only, as the paper mostly optimises) do no work:
+    their L_t is reported as 0 and their gradient is 0; the other frames are unchanged."""
+    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=4, n=3000, m=2500))
+    g = run_traj(tr, frame_w=w)
+    live = [t for t in range(4) if w[t] != 0.0]
+    dead = [t for t in range(4) if w[t] == 0.0]
+    ref = oracle.loss_traj(tr, weights=w, frames=live)
+    for t in live:
+        parity.check_nn(g["nn_ab"][t], ref["frames"][t]["nn_ab"], g["nn_ba"][t],
+                        ref["frames"][t]["nn_ba"])
+    parity.check_loss(g["loss_frames"][live], ref["loss_frames"][live])
+    parity.check_grad(g["grad_verts"][live], ref["grad_verts"][live])
+    parity.check_loss(g["loss_total"], [np.nansum(np.asarray(w) * ref["loss_frames"])],
+                      what="total")
+    assert np.all(g["loss_frames"][dead] == 0.0)
+    assert np.all(g["grad_verts"][dead] == 0.0)
+    # the backward-only call skips frames whose upstream gradient is 0 the same way
+    v, f, d, y = to_dev(tr)
+    r = L().dc_loss_traj(v, f, d, y, check=True)
+    gb = L().dc_loss_traj_bwd(v, f, d, y, r["nn_ab"], r["nn_ba"],
+                              torch.tensor(w, dtype=torch.float32, device=DEV), check=True)
+    torch.cuda.synchronize()
+    gb = gb.cpu().numpy()
+    assert np.all(gb[dead] == 0.0)
+    assert parity.rel_l2(gb[live], g["grad_verts"][live]) < 1e-6
 
 
 @pytest.mark.slow
