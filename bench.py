@@ -30,9 +30,10 @@ import workloads  # noqa: E402
 
 FLOP_PER_PAIR = 8        # 3 sub + 3 mul/fma products + 2 adds per distance, shared by both directions
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_chamfer launch on this workload, from
-# the ncu capture summarised in profiles/; None until measured for the current kernel.
-CHAMFER_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_chamfer launch on the default workload
+# (trajectory_50x50, 40 frames), from the one-pass ncu capture summarised in
+# profiles/k_chamfer_trajectory_50x50.md (22.84 MB read, 0 written); None for other workloads.
+CHAMFER_TRAFFIC_BYTES = {"trajectory_50x50": 22.84e6}
 
 
 def parse():
@@ -154,9 +155,10 @@ def cpu_baseline(tr, seconds):
     el = time.perf_counter() - t0
     return {"value": pairs / el, "unit": "pairs/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": f"{k} frames of {tr.name}, each cut to its first {n_s} draws and first "
-                      f"{n_s} targets (loss + vertex gradient, FP64 with float32 neighbour "
-                      f"decisions), {el:.1f} s"}
+            "sample": f"{k} frame evaluations of {tr.name} (frame k mod {tr.T}), each with its "
+                      f"first {n_s} draws and first {n_s} targets"
+                      f"{' (the whole frame)' if n_s >= min(tr.n(0), tr.m(0)) else ''}: loss + "
+                      f"vertex gradient, FP64 with float32 neighbour decisions, {el:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -307,7 +309,8 @@ def run_gpu(args, rank, world, dist):
     achieved = FLOP_PER_PAIR * pairs / chamfer_avg_s / 1e12 if chamfer_n else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": (achieved / peak_tflops) if (achieved and peak_tflops) else None,
-            "traffic": CHAMFER_TRAFFIC_BYTES, "kernel": "k_chamfer<true>",
+            "traffic": (CHAMFER_TRAFFIC_BYTES.get(args.workload) if args.frames is None
+                        else None), "kernel": "k_chamfer<true>",
             "peak_basis": f"FP32 FMA peak 2 x {FP32_LANES_PER_SM} lanes x {sms} SMs x median "
                           f"SM clock under load ({sm_mhz:.0f} MHz); at the {sm_max:.0f} MHz "
                           f"maximum it is "

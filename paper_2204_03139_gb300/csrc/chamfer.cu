@@ -169,10 +169,16 @@ __device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const fl
     }
 }
 
-// resident CTAs per SM the register budget is sized for, per CTA width
+// resident CTAs per SM the register budget is sized for, per CTA width: 12 warps per SM with
+// 16 rows per thread, 16 warps with fewer (fewer row registers)
 template <int W>
 struct MinBlocks {
-    static constexpr int value = W == 4 ? 3 : (W == 2 ? 6 : 12);
+#ifdef DC_WARPS_PER_SM
+    static constexpr int warps_per_sm = DC_WARPS_PER_SM;
+#else
+    static constexpr int warps_per_sm = ROWS_PER_THREAD >= 16 ? 12 : 16;
+#endif
+    static constexpr int value = warps_per_sm / W;
 };
 
 template <bool BIDIR, int W>

@@ -164,9 +164,10 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
     }
 
     // ---- target points of this slice (Eq. 1 only), 8 per warp step, 4 lanes per target ----
-    // A target's minimum points at one thread's group of ROWS_PER_THREAD (= 16) sim points:
-    // lane q of the target's group checks rows 4q..4q+3 of it.
-    static_assert(ROWS_PER_THREAD == 16, "four lanes of four re-scan candidates per target");
+    // A target's minimum points at one thread's group of ROWS_PER_THREAD sim points: lane q
+    // of the target's group checks rows RPL q .. RPL q + RPL - 1 of it.
+    static_assert(ROWS_PER_THREAD % 4 == 0, "four lanes share a row group");
+    constexpr int RPL = ROWS_PER_THREAD / 4;
     float sba = 0.f, cba_c = 0.f;
     if (e.bidir) {
         const int j0 = (int)((long long)M * sl / e.slices);
@@ -184,13 +185,13 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
                 if (p != EMPTY) {
                     const unsigned dq = (unsigned)(p >> 32);
                     dmin = __uint_as_float(dq);
-                    const int rb = (int)(p & 0xffffffffu) * ROWS_PER_THREAD + 4 * q;
-                    float4 xr[4];
+                    const int rb = (int)(p & 0xffffffffu) * ROWS_PER_THREAD + RPL * q;
+                    float4 xr[RPL];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t)
+                    for (int t = 0; t < RPL; ++t)
                         xr[t] = w.x[row0 + min(rb + t, N - 1)];
 #pragma unroll
-                    for (int t = 3; t >= 0; --t)
+                    for (int t = RPL - 1; t >= 0; --t)
                         if (rb + t < N &&
                             __float_as_uint(dist2(xr[t].x, xr[t].y, xr[t].z, tx, ty, tz)) == dq)
                             first = rb + t;
