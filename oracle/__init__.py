@@ -49,13 +49,15 @@ def lib() -> ctypes.CDLL:
         I = ctypes.c_int
         D = ctypes.c_double
         _lib.orc_frame.restype = I
-        _lib.orc_frame.argtypes = [P, P, I, I, P, I, P, I, I, D, I] + [P] * 16
+        _lib.orc_frame.argtypes = [P, P, P, I, I, P, I, P, I, I, D, I] + [P] * 16
         _lib.orc_chamfer.restype = I
         _lib.orc_chamfer.argtypes = [P, I, P, I, I, D, P, P]
         _lib.orc_nn_pair.restype = None
         _lib.orc_nn_pair.argtypes = [P, I, P, I, P, P, P, P, P, P]
         _lib.orc_face_areas.restype = None
         _lib.orc_face_areas.argtypes = [P, P, I, P]
+        _lib.orc_mask_areas.restype = None
+        _lib.orc_mask_areas.argtypes = [P, P, I]
         _lib.orc_area_cdf.restype = None
         _lib.orc_area_cdf.argtypes = [P, I, P]
         _lib.orc_pick_face.restype = I
@@ -84,10 +86,14 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def face_areas(verts, faces) -> np.ndarray:
+def face_areas(verts, faces, face_mask=None) -> np.ndarray:
+    """Face areas; with a mask, the area weights of faces outside the subset are 0."""
     v, f = _c(verts, np.float32), _c(faces, np.int32)
     out = np.empty(f.shape[0], np.float64)
     lib().orc_face_areas(_p(v), _p(f), f.shape[0], _p(out))
+    if face_mask is not None:
+        m = _c(face_mask, np.uint8)
+        lib().orc_mask_areas(_p(out), _p(m), f.shape[0])
     return out
 
 
@@ -112,9 +118,14 @@ def bary(r1: float, r2: float) -> np.ndarray:
 
 
 def frame(verts, faces, draws, tgt, mode: int = BIDIR_MEAN, gscale: float = 1.0,
-          exact64: bool = False, details: bool = True, grads: bool = True) -> dict:
-    """One frame: loss, gradients and every intermediate (see orc_frame)."""
+          exact64: bool = False, details: bool = True, grads: bool = True,
+          face_mask=None) -> dict:
+    """One frame: loss, gradients and every intermediate (see orc_frame). face_mask [F]:
+    sample only the faces with a nonzero entry."""
     v, f = _c(verts, np.float32), _c(faces, np.int32)
+    fm = None if face_mask is None else _c(face_mask, np.uint8)
+    if fm is not None and fm.shape != (f.shape[0],):
+        raise ValueError("face_mask must have one entry per face")
     d, y = _c(draws, np.float32), _c(tgt, np.float32)
     V, F, N, M = v.shape[0], f.shape[0], d.shape[0], y.shape[0]
     out = {"loss": np.zeros(1), "loss_exact": np.full(1, np.nan)}
@@ -129,7 +140,8 @@ def frame(verts, faces, draws, tgt, mode: int = BIDIR_MEAN, gscale: float = 1.0,
                d2_ab=np.empty(N, np.float32), nn_ba=np.empty(M, np.int32),
                d_ba=np.empty(M, np.float32), d2_ba=np.empty(M, np.float32))
     g = out.get
-    rc = lib().orc_frame(_p(v), _p(f), V, F, _p(d), N, _p(y), M, int(mode), float(gscale),
+    rc = lib().orc_frame(_p(v), _p(f), _p(fm), V, F, _p(d), N, _p(y), M, int(mode),
+                         float(gscale),
                          int(exact64), _p(out["loss"]), _p(out["loss_exact"]),
                          _p(g("grad_verts")), _p(g("face_idx")), _p(g("margin")),
                          _p(g("bary")), _p(g("x64")), _p(g("x32")), _p(out["nn_ab"]),
@@ -182,7 +194,8 @@ def loss_traj(traj, mode: int = BIDIR_MEAN, weights=None, gscale=None, frames=No
     per = {}
     for t in frames:
         r = frame(traj.verts[t], traj.faces, traj.frame_draws(t), traj.frame_targets(t),
-                  mode=mode, gscale=float(gs[t]), details=details, grads=grads)
+                  mode=mode, gscale=float(gs[t]), details=details, grads=grads,
+                  face_mask=getattr(traj, "face_mask", None))
         loss_frames[t] = r["loss"]
         if grads:
             grad[t] = r["grad_verts"]

@@ -71,6 +71,14 @@ void orc_face_areas(const float* verts, const int32_t* faces, int F, double* are
     }
 }
 
+/* Sec. IV-F (fold scenario) and Sec. IV-C (the regressors' training clouds): points are
+ * sampled from a subset of the faces only. A face outside the subset (mask[f] == 0) gets
+ * area weight 0, so the inverse-CDF pick below never selects it. */
+void orc_mask_areas(double* area, const uint8_t* mask, int F) {
+    for (int f = 0; f < F; ++f)
+        if (!mask[f]) area[f] = 0.0;
+}
+
 /* Sec. III-B: inclusive prefix sum of the areas, summed in face order. */
 void orc_area_cdf(const double* area, int F, double* cdf) {
     double acc = 0.0;
@@ -181,6 +189,7 @@ static void min_f64(const double* q, int n, const double* p, int m, double* best
 /*
  * One frame of the loss and its gradient.
  *   verts [V][3], faces [F][3] (0-based), draws [N][3] = (r_f, r1, r2), tgt [M][3].
+ *   mask [F], nullable: sample only faces with a nonzero entry (orc_mask_areas).
  *   mode: ORC_BIDIR_MEAN (Eq. 1) or ORC_UNIDIR_SUM (Eq. 2).
  *   gscale: multiplier of dL_t in the gradient outputs (the upstream derivative).
  *   exact64: also compute loss_exact from the double-precision minima.
@@ -188,7 +197,8 @@ static void min_f64(const double* q, int n, const double* p, int m, double* best
  * Returns ORC_OK, ORC_EINVAL (empty sizes or a face index out of range) or ORC_EDEGENERATE
  * (total area zero or not finite).
  */
-int orc_frame(const float* verts, const int32_t* faces, int V, int F, const float* draws, int N,
+int orc_frame(const float* verts, const int32_t* faces, const uint8_t* mask, int V, int F,
+              const float* draws, int N,
               const float* tgt, int M, int mode, double gscale, int exact64, double* loss,
               double* loss_exact, double* grad_verts, int32_t* face_idx, double* margin,
               double* bary, double* x64_out, float* x32_out, int32_t* nn_ab, float* d_ab,
@@ -213,6 +223,7 @@ int orc_frame(const float* verts, const int32_t* faces, int V, int F, const floa
     double* g = calloc(3 * (size_t)N, sizeof(double));
 
     orc_face_areas(verts, faces, F, area);
+    if (mask) orc_mask_areas(area, mask, F);
     orc_area_cdf(area, F, cdf);
     const double A = cdf[F - 1];
     if (!(A > 0.0) || !isfinite(A)) {

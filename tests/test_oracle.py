@@ -110,6 +110,59 @@ def test_uniform_density_on_warped_flat_square():
         assert abs(x[:, k].var() - 1 / 12) < 5 * np.sqrt(1 / 180 / n)
 
 
+def test_masked_equal_area_pick_is_floor_over_the_subset():
+    """Sampling from a face subset (Sec. IV-F): on the flat 17x17 grid (512 faces of exactly
+    equal area) with the upper-half mask (256 faces), the pick is the floor(r_f * K)-th face
+    of the subset in face order, for every draw, including draws exactly on a boundary k/K."""
+    tr = W.flat_square(17, 20000, seed=14)
+    mask = W.upper_half_mask(17)
+    sub = np.flatnonzero(mask)
+    K = sub.size
+    assert K == 256 and np.all(mask[:256] == 0)  # faces are stored row by row from v = 0
+    d = tr.draws.copy()
+    d[:K, 0] = (np.arange(K) / K).astype(np.float32)  # exact boundaries
+    r = oracle.frame(tr.verts[0], tr.faces, d, tr.targets[:1], mode=oracle.UNIDIR_SUM,
+                     face_mask=mask)
+    expect = sub[np.floor(d[:, 0].astype(np.float64) * K).astype(np.int64)]
+    np.testing.assert_array_equal(r["face_idx"], expect)
+    # the mask only reweights: an all-ones mask changes nothing
+    r1 = oracle.frame(tr.verts[0], tr.faces, d, tr.targets[:1], mode=oracle.UNIDIR_SUM,
+                      face_mask=np.ones(tr.F, np.uint8))
+    r0 = oracle.frame(tr.verts[0], tr.faces, d, tr.targets[:1], mode=oracle.UNIDIR_SUM)
+    np.testing.assert_array_equal(r1["face_idx"], r0["face_idx"])
+
+
+def test_masked_sampling_uniform_on_the_subset():
+    """With the upper-half mask of a 13x13 grid (the line v = 1/2 is a grid line) on a warped
+    flat square, every sample lies on a kept face and the density is uniform on the kept
+    region [0,1] x [1/2,1] (a mask that only dropped faces from the face count would not
+    keep the area weighting). Faces outside the subset are never picked."""
+    stats = pytest.importorskip("scipy.stats")
+    tr = W.flat_square(13, 200_000, seed=15)
+    mask = W.upper_half_mask(13)
+    v = tr.verts[0].copy()
+    v[:, 0] = v[:, 0] ** 2  # unequal face areas along u (the kept region is unchanged)
+    r = oracle.frame(v, tr.faces, tr.draws, tr.targets[:1], mode=oracle.UNIDIR_SUM,
+                     face_mask=mask)
+    assert np.all(mask[r["face_idx"]] == 1)
+    x = r["x64"]
+    n = x.shape[0]
+    assert np.all(x[:, 1] >= 0.5 - 1e-12)
+    h, _, _ = np.histogram2d(x[:, 0], x[:, 1], bins=(10, 5), range=[[0, 1], [0.5, 1]])
+    chi2 = float(np.sum((h - n / 50) ** 2 / (n / 50)))
+    assert stats.chi2.sf(chi2, 49) > 1e-3
+    assert abs(x[:, 0].mean() - 0.5) < 5 * np.sqrt(1 / 12 / n)
+    assert abs(x[:, 1].mean() - 0.75) < 5 * np.sqrt(1 / 48 / n)
+
+
+def test_empty_face_subset_is_degenerate():
+    tr = W.flat_square(9, 100, seed=16)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.frame(tr.verts[0], tr.faces, tr.draws, tr.targets[:1],
+                     face_mask=np.zeros(tr.F, np.uint8))
+    assert e.value.code == oracle.EDEGENERATE
+
+
 # ---------------------------------------------------------------------------------------------
 # a3: barycentric point (Eq. 3)
 # ---------------------------------------------------------------------------------------------

@@ -39,6 +39,7 @@ class Trajectory:
     targets: np.ndarray          # [sum M_t, 3] float32
     n_off: np.ndarray            # [T+1] int64
     m_off: np.ndarray            # [T+1] int64
+    face_mask: np.ndarray | None = None  # [F] uint8: sample only faces with a nonzero entry
     name: str = ""
     meta: dict = field(default_factory=dict)
 
@@ -160,6 +161,15 @@ def lift_motion(u: np.ndarray, v: np.ndarray, s: float, a: float = 0.35,
     x = u - pull * dx + frac * cx
     y = v - pull * dy + frac * cy
     return np.stack([x, y, h], axis=-1)
+
+
+def upper_half_mask(n_grid: int) -> np.ndarray:
+    """[F] uint8 mask of the faces of an n x n grid whose rest centroid lies in the upper half
+    (v > 1/2): the subset the paper samples from in its fold scenario, where the half of the
+    cloth that stays flat on the table is hidden from the cameras (Sec. IV-F)."""
+    _, v = grid_uv(n_grid)
+    f = grid_faces(n_grid)
+    return np.ascontiguousarray((v[f].mean(axis=1) > 0.5).astype(np.uint8))
 
 
 def add_outliers(rng: np.random.Generator, pts: np.ndarray, frac: float) -> np.ndarray:
