@@ -67,15 +67,25 @@ enum {
 size_t dc_workspace_size(int T, int V, int F, int N, int M);
 
 /*
+ * Face subsets. The entry points that sample take face_mask [F] (uint8, nullable: every
+ * face): only faces with a nonzero entry are sampled. A face outside the subset gets area
+ * weight 0 before the prefix sum, so the inverse-CDF pick never selects it -- the paper
+ * samples the simulated cloud from the visible half of the cloth in its fold scenario
+ * (Sec. IV-F) and from a face subset to mimic occlusion (Sec. IV-C). A subset of zero total
+ * area is reported as DC_EDEGENERATE, like a zero-area frame.
+ */
+
+/*
  * dc_sample -- area-weighted surface sampling (Sec. III-B, Eq. 3).
+ *   face_mask [F] nullable: sample only these faces (see above).
  *   points   [T][N][3] out: x_i of every frame.
  *   face_idx [T][N] out, nullable: the picked face f_i.
  *   bary     [T][N][3] out, nullable: (w0, w1, w2).
  * Uses ws for the per-frame area CDF.
  */
-int dc_sample(const float* verts, const int32_t* faces, const float* draws, int T, int V, int F,
-              int N, float* points, int32_t* face_idx, float* bary, void* ws, size_t ws_bytes,
-              dc_stream_t stream);
+int dc_sample(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+              const float* draws, int T, int V, int F, int N, float* points, int32_t* face_idx,
+              float* bary, void* ws, size_t ws_bytes, dc_stream_t stream);
 
 /*
  * dc_chamfer_fwd -- Chamfer distance of given clouds, per frame (Eq. 1 or Eq. 2).
@@ -103,6 +113,7 @@ int dc_chamfer_bwd(const float* a, const float* b, const int32_t* nn_ab, const i
 /*
  * dc_loss_traj -- the whole loss over a trajectory, and optionally its vertex gradient
  * (Sec. III-B, Eq. 1-4; the per-frame loss of Sec. III-C).
+ *   face_mask   [F] nullable: sample only these faces (see above).
  *   frame_w     [T] nullable (all ones): weights w_t. A frame whose weight is 0 is skipped:
  *               no sampling, Chamfer or gradient work is done for it, its L_t is reported as
  *               0 and its gradient rows are 0 (the paper mostly optimises one frame, Sec. III-C).
@@ -113,8 +124,9 @@ int dc_chamfer_bwd(const float* a, const float* b, const int32_t* nn_ab, const i
  *   nn_ab [T][N], nn_ba [T][M] out, nullable: the neighbours (kept for dc_loss_traj_bwd).
  * ws sized by dc_workspace_size(T, V, F, N, M). Sampled points live in ws only.
  */
-int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
-                 const float* targets, int T, int V, int F, int N, int M, int mode,
+int dc_loss_traj(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+                 const float* draws, const float* targets, int T, int V, int F, int N, int M,
+                 int mode,
                  const float* frame_w, float* loss_total, float* loss_frames, float* grad_verts,
                  int32_t* nn_ab, int32_t* nn_ba, void* ws, size_t ws_bytes,
                  dc_stream_t stream);
@@ -122,12 +134,13 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
 /*
  * dc_loss_traj_bwd -- vertex gradient of sum_t g_t L_t given the neighbours a previous
  * dc_loss_traj returned. The sampled points are recomputed from the draws (nothing from
- * the forward is stored but nn_ab / nn_ba).
+ * the forward is stored but nn_ab / nn_ba). face_mask as in that call.
  *   grad_frames [T]: g_t = dObjective/dL_t; frames with g_t = 0 are skipped (zero rows).
  *   grad_verts [T][V][3] out, overwritten.
  */
-int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draws,
-                     const float* targets, int T, int V, int F, int N, int M, int mode,
+int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+                     const float* draws, const float* targets, int T, int V, int F, int N, int M,
+                     int mode,
                      const int32_t* nn_ab, const int32_t* nn_ba, const float* grad_frames,
                      float* grad_verts, void* ws, size_t ws_bytes, dc_stream_t stream);
 
@@ -138,6 +151,7 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draw
 typedef struct dc_frame {
     const float* verts;   /* [V][3] */
     const int32_t* faces; /* [F][3] */
+    const uint8_t* face_mask; /* [F], nullable: sample only these faces (see above) */
     const float* draws;   /* [N][3] */
     const float* targets; /* [M][3] */
     int32_t V, F, N, M;
@@ -209,8 +223,9 @@ int dc_ws_status(const void* ws, dc_stream_t stream);
  *   All calls on a device share the one array and each overwrites it: calls that may overlap
  *   on the GPU (different streams, or threads without ordering) race and must not be issued.
  */
-int dc_loss_traj_noalloc(const float* verts, const int32_t* faces, const float* draws,
-                         const float* targets, int T, int V, int F, int N, int M, int mode,
+int dc_loss_traj_noalloc(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+                         const float* draws, const float* targets, int T, int V, int F, int N,
+                         int M, int mode,
                          const float* frame_w, float* loss_total, float* loss_frames,
                          float* grad_verts, int32_t* nn_ab, int32_t* nn_ba, int32_t* status,
                          dc_stream_t stream);

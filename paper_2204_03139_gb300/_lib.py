@@ -37,7 +37,8 @@ class dc_tune(ctypes.Structure):
 
 class dc_frame(ctypes.Structure):
     _fields_ = [("verts", ctypes.c_void_p), ("faces", ctypes.c_void_p),
-                ("draws", ctypes.c_void_p), ("targets", ctypes.c_void_p),
+                ("face_mask", ctypes.c_void_p), ("draws", ctypes.c_void_p),
+                ("targets", ctypes.c_void_p),
                 ("V", ctypes.c_int32), ("F", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("M", ctypes.c_int32), ("weight", ctypes.c_float), ("tag", ctypes.c_int32),
                 ("loss", ctypes.c_void_p), ("grad_verts", ctypes.c_void_p),
@@ -61,11 +62,12 @@ def lib() -> ctypes.CDLL:
             P, I, S, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
             sig = {
                 "dc_workspace_size": (S, [I, I, I, I, I]),
-                "dc_sample": (I, [P, P, P, I, I, I, I, P, P, P, P, S, P]),
+                "dc_sample": (I, [P, P, P, P, I, I, I, I, P, P, P, P, S, P]),
                 "dc_chamfer_fwd": (I, [P, P, I, I, I, I, P, P, P, P, S, P]),
                 "dc_chamfer_bwd": (I, [P, P, P, P, I, I, I, I, P, P, P]),
-                "dc_loss_traj": (I, [P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P, S, P]),
-                "dc_loss_traj_bwd": (I, [P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, S, P]),
+                "dc_loss_traj": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P, S,
+                                     P]),
+                "dc_loss_traj_bwd": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, S, P]),
                 "dc_batch_workspace_size": (S, [P, I]),
                 "dc_batch_plan": (I, [P, I, I, P, S, P]),
                 "dc_batch_run": (I, [P, P, P]),
@@ -74,8 +76,8 @@ def lib() -> ctypes.CDLL:
                 "dc_launch_count": (ctypes.c_longlong, []),
                 "dc_prof_start": (I, [I]),
                 "dc_prof_stop": (I, [ctypes.POINTER(F), ctypes.POINTER(I)]),
-                "dc_loss_traj_noalloc": (I, [P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P,
-                                             P]),
+                "dc_loss_traj_noalloc": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P,
+                                             P, P]),
                 "dc_tune_set": (I, [P]),
                 "dc_tune_get": (I, [P]),
             }
@@ -122,6 +124,18 @@ def _i32(t, name):
     return t
 
 
+def _mask(m, F):
+    """face_mask: None, or a contiguous uint8 (or bool) CUDA tensor of one entry per face."""
+    if m is None:
+        return None
+    if m.dtype == torch.bool:
+        m = m.to(torch.uint8)
+    if m.dtype != torch.uint8 or not m.is_contiguous() or not m.is_cuda or m.numel() != F:
+        raise ValueError("face_mask must be a contiguous uint8 CUDA tensor with one entry per "
+                         "face")
+    return m
+
+
 # one workspace per (device, stream): calls on one stream are ordered, so they may share it
 _ws_cache: dict = {}
 
@@ -151,12 +165,14 @@ def dc_workspace_size(T, V, F, N, M) -> int:
     return int(lib().dc_workspace_size(T, V, F, N, M))
 
 
-def dc_sample(verts, faces, draws, face_idx=True, bary=True, check=False):
-    """Area-weighted sampling (Sec. III-B, Eq. 3). verts [T,V,3], faces [F,3], draws [T,N,3].
+def dc_sample(verts, faces, draws, face_idx=True, bary=True, check=False, face_mask=None):
+    """Area-weighted sampling (Sec. III-B, Eq. 3). verts [T,V,3], faces [F,3], draws [T,N,3];
+    face_mask [F] (optional): sample only the faces with a nonzero entry.
     Returns points [T,N,3], face_idx [T,N] and bary [T,N,3] (or None)."""
     dev = _dev(verts)
     _f32(verts, "verts"), _i32(faces, "faces"), _f32(draws, "draws")
     T, V, F, N = verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1]
+    fm = _mask(face_mask, F)
     pts = torch.empty((T, N, 3), dtype=torch.float32, device=dev)
     fi = torch.empty((T, N), dtype=torch.int32, device=dev) if face_idx else None
     bc = torch.empty((T, N, 3), dtype=torch.float32, device=dev) if bary else None
@@ -164,8 +180,8 @@ def dc_sample(verts, faces, draws, face_idx=True, bary=True, check=False):
     if nb == 0:
         raise DCError(DC_EINVAL, "bad sizes")
     ws = workspace(nb, dev)
-    _check(lib().dc_sample(_ptr(verts), _ptr(faces), _ptr(draws), T, V, F, N, _ptr(pts),
-                           _ptr(fi), _ptr(bc), _ptr(ws), ws.numel(), _stream(dev)))
+    _check(lib().dc_sample(_ptr(verts), _ptr(faces), _ptr(fm), _ptr(draws), T, V, F, N,
+                           _ptr(pts), _ptr(fi), _ptr(bc), _ptr(ws), ws.numel(), _stream(dev)))
     if check:
         check_ws(ws)
     return pts, fi, bc
@@ -202,10 +218,11 @@ def dc_chamfer_bwd(a, b, nn_ab, nn_ba, grad_loss, mode=BIDIR_MEAN):
 
 
 def dc_loss_traj(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None, grad=True,
-                 total=True, nn=True, check=False, out=None):
+                 total=True, nn=True, check=False, out=None, face_mask=None):
     """The whole loss over a trajectory (Sec. III-B, Eq. 1-4).
 
-    verts [T,V,3], faces [F,3], draws [T,N,3], targets [T,M,3] (CUDA, contiguous).
+    verts [T,V,3], faces [F,3], draws [T,N,3], targets [T,M,3] (CUDA, contiguous); face_mask
+    [F] (optional): sample only the faces with a nonzero entry.
     Returns a dict with loss_total [1] (or None), loss_frames [T], grad_verts [T,V,3] (or
     None), nn_ab [T,N], nn_ba [T,M] (or None). `out` may supply preallocated outputs."""
     dev = _dev(verts)
@@ -237,16 +254,17 @@ def dc_loss_traj(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None, gr
     ws = o.get("ws")
     if ws is None or ws.numel() < nb:
         ws = workspace(nb, dev)
-    _check(lib().dc_loss_traj(_ptr(verts), _ptr(faces), _ptr(draws), _ptr(targets), T, V, F, N,
-                              M, mode, _ptr(frame_w), _ptr(lt), _ptr(lf), _ptr(gv), _ptr(nab),
-                              _ptr(nba), _ptr(ws), ws.numel(), _stream(dev)))
+    fm = _mask(face_mask, F)
+    _check(lib().dc_loss_traj(_ptr(verts), _ptr(faces), _ptr(fm), _ptr(draws), _ptr(targets), T,
+                              V, F, N, M, mode, _ptr(frame_w), _ptr(lt), _ptr(lf), _ptr(gv),
+                              _ptr(nab), _ptr(nba), _ptr(ws), ws.numel(), _stream(dev)))
     if check:
         check_ws(ws)
     return {"loss_total": lt, "loss_frames": lf, "grad_verts": gv, "nn_ab": nab, "nn_ba": nba}
 
 
 def dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab, nn_ba, grad_frames,
-                     mode=BIDIR_MEAN, check=False, grad_verts=None):
+                     mode=BIDIR_MEAN, check=False, grad_verts=None, face_mask=None):
     """Vertex gradient of sum_t g_t L_t, recomputing the samples from the draws."""
     dev = _dev(verts)
     T, V, F, N, M = (verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1],
@@ -254,8 +272,9 @@ def dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab, nn_ba, grad_frames,
     gv = grad_verts if grad_verts is not None else torch.empty_like(verts)
     nb = dc_workspace_size(T, V, F, N, M)
     ws = workspace(nb, dev)
-    _check(lib().dc_loss_traj_bwd(_ptr(verts), _ptr(faces), _ptr(draws), _ptr(targets), T, V,
-                                  F, N, M, mode, _ptr(nn_ab), _ptr(nn_ba),
+    fm = _mask(face_mask, F)
+    _check(lib().dc_loss_traj_bwd(_ptr(verts), _ptr(faces), _ptr(fm), _ptr(draws), _ptr(targets),
+                                  T, V, F, N, M, mode, _ptr(nn_ab), _ptr(nn_ba),
                                   _ptr(_f32(grad_frames, "grad_frames")), _ptr(gv), _ptr(ws),
                                   ws.numel(), _stream(dev)))
     if check:
@@ -279,7 +298,7 @@ def prof_stop() -> tuple[float, int]:
 
 
 def dc_loss_traj_noalloc(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None,
-                         grad=True, check=False):
+                         grad=True, check=False, face_mask=None):
     """dc_loss_traj on the library's built-in 16 MiB scratch array instead of a workspace,
     for callers that cannot allocate device memory when they need the loss. The outputs are
     allocated here for convenience; a caller that cannot allocate passes its own buffers to
@@ -294,9 +313,11 @@ def dc_loss_traj_noalloc(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=
     nab = torch.empty((T, N), dtype=torch.int32, device=dev)
     nba = torch.empty((T, M), dtype=torch.int32, device=dev) if mode == BIDIR_MEAN else None
     st = torch.zeros(1, dtype=torch.int32, device=dev)
-    _check(lib().dc_loss_traj_noalloc(_ptr(verts), _ptr(faces), _ptr(draws), _ptr(targets), T, V,
-                                      F, N, M, mode, _ptr(frame_w), _ptr(lt), _ptr(lf), _ptr(gv),
-                                      _ptr(nab), _ptr(nba), _ptr(st), _stream(dev)))
+    fm = _mask(face_mask, F)
+    _check(lib().dc_loss_traj_noalloc(_ptr(verts), _ptr(faces), _ptr(fm), _ptr(draws),
+                                      _ptr(targets), T, V, F, N, M, mode, _ptr(frame_w),
+                                      _ptr(lt), _ptr(lf), _ptr(gv), _ptr(nab), _ptr(nba),
+                                      _ptr(st), _stream(dev)))
     if check:
         code = int(st.item())
         if code != DC_OK:

@@ -15,11 +15,12 @@ class DCLoss(torch.autograd.Function):
     """loss_frames[t] = L_t(verts[t]); differentiable with respect to verts only."""
 
     @staticmethod
-    def forward(ctx, verts, faces, draws, targets, mode=_lib.BIDIR_MEAN):
+    def forward(ctx, verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, face_mask=None):
         verts = verts.detach().contiguous()
         r = _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode, grad=False, total=False,
-                              nn=True)
+                              nn=True, face_mask=face_mask)
         ctx.mode = mode
+        ctx.face_mask = face_mask
         nn_ba = r["nn_ba"] if r["nn_ba"] is not None else r["nn_ab"]
         ctx.save_for_backward(verts, faces, draws, targets, r["nn_ab"], nn_ba)
         return r["loss_frames"]
@@ -29,12 +30,15 @@ class DCLoss(torch.autograd.Function):
         verts, faces, draws, targets, nn_ab, nn_ba = ctx.saved_tensors
         g = _lib.dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab,
                                   nn_ba if ctx.mode == _lib.BIDIR_MEAN else None,
-                                  grad_frames.detach().float().contiguous(), mode=ctx.mode)
-        return g, None, None, None, None
+                                  grad_frames.detach().float().contiguous(), mode=ctx.mode,
+                                  face_mask=ctx.face_mask)
+        return g, None, None, None, None, None
 
 
-def loss_traj(verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, frame_w=None):
-    """Differentiable sum_t w_t L_t (w_t = 1 by default) and the per-frame losses."""
-    lf = DCLoss.apply(verts, faces, draws, targets, mode)
+def loss_traj(verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, frame_w=None,
+              face_mask=None):
+    """Differentiable sum_t w_t L_t (w_t = 1 by default) and the per-frame losses.
+    face_mask [F] (optional): sample only the faces with a nonzero entry."""
+    lf = DCLoss.apply(verts, faces, draws, targets, mode, face_mask)
     w = torch.ones_like(lf) if frame_w is None else frame_w
     return (w * lf).sum(), lf

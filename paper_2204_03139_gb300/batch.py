@@ -30,6 +30,7 @@ class DeviceTrajectory:
     targets: torch.Tensor  # [sum M_t, 3] float32
     n_off: np.ndarray
     m_off: np.ndarray
+    face_mask: torch.Tensor | None = None  # [F] uint8: sample only faces with a nonzero entry
 
     @property
     def T(self):
@@ -41,14 +42,20 @@ class DeviceTrajectory:
                                 torch.from_numpy(tr.faces).to(device),
                                 torch.from_numpy(tr.draws).to(device),
                                 torch.from_numpy(tr.targets).to(device),
-                                np.asarray(tr.n_off, np.int64), np.asarray(tr.m_off, np.int64))
+                                np.asarray(tr.n_off, np.int64), np.asarray(tr.m_off, np.int64),
+                                _device_mask(getattr(tr, "face_mask", None), device))
 
     def pairs(self) -> int:
         return int(np.sum(np.diff(self.n_off) * np.diff(self.m_off)))
 
 
-# numpy view of the C struct dc_frame (include/diffcloud.h), 88 bytes per frame
-FRAME_DTYPE = np.dtype([("verts", "u8"), ("faces", "u8"), ("draws", "u8"), ("targets", "u8"),
+def _device_mask(m, device):
+    return None if m is None else torch.from_numpy(np.ascontiguousarray(m, np.uint8)).to(device)
+
+
+# numpy view of the C struct dc_frame (include/diffcloud.h), 96 bytes per frame
+FRAME_DTYPE = np.dtype([("verts", "u8"), ("faces", "u8"), ("face_mask", "u8"), ("draws", "u8"),
+                        ("targets", "u8"),
                         ("V", "i4"), ("F", "i4"), ("N", "i4"), ("M", "i4"), ("weight", "f4"),
                         ("tag", "i4"), ("loss", "u8"), ("grad_verts", "u8"), ("nn_ab", "u8"),
                         ("nn_ba", "u8")])
@@ -104,6 +111,10 @@ class BatchedLoss:
             row = tab[k:k + T]
             row["verts"] = tr.verts.data_ptr() + 12 * V * t
             row["faces"] = tr.faces.data_ptr()
+            if tr.face_mask is not None:
+                if tr.face_mask.dtype != torch.uint8 or tr.face_mask.numel() != F:
+                    raise ValueError("face_mask must be a uint8 tensor with one entry per face")
+                row["face_mask"] = tr.face_mask.data_ptr()
             row["draws"] = tr.draws.data_ptr() + 12 * n_off[:-1]
             row["targets"] = tr.targets.data_ptr() + 12 * m_off[:-1]
             row["V"], row["F"] = V, F

@@ -282,7 +282,8 @@ int dc_ws_status(const void* ws, dc_stream_t stream) {
     return st;
 }
 
-int dc_sample(const float* verts, const int32_t* faces, const float* draws, int T, int V, int F,
+int dc_sample(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+              const float* draws, int T, int V, int F,
               int N, float* points, int32_t* face_idx, float* bary, void* ws, size_t ws_bytes,
               dc_stream_t stream) {
     if (T <= 0 || V <= 0 || F <= 0 || N <= 0) return fail(DC_EINVAL, "sizes must be positive");
@@ -291,6 +292,7 @@ int dc_sample(const float* verts, const int32_t* faces, const float* draws, int 
     UniformArgs a{};
     a.verts = verts;
     a.faces = faces;
+    a.mask = face_mask;
     a.draws = draws;
     a.out_pts = points;
     a.out_face = face_idx;
@@ -341,8 +343,9 @@ int dc_chamfer_bwd(const float* a, const float* b, const int32_t* nn_ab, const i
     return DC_OK;
 }
 
-int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
-                 const float* targets, int T, int V, int F, int N, int M, int mode,
+int dc_loss_traj(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+                 const float* draws, const float* targets, int T, int V, int F, int N, int M,
+                 int mode,
                  const float* frame_w, float* loss_total, float* loss_frames, float* grad_verts,
                  int32_t* nn_ab, int32_t* nn_ba, void* ws, size_t ws_bytes,
                  dc_stream_t stream) {
@@ -354,6 +357,7 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
     UniformArgs a{};
     a.verts = verts;
     a.faces = faces;
+    a.mask = face_mask;
     a.draws = draws;
     a.tgt = targets;
     a.loss = loss_frames;
@@ -372,8 +376,9 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const float* draws,
     return run_uniform(a, ph, epi, loss_total, ws, ws_bytes, stream);
 }
 
-int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draws,
-                     const float* targets, int T, int V, int F, int N, int M, int mode,
+int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+                     const float* draws, const float* targets, int T, int V, int F, int N, int M,
+                     int mode,
                      const int32_t* nn_ab, const int32_t* nn_ba, const float* grad_frames,
                      float* grad_verts, void* ws, size_t ws_bytes, dc_stream_t stream) {
     int rc = check_common(T, N, M, mode);
@@ -386,6 +391,7 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const float* draw
     UniformArgs a{};
     a.verts = verts;
     a.faces = faces;
+    a.mask = face_mask;
     a.draws = draws;
     a.tgt = targets;
     a.nn_ab = const_cast<int32_t*>(nn_ab);
@@ -475,6 +481,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
         FrameDesc d{};
         d.verts = f.verts;
         d.faces = f.faces;
+        d.mask = f.face_mask;
         d.draws = f.draws;
         d.tgt = f.targets;
         d.loss = f.loss ? f.loss : w.loss + k;
@@ -591,7 +598,8 @@ void* g_noalloc_ptr[64];  // device address of g_noalloc_scratch, per device
 }  // namespace
 
 extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
-                                    const float* draws, const float* targets, int T, int V, int F,
+                                    const uint8_t* face_mask, const float* draws,
+                                    const float* targets, int T, int V, int F,
                                     int N, int M, int mode, const float* frame_w,
                                     float* loss_total, float* loss_frames, float* grad_verts,
                                     int32_t* nn_ab, int32_t* nn_ba, int32_t* status,
@@ -626,8 +634,9 @@ extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
     }
     // Every region of the scratch that a call reads is written earlier in the same call (the
     // status word included), so nothing needs clearing between calls.
-    rc = dc_loss_traj(verts, faces, draws, targets, T, V, F, N, M, mode, frame_w, loss_total,
-                      loss_frames, grad_verts, nn_ab, nn_ba, ws, DC_NOALLOC_SCRATCH_BYTES, stream);
+    rc = dc_loss_traj(verts, faces, face_mask, draws, targets, T, V, F, N, M, mode, frame_w,
+                      loss_total, loss_frames, grad_verts, nn_ab, nn_ba, ws,
+                      DC_NOALLOC_SCRATCH_BYTES, stream);
     if (rc) return rc;
     if (status) {
         e = cudaMemcpyAsync(status, &static_cast<const WsHeader*>(ws)->status, sizeof(int32_t),

@@ -42,6 +42,7 @@ constexpr unsigned long long EMPTY = ~0ull;
 struct FrameDesc {
     const float* verts;   // [V][3]; NULL for a frame given as points (Chamfer only)
     const int* faces;     // [F][3]
+    const uint8_t* mask;  // [F] nullable: faces with a zero entry get area weight 0
     const float* draws;   // [N][3]
     const float* pts;     // [N][3] sim points given directly; NULL when sampled
     const float* tgt;     // [M][3]
@@ -136,6 +137,7 @@ __host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
 struct UniformArgs {
     const float* verts;
     const int* faces;
+    const uint8_t* mask;
     const float* draws;
     const float* pts;
     const float* tgt;

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, 
             FrameDesc f;
             f.verts = a.verts ? a.verts + 3LL * k * a.V : nullptr;
             f.faces = a.faces;
+            f.mask = a.mask;
             f.draws = a.draws ? a.draws + 3LL * k * a.N : nullptr;
             f.pts = a.pts ? a.pts + 3LL * k * a.N : nullptr;
             f.tgt = a.tgt ? a.tgt + 3LL * k * a.M : nullptr;
@@ -187,6 +188,16 @@ __device__ __forceinline__ float face_area(const float* __restrict__ verts,
     return __fmul_rn(0.5f, __fsqrt_rn(n2));
 }
 
+// The area weight of face f: its area, or 0 for a face outside the sampled subset
+// (Sec. IV-F). The face is still checked, so that bad indices are reported either way.
+__device__ __forceinline__ float face_weight(const float* __restrict__ verts,
+                                             const int* __restrict__ faces,
+                                             const uint8_t* __restrict__ mask, int V, int f,
+                                             bool& bad_idx, bool& bad_val) {
+    const float a = face_area(verts, faces, V, f, bad_idx, bad_val);
+    return (mask && mask[f] == 0) ? 0.0f : a;
+}
+
 constexpr int CDF_THREADS = 1024;
 
 __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
@@ -200,6 +211,7 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
         return;
     }
     const int* faces = fr->faces;
+    const uint8_t* mask = fr->mask;
     const int F = fr->F, V = fr->V;
     float* cdf = w.cdf + fr->cdf0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -208,7 +220,8 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
     bool bad_idx = false, bad_val = false;
 
     FF v = {0.0f, 0.0f};
-    for (int f = f0; f < f1; ++f) v = ff_add1(v, face_area(verts, faces, V, f, bad_idx, bad_val));
+    for (int f = f0; f < f1; ++f)
+        v = ff_add1(v, face_weight(verts, faces, mask, V, f, bad_idx, bad_val));
 
     // block-wide inclusive scan of the segment sums
 #pragma unroll
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
     FF run = warp > 0 ? ff_add(s_w[warp - 1], ex) : ex;
 
     for (int f = f0; f < f1; ++f) {
-        run = ff_add1(run, face_area(verts, faces, V, f, bad_idx, bad_val));
+        run = ff_add1(run, face_weight(verts, faces, mask, V, f, bad_idx, bad_val));
         cdf[f] = run.hi;
     }
     if (bad_idx || bad_val) set_status(&w.hdr->status, DC_EINVAL);

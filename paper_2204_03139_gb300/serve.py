@@ -81,7 +81,7 @@ def _slice(d: DeviceTrajectory, a: int, b: int) -> DeviceTrajectory:
     n0, n1 = int(d.n_off[a]), int(d.n_off[b])
     m0, m1 = int(d.m_off[a]), int(d.m_off[b])
     return DeviceTrajectory(d.verts[a:b], d.faces, d.draws[n0:n1], d.targets[m0:m1],
-                            d.n_off[a:b + 1] - n0, d.m_off[a:b + 1] - m0)
+                            d.n_off[a:b + 1] - n0, d.m_off[a:b + 1] - m0, d.face_mask)
 
 
 def _frames_of(traj):
@@ -97,7 +97,8 @@ def _frames_of(traj):
 
 def request_bytes(traj, grad: bool = True) -> int:
     """Device bytes a request holds while admitted: inputs, outputs, workspace share."""
-    inputs = (traj.verts.nbytes + traj.faces.nbytes + traj.draws.nbytes + traj.targets.nbytes)
+    inputs = (traj.verts.nbytes + traj.faces.nbytes + traj.draws.nbytes + traj.targets.nbytes
+              + traj.F)  # and the face mask, if any
     outputs = 4 * traj.T + (traj.verts.nbytes if grad else 0)
     ws = int(_lib.lib().dc_batch_workspace_size(_frames_of(traj), traj.T))
     if ws == 0:
@@ -209,8 +210,11 @@ class Server:
             # pinned host copies, kept on the trajectory object for repeated submissions
             host = getattr(tr, "_dc_pinned", None)
             if host is None:
+                arrays = [tr.verts, tr.faces, tr.draws, tr.targets]
+                if getattr(tr, "face_mask", None) is not None:
+                    arrays.append(np.asarray(tr.face_mask, np.uint8))
                 host = tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                             for a in (tr.verts, tr.faces, tr.draws, tr.targets))
+                             for a in arrays)
                 try:
                     tr._dc_pinned = host
                 except AttributeError:
@@ -221,7 +225,8 @@ class Server:
                 r.ready.record(self._copy)
             r.host = host  # pinned buffers live until the copy has finished
             r.dev = DeviceTrajectory(dv[0], dv[1], dv[2], dv[3], np.asarray(tr.n_off, np.int64),
-                                     np.asarray(tr.m_off, np.int64))
+                                     np.asarray(tr.m_off, np.int64),
+                                     dv[4] if len(dv) > 4 else None)
             r.loss = np.empty(tr.T, np.float32)
             r.gradv = np.empty(tr.verts.shape, np.float32) if r.grad else None
             # cut into items of consecutive frames of at most item_pairs pairs
@@ -357,7 +362,9 @@ def serve_plain(requests, device="cuda:0", mode: int = _lib.BIDIR_MEAN):
         f = torch.from_numpy(tr.faces).to(dev)
         d = torch.from_numpy(np.ascontiguousarray(tr.draws_tn3())).to(dev)
         y = torch.from_numpy(np.ascontiguousarray(tr.targets_tm3())).to(dev)
-        r = _lib.dc_loss_traj(v, f, d, y, mode=mode)
+        m = getattr(tr, "face_mask", None)
+        m = None if m is None else torch.from_numpy(np.asarray(m, np.uint8)).to(dev)
+        r = _lib.dc_loss_traj(v, f, d, y, mode=mode, face_mask=m)
         r["grad_verts"].cpu()
         float(r["loss_total"][0])
         lat.append(time.perf_counter() - t0 - arrival)

@@ -19,10 +19,11 @@ LOSS_RTOL = 1e-5
 GRAD_RTOL = 1e-4
 
 
-def frame_margins(verts_t, faces, draws_t):
+def frame_margins(verts_t, faces, draws_t, face_mask=None):
     """Oracle face picks and CDF margins of one frame's draws (no Chamfer needed)."""
     one = np.zeros((1, 3), np.float32)
-    r = oracle.frame(verts_t, faces, draws_t, one, mode=oracle.UNIDIR_SUM, grads=False)
+    r = oracle.frame(verts_t, faces, draws_t, one, mode=oracle.UNIDIR_SUM, grads=False,
+                     face_mask=face_mask)
     return r["face_idx"], r["margin"]
 
 
@@ -33,12 +34,13 @@ def nudge_draws(traj, window: float = WINDOW):
     tr = copy.copy(traj)
     tr.draws = traj.draws.copy()
     moved = 0
+    mask = getattr(traj, "face_mask", None)
     for t in range(traj.T):
         d = tr.draws[traj.n_off[t]:traj.n_off[t + 1]]
-        fi, mg = frame_margins(traj.verts[t], traj.faces, d)
+        fi, mg = frame_margins(traj.verts[t], traj.faces, d, mask)
         bad = np.nonzero(mg < window)[0]
         if bad.size:
-            cdf = oracle.area_cdf(oracle.face_areas(traj.verts[t], traj.faces))
+            cdf = oracle.area_cdf(oracle.face_areas(traj.verts[t], traj.faces, mask))
             A = cdf[-1]
             f = fi[bad]
             lo = np.where(f > 0, cdf[np.maximum(f - 1, 0)], 0.0)

@@ -61,21 +61,21 @@ FAKE = ctypes.c_void_p(0x100000)  # never dereferenced: validation fails first
 def test_host_side_validation(L):
     from paper_2204_03139_gb300 import _lib
 
-    rc = L.dc_loss_traj(None, FAKE, FAKE, FAKE, 1, 3, 1, 4, 4, 0, None, None, FAKE, None, None,
-                        None, FAKE, 1 << 20, None)
+    rc = L.dc_loss_traj(None, FAKE, None, FAKE, FAKE, 1, 3, 1, 4, 4, 0, None, None,
+                        FAKE, None, None, None, FAKE, 1 << 20, None)
     assert rc == _lib.DC_EINVAL and "NULL" in _lib.last_error()
-    rc = L.dc_loss_traj(FAKE, FAKE, FAKE, FAKE, 1, 3, 1, 0, 4, 0, None, None, FAKE, None, None,
-                        None, FAKE, 1 << 20, None)
+    rc = L.dc_loss_traj(FAKE, FAKE, None, FAKE, FAKE, 1, 3, 1, 0, 4, 0, None, None,
+                        FAKE, None, None, None, FAKE, 1 << 20, None)
     assert rc == _lib.DC_EINVAL
-    rc = L.dc_loss_traj(FAKE, FAKE, FAKE, FAKE, 1, 3, 1, 4, 4, 7, None, None, FAKE, None, None,
-                        None, FAKE, 1 << 20, None)
+    rc = L.dc_loss_traj(FAKE, FAKE, None, FAKE, FAKE, 1, 3, 1, 4, 4, 7, None, None,
+                        FAKE, None, None, None, FAKE, 1 << 20, None)
     assert rc == _lib.DC_EINVAL and "mode" in _lib.last_error()
     # workspace too small / misaligned
-    rc = L.dc_loss_traj(FAKE, FAKE, FAKE, FAKE, 1, 3, 1, 4, 4, 0, None, None, FAKE, None, None,
-                        None, FAKE, 16, None)
+    rc = L.dc_loss_traj(FAKE, FAKE, None, FAKE, FAKE, 1, 3, 1, 4, 4, 0, None, None,
+                        FAKE, None, None, None, FAKE, 16, None)
     assert rc == _lib.DC_ENOSPC
-    rc = L.dc_loss_traj(FAKE, FAKE, FAKE, FAKE, 1, 3, 1, 4, 4, 0, None, None, FAKE, None, None,
-                        None, ctypes.c_void_p(0x100010), 1 << 30, None)
+    rc = L.dc_loss_traj(FAKE, FAKE, None, FAKE, FAKE, 1, 3, 1, 4, 4, 0, None, None,
+                        FAKE, None, None, None, ctypes.c_void_p(0x100010), 1 << 30, None)
     assert rc == _lib.DC_EINVAL and "aligned" in _lib.last_error()
     # misaligned data pointer
     rc = L.dc_chamfer_fwd(ctypes.c_void_p(0x100002), FAKE, 1, 4, 4, 0, FAKE, None, None, FAKE,
@@ -83,7 +83,7 @@ def test_host_side_validation(L):
     assert rc == _lib.DC_EINVAL
     rc = L.dc_chamfer_bwd(FAKE, FAKE, FAKE, None, 1, 4, 4, 0, FAKE, FAKE, None)
     assert rc == _lib.DC_EINVAL and "nn_ba" in _lib.last_error()
-    rc = L.dc_sample(FAKE, FAKE, FAKE, 1, 3, 1, -1, FAKE, None, None, FAKE, 1 << 20, None)
+    rc = L.dc_sample(FAKE, FAKE, None, FAKE, 1, 3, 1, -1, FAKE, None, None, FAKE, 1 << 20, None)
     assert rc == _lib.DC_EINVAL
 
 

@@ -68,6 +68,28 @@ def test_batch_skips_zero_weight_frames(trajs):
         assert np.all(lf[dead] == 0.0) and np.all(gv[dead] == 0.0)
 
 
+def test_batch_with_face_subsets(trajs):
+    """Each trajectory samples its own face subset (alternate trajectories: the upper half of
+    the cloth, or every face); the batch matches the oracle with the same masks."""
+    import copy
+
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
+
+    mtr = []
+    for k, t in enumerate(trajs):
+        t = copy.copy(t)
+        n = int(round(t.V ** 0.5))
+        t.face_mask = W.upper_half_mask(n) if k % 2 == 0 else None
+        mtr.append(parity.nudge_draws(t)[0])
+    b = BatchedLoss([DeviceTrajectory.from_host(t, DEV) for t in mtr], grad=True)
+    b.run(check=True)
+    torch.cuda.synchronize()
+    for k, t in enumerate(mtr):
+        ref = oracle.loss_traj(t)
+        parity.check_loss(b.loss_frames[k].cpu().numpy(), ref["loss_frames"])
+        parity.check_grad(b.grad_verts[k].cpu().numpy(), ref["grad_verts"])
+
+
 def test_batch_equals_per_frame_form(trajs):
     from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory, per_frame_loss
 

@@ -40,10 +40,15 @@ def to_dev(tr):
             torch.from_numpy(np.ascontiguousarray(tr.targets_tm3())).to(DEV))
 
 
+def dev_mask(tr):
+    m = getattr(tr, "face_mask", None)
+    return None if m is None else torch.from_numpy(np.ascontiguousarray(m, np.uint8)).to(DEV)
+
+
 def run_traj(tr, mode=0, frame_w=None):
     v, f, d, y = to_dev(tr)
     w = None if frame_w is None else torch.tensor(frame_w, dtype=torch.float32, device=DEV)
-    r = L().dc_loss_traj(v, f, d, y, mode=mode, frame_w=w, check=True)
+    r = L().dc_loss_traj(v, f, d, y, mode=mode, frame_w=w, check=True, face_mask=dev_mask(tr))
     torch.cuda.synchronize()
     return {k: (x.cpu().numpy() if isinstance(x, torch.Tensor) else x) for k, x in r.items()}
 
@@ -89,6 +94,60 @@ def test_trajectory_50x50_weights_total():
     g = run_traj(tr, frame_w=w)
     ref = oracle.loss_traj(tr, weights=w)
     compare_traj(tr, g, ref, list(range(tr.T)), weights=w)
+
+
+# ---------------------------------------------------------------------------------------------
+# sampling from a face subset (Sec. IV-F fold scenario)
+# ---------------------------------------------------------------------------------------------
+def masked(tr, mask):
+    import copy
+
+    out = copy.copy(tr)
+    out.face_mask = np.ascontiguousarray(mask, np.uint8)
+    return out
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_face_subset_matches_oracle(mode):
+    """The fold scenario's sampling (only the upper half of the cloth): face picks, points,
+    neighbours, loss and gradient against the oracle with the same mask; no sample lands on a
+    masked face and vertices touched only by masked faces get no gradient."""
+    mask = W.upper_half_mask(50)
+    tr, _ = parity.nudge_draws(masked(W.trajectory_50x50(T=3, n=4000, m=3000), mask))
+    g = run_traj(tr, mode)
+    ref = oracle.loss_traj(tr, mode=mode)
+    compare_traj(tr, g, ref, list(range(tr.T)), mode)
+    v, f, d, _ = to_dev(tr)
+    pts, fi, _ = L().dc_sample(v, f, d, check=True, face_mask=dev_mask(tr))
+    fi = fi.cpu().numpy()
+    assert np.all(mask[fi] == 1)
+    for t in range(tr.T):
+        r = oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t), tr.frame_targets(t)[:1],
+                         mode=1, grads=False, face_mask=mask)
+        parity.check_face_picks(fi[t], r["face_idx"], r["margin"])
+    kept = np.zeros(tr.V, bool)
+    kept[tr.faces[mask == 1].ravel()] = True
+    assert np.all(g["grad_verts"][:, ~kept] == 0.0)
+    # the backward-only call with the same mask reproduces the gradient
+    r = L().dc_loss_traj(v, f, d, to_dev(tr)[3], mode=mode, check=True,
+                         face_mask=dev_mask(tr))
+    gb = L().dc_loss_traj_bwd(v, f, d, to_dev(tr)[3], r["nn_ab"], r["nn_ba"],
+                              torch.ones(tr.T, device=DEV), mode=mode, check=True,
+                              face_mask=dev_mask(tr))
+    assert parity.rel_l2(gb.cpu().numpy(), g["grad_verts"]) < 1e-6
+
+
+def test_full_mask_changes_nothing_and_empty_subset_is_degenerate():
+    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=2, n=2000, m=2000))
+    a = run_traj(tr)
+    b = run_traj(masked(tr, np.ones(tr.F, np.uint8)))
+    np.testing.assert_array_equal(a["nn_ab"], b["nn_ab"])
+    np.testing.assert_array_equal(a["loss_frames"], b["loss_frames"])
+    v, f, d, y = to_dev(tr)
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj(v, f, d, y, check=True,
+                         face_mask=torch.zeros(tr.F, dtype=torch.uint8, device=DEV))
+    assert e.value.code == L().DC_EDEGENERATE
 
 
 @pytest.mark.parametrize("w", [[0.0, 0.0, 0.0, 1.0], [0.0, 1.5, 0.0, 0.5], [1.0, 0.0, 2.0, 0.0]])

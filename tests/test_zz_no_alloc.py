@@ -55,8 +55,8 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     _dev()
     L = _lib.lib()
     fake = ctypes.c_void_p(0x100000)  # never touched: the size check comes first
-    rc = L.dc_loss_traj_noalloc(fake, fake, fake, fake, 16, 2500, 4802, 10000, 10000, 0, None,
-                                None, fake, None, None, None, None, None)
+    rc = L.dc_loss_traj_noalloc(fake, fake, None, fake, fake, 16, 2500, 4802, 10000, 10000, 0,
+                                None, None, fake, None, None, None, None, None)
     assert rc == _lib.DC_ENOSPC
     assert "built-in scratch" in _lib.last_error()
 
