@@ -12,13 +12,15 @@ from . import _lib
 
 
 class DCLoss(torch.autograd.Function):
-    """loss_frames[t] = L_t(verts[t]); differentiable with respect to verts only."""
+    """loss_frames[t] = L_t(verts[t]); differentiable with respect to verts only. Frames
+    whose entry of frame_w is 0 are skipped (their L_t is reported as 0)."""
 
     @staticmethod
-    def forward(ctx, verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, face_mask=None):
+    def forward(ctx, verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, face_mask=None,
+                frame_w=None):
         verts = verts.detach().contiguous()
         r = _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode, grad=False, total=False,
-                              nn=True, face_mask=face_mask)
+                              nn=True, face_mask=face_mask, frame_w=frame_w)
         ctx.mode = mode
         ctx.face_mask = face_mask
         nn_ba = r["nn_ba"] if r["nn_ba"] is not None else r["nn_ab"]
@@ -32,13 +34,17 @@ class DCLoss(torch.autograd.Function):
                                   nn_ba if ctx.mode == _lib.BIDIR_MEAN else None,
                                   grad_frames.detach().float().contiguous(), mode=ctx.mode,
                                   face_mask=ctx.face_mask)
-        return g, None, None, None, None, None
+        return g, None, None, None, None, None, None
 
 
 def loss_traj(verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, frame_w=None,
               face_mask=None):
     """Differentiable sum_t w_t L_t (w_t = 1 by default) and the per-frame losses.
-    face_mask [F] (optional): sample only the faces with a nonzero entry."""
-    lf = DCLoss.apply(verts, faces, draws, targets, mode, face_mask)
-    w = torch.ones_like(lf) if frame_w is None else frame_w
+    face_mask [F] (optional): sample only the faces with a nonzero entry. Frames of weight 0
+    do no work in either direction (their L_t is reported as 0)."""
+    fw = None
+    if frame_w is not None:
+        fw = torch.as_tensor(frame_w, dtype=torch.float32, device=verts.device).contiguous()
+    lf = DCLoss.apply(verts, faces, draws, targets, mode, face_mask, fw)
+    w = torch.ones_like(lf) if fw is None else fw
     return (w * lf).sum(), lf
