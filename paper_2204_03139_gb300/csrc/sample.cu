@@ -220,8 +220,12 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
     bool bad_idx = false, bad_val = false;
 
     FF v = {0.0f, 0.0f};
-    for (int f = f0; f < f1; ++f)
-        v = ff_add1(v, face_weight(verts, faces, mask, V, f, bad_idx, bad_val));
+    // pass 1: the segment's area weights, kept in the thread's own slots of the CDF buffer
+    for (int f = f0; f < f1; ++f) {
+        const float a = face_weight(verts, faces, mask, V, f, bad_idx, bad_val);
+        cdf[f] = a;
+        v = ff_add1(v, a);
+    }
 
     // block-wide inclusive scan of the segment sums
 #pragma unroll
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
     FF run = warp > 0 ? ff_add(s_w[warp - 1], ex) : ex;
 
     for (int f = f0; f < f1; ++f) {
-        run = ff_add1(run, face_weight(verts, faces, mask, V, f, bad_idx, bad_val));
+        run = ff_add1(run, cdf[f]);  // pass 2 reads back this thread's own area weights
         cdf[f] = run.hi;
     }
     if (bad_idx || bad_val) set_status(&w.hdr->status, DC_EINVAL);
