@@ -1,0 +1,42 @@
+"""Pipelined loss + gradient over a stream of trajectories (GB300 only): every step's
+results equal the plain call's on the same inputs, with several steps in flight."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_pipeline_matches_plain_calls():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_03139_gb300 import _lib
+    from paper_2204_03139_gb300.pipeline import LossPipeline
+
+    dev = torch.device("cuda:0")
+    trs = [W.lift_trajectory(100 + k, 20, 4, 3000, 3000, name=f"p{k}") for k in range(5)]
+    tr0 = trs[0]
+    T, V, F, N, M = tr0.T, tr0.V, tr0.F, tr0.n(0), tr0.m(0)
+    pipe = LossPipeline(T, V, F, N, M, device=dev, depth=2)
+    host = [tuple(LossPipeline.pin(a) for a in (t.verts, t.faces, t.draws_tn3(), t.targets_tm3()))
+            for t in trs]
+    outs = [(LossPipeline.pinned((T, V, 3)), LossPipeline.pinned(1), LossPipeline.pinned(T))
+            for _ in trs]
+    events = []
+    for k in range(3):  # the same trajectories again: slots are reused while steps are in flight
+        for h, o in zip(host, outs):
+            events.append(pipe.submit(*h, grad_out=o[0], loss_out=o[1], frames_out=o[2]))
+        for e in events:
+            e.synchronize()
+        events.clear()
+        assert pipe.status() == _lib.DC_OK
+        for t, o in zip(trs, outs):
+            ref = _lib.dc_loss_traj(*(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+                                      (t.verts, t.faces, t.draws_tn3(), t.targets_tm3())))
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(o[2].numpy(), ref["loss_frames"].cpu().numpy())
+            np.testing.assert_array_equal(o[1].numpy(), ref["loss_total"].cpu().numpy())
+            g = ref["grad_verts"].cpu().numpy()
+            assert np.linalg.norm(o[0].numpy() - g) <= 1e-6 * np.linalg.norm(g)
