@@ -53,15 +53,19 @@ def parse():
     return p.parse_args()
 
 
-def make_workload(name, frames=None):
+def make_workload(name, frames=None, rank=0):
+    """The named workload; under torchrun every rank gets its own copy (its own seed)."""
+    from paper_2204_03139_gb300.ranks import rank_seed
+
+    sb = workloads.SEED_BASE
     if name == "trajectory_50x50":
-        return workloads.trajectory_50x50(T=frames or 40)
+        return workloads.trajectory_50x50(seed=rank_seed(sb + 2, rank), T=frames or 40)
     if name == "trajectory_100x100":
-        return workloads.trajectory_100x100(T=frames or 100)
+        return workloads.trajectory_100x100(seed=rank_seed(sb + 4, rank), T=frames or 100)
     if name == "single_frame":
-        return workloads.single_frame()
+        return workloads.single_frame(seed=rank_seed(sb + 1, rank))
     if name == "batched_uneven":
-        return workloads.batched_uneven()
+        return workloads.batched_uneven(seed=rank_seed(sb + 3, rank))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -205,7 +209,7 @@ def run_gpu(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    tr = make_workload(args.workload, args.frames)
+    tr = make_workload(args.workload, args.frames, rank)
     pairs = tr.pairs()
     T, V, F, N, M = tr.T, tr.V, tr.F, tr.n(0), tr.m(0)
 
@@ -254,13 +258,9 @@ def run_gpu(args, rank, world, dist):
     launches = _lib.launch_count() - launches0
     clk = clocks.stop()
     per = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(per)
-    if dist is not None:
-        import torch.distributed as td
+    from paper_2204_03139_gb300.ranks import max_over_ranks
 
-        tt = torch.tensor([total_ms], dtype=torch.float64)
-        td.all_reduce(tt, op=td.ReduceOp.MAX)
-        total_ms = float(tt[0])
+    total_ms = max_over_ranks(sum(per), dist)  # the job takes as long as its slowest rank
     ms_per_step = total_ms / args.steps
     value = world * pairs / (ms_per_step / 1e3)
 
@@ -390,7 +390,7 @@ def run_batched(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    trajs = workloads.batched_uneven()
+    trajs = make_workload("batched_uneven", rank=rank)
     pairs = sum(t.pairs() for t in trajs)
     frames = sum(t.T for t in trajs)
     dts = [DeviceTrajectory.from_host(t, dev) for t in trajs]
@@ -405,12 +405,17 @@ def run_batched(args, rank, world, dist):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     stream = torch.cuda.current_stream(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     for i in range(steps):
         flush.zero_()
         ev[i][0].record(stream)
         b.run()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     clk = clocks.stop()
     # graph replays launch nothing from the host: count and time the Chamfer kernel on the
     # same launch sequence issued eagerly
@@ -421,8 +426,10 @@ def run_batched(args, rank, world, dist):
     torch.cuda.synchronize()
     chamfer_ms, chamfer_n = _lib.prof_stop()
     launches = (_lib.launch_count() - launches0) // 3 * steps
+    from paper_2204_03139_gb300.ranks import max_over_ranks
+
     per = [a.elapsed_time(c) for a, c in ev]
-    ms = statistics.mean(per)
+    ms = max_over_ranks(statistics.mean(per), dist)
     # the plain per-frame form on the same inputs
     per_frame_loss(dts)
     torch.cuda.synchronize()
