@@ -230,6 +230,16 @@ int dc_loss_traj_noalloc(const float* verts, const int32_t* faces, const uint8_t
                          float* grad_verts, int32_t* nn_ab, int32_t* nn_ba, int32_t* status,
                          dc_stream_t stream);
 
+/*
+ * dc_fp32_fma_rate -- measured FP32 FMA throughput of the current device, in flop/s (an FMA
+ * counts 2). The paper has no counterpart: this is the measured cross-check of the peak the
+ * Chamfer kernel's roofline fraction is reported against. packed = 0 times scalar FMAs,
+ * packed = 1 packed f32x2 FMAs; every SM runs independent chains at full occupancy for `iters`
+ * iterations (16 lane operations per thread each; 20000 takes a few milliseconds). Runs on
+ * `stream` and waits for it; allocates nothing.
+ */
+int dc_fp32_fma_rate(int packed, int iters, double* flop_per_s, dc_stream_t stream);
+
 /* Description of the last failure on the calling thread ("" if none). */
 const char* dc_last_error(void);
 

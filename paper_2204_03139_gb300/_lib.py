@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
                 "dc_loss_traj_noalloc": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P,
                                              P, P]),
                 "dc_tune_set": (I, [P]),
+                "dc_fp32_fma_rate": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
                 "dc_tune_get": (I, [P]),
             }
             for name, (res, args) in sig.items():
@@ -335,3 +336,13 @@ def tune_get() -> int:
     t = dc_tune(0)
     _check(lib().dc_tune_get(ctypes.byref(t)))
     return int(t.warps_per_cta)
+
+
+def fp32_fma_rate(packed: bool, iters: int = 20000, device=None) -> float:
+    """Measured FP32 FMA throughput of the device in flop/s (scalar or packed f32x2 FMAs)."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    r = ctypes.c_double(0.0)
+    with torch.cuda.device(dev):
+        _check(lib().dc_fp32_fma_rate(int(bool(packed)), int(iters), ctypes.byref(r),
+                                      _stream(dev)))
+    return float(r.value)

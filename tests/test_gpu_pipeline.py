@@ -40,3 +40,17 @@ def test_pipeline_matches_plain_calls():
             np.testing.assert_array_equal(o[1].numpy(), ref["loss_total"].cpu().numpy())
             g = ref["grad_verts"].cpu().numpy()
             assert np.linalg.norm(o[0].numpy() - g) <= 1e-6 * np.linalg.norm(g)
+
+
+def test_fp32_fma_rate_is_near_the_fp32_peak():
+    """The measured FMA rate (the cross-check of the roofline's FP32 peak) lies between 30% and
+    110% of 2 x 128 lanes x SMs x 2.1 GHz, for scalar and packed FMAs."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_03139_gb300 import _lib
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    top = 2 * 128 * sms * 2.1e9
+    for packed in (False, True):
+        r = _lib.fp32_fma_rate(packed, iters=5000)
+        assert 0.3 * top < r < 1.1 * top, (packed, r / top)
