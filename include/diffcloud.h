@@ -76,6 +76,16 @@ size_t dc_workspace_size(int T, int V, int F, int N, int M);
  */
 
 /*
+ * dc_area_cdf -- the per-frame area weighting of the sampler (Sec. III-B): the face areas
+ * A_f = 1/2 |(p1 - p0) x (p2 - p0)| (0 outside face_mask, nullable) and their inclusive prefix
+ * sum, cdf [T][F] out (float32, the rounding of the exact prefix sum of the float32 areas;
+ * cdf[t][F-1] is the frame's total area A). ws sized by dc_workspace_size(T, V, F, 1, 0).
+ * A frame of zero total area is recorded as DC_EDEGENERATE (dc_ws_status).
+ */
+int dc_area_cdf(const float* verts, const int32_t* faces, const uint8_t* face_mask, int T,
+                int V, int F, float* cdf, void* ws, size_t ws_bytes, dc_stream_t stream);
+
+/*
  * dc_sample -- area-weighted surface sampling (Sec. III-B, Eq. 3).
  *   face_mask [F] nullable: sample only these faces (see above).
  *   points   [T][N][3] out: x_i of every frame.

@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
             sig = {
                 "dc_workspace_size": (S, [I, I, I, I, I]),
                 "dc_sample": (I, [P, P, P, P, I, I, I, I, P, P, P, P, S, P]),
+                "dc_area_cdf": (I, [P, P, P, I, I, I, P, P, S, P]),
                 "dc_chamfer_fwd": (I, [P, P, I, I, I, I, P, P, P, P, S, P]),
                 "dc_chamfer_bwd": (I, [P, P, P, P, I, I, I, I, P, P, P]),
                 "dc_loss_traj": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P, S,
@@ -164,6 +165,25 @@ def check_ws(ws: torch.Tensor):
 
 def dc_workspace_size(T, V, F, N, M) -> int:
     return int(lib().dc_workspace_size(T, V, F, N, M))
+
+
+def dc_area_cdf(verts, faces, face_mask=None, check=False):
+    """Per-frame area CDF (Sec. III-B): [T, F] float32 inclusive prefix sums of the face areas
+    (0 outside face_mask); the last entry of each row is the frame's total area."""
+    dev = _dev(verts)
+    _f32(verts, "verts"), _i32(faces, "faces")
+    T, V, F = verts.shape[0], verts.shape[1], faces.shape[0]
+    fm = _mask(face_mask, F)
+    cdf = torch.empty((T, F), dtype=torch.float32, device=dev)
+    nb = dc_workspace_size(T, V, F, 1, 0)
+    if nb == 0:
+        raise DCError(DC_EINVAL, "bad sizes")
+    ws = workspace(nb, dev)
+    _check(lib().dc_area_cdf(_ptr(verts), _ptr(faces), _ptr(fm), T, V, F, _ptr(cdf), _ptr(ws),
+                             ws.numel(), _stream(dev)))
+    if check:
+        check_ws(ws)
+    return cdf
 
 
 def dc_sample(verts, faces, draws, face_idx=True, bary=True, check=False, face_mask=None):

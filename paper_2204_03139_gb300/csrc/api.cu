@@ -282,10 +282,38 @@ int dc_ws_status(const void* ws, dc_stream_t stream) {
     return st;
 }
 
+int dc_area_cdf(const float* verts, const int32_t* faces, const uint8_t* face_mask, int T,
+                int V, int F, float* cdf, void* ws, size_t ws_bytes, dc_stream_t stream) {
+    if (T <= 0 || V <= 0 || F <= 0) return fail(DC_EINVAL, "sizes must be positive");
+    int rc = check_ptrs({verts, faces, cdf}, "dc_area_cdf");
+    if (rc) return rc;
+    UniformArgs a{};
+    a.verts = verts;
+    a.faces = faces;
+    a.mask = face_mask;
+    a.T = T;
+    a.V = V;
+    a.F = F;
+    a.N = 1;  // no sampling: the smallest valid layout
+    a.M = 0;
+    a.mode = DC_BIDIR_MEAN;
+    rc = run_uniform(a, PH_AREA, 0, nullptr, ws, ws_bytes, stream);
+    if (rc) return rc;
+    // the CDFs of the frames lie back to back in the workspace (frame t at t F)
+    Sizes sz;
+    long long sub[3];
+    int spu = 0;
+    uniform_sizes(T, V, F, 1, 0, sz, sub, spu);
+    const Ws w = make_ws(ws, make_layout(sz));
+    cudaError_t e = cudaMemcpyAsync(cdf, w.cdf, sizeof(float) * (size_t)T * F,
+                                    cudaMemcpyDeviceToDevice, stream);
+    if (e) return cuda_fail(e, "dc_area_cdf");
+    return DC_OK;
+}
+
 int dc_sample(const float* verts, const int32_t* faces, const uint8_t* face_mask,
-              const float* draws, int T, int V, int F,
-              int N, float* points, int32_t* face_idx, float* bary, void* ws, size_t ws_bytes,
-              dc_stream_t stream) {
+              const float* draws, int T, int V, int F, int N, float* points, int32_t* face_idx,
+              float* bary, void* ws, size_t ws_bytes, dc_stream_t stream) {
     if (T <= 0 || V <= 0 || F <= 0 || N <= 0) return fail(DC_EINVAL, "sizes must be positive");
     int rc = check_ptrs({verts, faces, draws, points}, "dc_sample");
     if (rc) return rc;

@@ -97,6 +97,34 @@ def test_trajectory_50x50_weights_total():
 
 
 # ---------------------------------------------------------------------------------------------
+# a1: the area CDF against the oracle
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["50x50", "100x100", "masked", "warped"])
+def test_area_cdf_within_bound_of_the_oracle(case):
+    """max |C_gpu - C_oracle| / A <= 2.5e-7, so that the 1e-6 face-pick window covers every
+    float32 disagreement; the GPU's C_f is the float32 rounding of the exact prefix sum of its
+    float32 areas, so it stays this close however many faces there are."""
+    if case == "100x100":
+        tr = W.trajectory_100x100(T=2)
+    else:
+        tr = W.trajectory_50x50(T=3, n=1000, m=1000)
+    mask = W.upper_half_mask(50) if case == "masked" else None
+    verts = tr.verts.copy()
+    if case == "warped":  # very unequal face areas
+        verts[..., 0] = verts[..., 0] ** 3
+    v = torch.from_numpy(verts).to(DEV)
+    f = torch.from_numpy(tr.faces).to(DEV)
+    m = None if mask is None else torch.from_numpy(mask).to(DEV)
+    c = L().dc_area_cdf(v, f, face_mask=m, check=True).cpu().numpy().astype(np.float64)
+    for t in range(tr.T):
+        ref = oracle.area_cdf(oracle.face_areas(verts[t], tr.faces, mask))
+        A = ref[-1]
+        assert np.max(np.abs(c[t] - ref)) / A <= 2.5e-7
+        if mask is not None:
+            assert np.all(np.diff(np.concatenate([[0.0], c[t]]))[mask == 0] == 0.0)
+
+
+# ---------------------------------------------------------------------------------------------
 # sampling from a face subset (Sec. IV-F fold scenario)
 # ---------------------------------------------------------------------------------------------
 def masked(tr, mask):
