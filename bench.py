@@ -149,6 +149,27 @@ def calibrate_oracle(tr, seconds):
         n_s = min(n_full, int(n_s * max(1.3, min(4.0, (seconds / max(el, 1e-4)) ** 0.5))))
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (Arm hosts may only give the implementer and part numbers)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model", "Hardware"):
+        for line in info:
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    parts = {ln.split(":", 1)[0].strip(): ln.split(":", 1)[1].strip() for ln in info if ":" in ln}
+    if "CPU implementer" in parts:
+        # Arm's part numbers for its Neoverse cores
+        names = {"0xd0c": "Neoverse N1", "0xd40": "Neoverse V1", "0xd49": "Neoverse N2",
+                 "0xd4f": "Neoverse V2", "0xd84": "Neoverse V3", "0xd8e": "Neoverse N3"}
+        part = parts.get("CPU part", "?")
+        name = names.get(part) if parts["CPU implementer"] == "0x41" else None
+        return name or f"implementer {parts['CPU implementer']} part {part}"
+    return "unknown"
+
+
 def cpu_baseline(tr, seconds):
     import oracle
 
@@ -159,7 +180,21 @@ def cpu_baseline(tr, seconds):
         pairs += oracle_sample_step(tr, k, n_s)
         k += 1
     el = time.perf_counter() - t0
-    return {"value": pairs / el, "unit": "pairs/s", "cores": oracle.num_threads(),
+    cores = oracle.num_threads()
+    # the same on one core, on a shorter sample (about a tenth of the time)
+    oracle.set_num_threads(1)
+    try:
+        n1, _ = calibrate_oracle(tr, max(0.5, seconds / 20))
+        t1, p1, k1 = time.perf_counter(), 0, 0
+        while time.perf_counter() - t1 < seconds / 10 or k1 == 0:
+            p1 += oracle_sample_step(tr, k1, n1)
+            k1 += 1
+        one = {"value": p1 / (time.perf_counter() - t1), "sample": f"{k1} frame evaluations, "
+               f"first {n1} draws and targets each"}
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": pairs / el, "unit": "pairs/s", "cores": cores,
+            "cpu_model": cpu_model(), "one_core": one,
             "kind": "oracle",
             "sample": f"{k} frame evaluations of {tr.name} (frame k mod {tr.T}), each with its "
                       f"first {n_s} draws and first {n_s} targets"

@@ -65,11 +65,17 @@ def lib() -> ctypes.CDLL:
         _lib.orc_bary.restype = None
         _lib.orc_bary.argtypes = [ctypes.c_float, ctypes.c_float, P]
         _lib.orc_num_threads.restype = I
+        _lib.orc_set_num_threads.restype = None
+        _lib.orc_set_num_threads.argtypes = [I]
     return _lib
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().orc_set_num_threads(int(n))
 
 
 def _p(a):

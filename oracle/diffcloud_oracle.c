@@ -53,6 +53,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the parallel neighbour search (for timing on one core or all of them). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Sec. III-B: area of every face, 1/2 |(p2 - p1) x (p3 - p1)|, in double. */
 void orc_face_areas(const float* verts, const int32_t* faces, int F, double* area) {
     for (int f = 0; f < F; ++f) {
