@@ -428,6 +428,7 @@ def run_gpu(args, rank, world, dist):
                                      "Eq. 1 bidirectional mean, fwd + vertex grad"}),
             "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
                                                                     int(0.99 * len(srt)))]},
+            "traj_loss_grad_per_s": world * 1e3 / ms_per_step,
             "roofline": roof,
             "clocks": clk,
             "gpu_launches": launches,
