@@ -50,6 +50,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--mode", default="eq1", choices=["eq1", "eq2"],
                    help="eq1: Eq. 1 bidirectional mean (default); eq2: Eq. 2 unidirectional sum")
+    p.add_argument("--item-pairs", type=float, default=16e9,
+                   help="serving: time slice of a long request, in point pairs")
+    p.add_argument("--batch-pairs", type=float, default=16e9,
+                   help="serving: batch size while the queue is short, in point pairs")
     p.add_argument("--frames", type=int, default=None,
                    help="use only the first FRAMES frames of the trajectory (profiling runs)")
     return p.parse_args()
@@ -578,7 +582,8 @@ def run_serving(args, rank, world, dist):
 
     def run_rate(rate, seed):
         reqs = arrivals(rate, seed)
-        srv = Server(dev, hbm_budget=120 << 30)
+        srv = Server(dev, hbm_budget=120 << 30, item_pairs=args.item_pairs,
+                     max_batch_pairs=args.batch_pairs)
         futs = []
         t0 = time.perf_counter()
         for at, tr in reqs:
@@ -598,7 +603,8 @@ def run_serving(args, rank, world, dist):
                 "mean_batch_requests": float(np.mean([r.batch_requests for r in res]))}
 
     # warm-up: build pinned copies, first launches
-    w = Server(dev, hbm_budget=120 << 30)
+    w = Server(dev, hbm_budget=120 << 30, item_pairs=args.item_pairs,
+               max_batch_pairs=args.batch_pairs)
     for tr in small + big:
         w.submit(tr).result(timeout=600)
     w.close()
@@ -623,7 +629,8 @@ def run_serving(args, rank, world, dist):
             "steps": head["requests"], "warmup": len(small) + len(big),
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving_poisson", "mix": "90% 50x50 T40 10k x 10k, "
+            "config": {"workload": "serving_poisson", "item_pairs": args.item_pairs,
+                       "batch_pairs": args.batch_pairs, "mix": "90% 50x50 T40 10k x 10k, "
                        "10% 100x100 T100 32768 x 32768", "hbm_budget_gb": 120,
                        "latency": "from arrival to the result on the host, queueing included"},
             "serving": results,

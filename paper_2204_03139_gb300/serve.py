@@ -10,10 +10,12 @@ every optimisation). The server batches continuously:
   - time slicing: an admitted request is cut into items of consecutive frames of at most
     `item_pairs` point pairs, so that a long request cannot hold the GPU for its whole
     duration (one persistent Chamfer launch occupies every SM until it ends);
-  - batching: whenever one of the compute streams is free, admitted items of the same mode,
-    oldest first, up to `max_batch_pairs`, go into one planned launch sequence
-    (dc_batch_plan / dc_batch_run): one persistent Chamfer launch covers all their frames,
-    whatever their sizes;
+  - batching: whenever one of the compute streams is free, admitted items of the same mode, up
+    to `max_batch_pairs`, go into one planned launch sequence (dc_batch_plan / dc_batch_run):
+    one persistent Chamfer launch covers all their frames, whatever their sizes. Requests are
+    served shortest remaining work first (a short request passes a long one; long ones run
+    one after another instead of sharing the GPU and all finishing late), except that a
+    request waiting longer than `max_wait_s` goes first, so that long ones never starve;
   - overlap: batches on different streams run at the same time while new requests are
     admitted and copied in; finished batches resolve their requests' futures and release their
     memory, which admits the next requests.
@@ -110,8 +112,8 @@ class Server:
     """Continuous-batching loss+gradient server on one GPU."""
 
     def __init__(self, device="cuda:0", hbm_budget: int = 120 << 30, streams: int = 2,
-                 max_batch_items: int = 512, max_batch_pairs: int = 8 * 10**9,
-                 item_pairs: int = 4 * 10**9):
+                 max_batch_items: int = 512, max_batch_pairs: int = 16 * 10**9,
+                 item_pairs: int = 16 * 10**9, max_wait_s: float = 0.2):
         """max_batch_pairs: batch size when the queue is short; under load batches grow up
         to 8x that. item_pairs: the time slice a long request is cut into."""
         self.device = torch.device(device)
@@ -119,6 +121,7 @@ class Server:
         self.max_batch_items = max_batch_items
         self.max_batch_pairs = max_batch_pairs
         self.item_pairs = item_pairs
+        self.max_wait_s = max_wait_s
         self._copy = torch.cuda.Stream(self.device)
         self._streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
         self._busy = [None] * streams
@@ -252,24 +255,31 @@ class Server:
             # (fewer launches per pair)
             waiting = len({id(it.req) for it in self._admitted})
             cap = self.max_batch_pairs * max(1, min(8, waiting // 8))
-            # round robin over requests in arrival order: at most one item of each request
-            # per pass, so a short request is not queued behind a long one's items
-            take, taken, pairs, full = [], set(), 0, False
-            while not full:
-                seen, added = set(), False
-                for it in self._admitted:
-                    if it.req.mode != mode or id(it.req) in seen or id(it) in taken:
-                        continue
-                    seen.add(id(it.req))
+            # shortest remaining work first; requests that waited past max_wait_s first of all
+            # (oldest first among them), so that long ones cannot starve
+            now = time.perf_counter()
+            reqs, items = {}, collections.defaultdict(list)
+            for it in self._admitted:
+                if it.req.mode == mode:
+                    reqs[id(it.req)] = it.req
+                    items[id(it.req)].append(it)
+            remaining = {k: sum(it.pairs for it in v) for k, v in items.items()}
+
+            def priority(k):
+                r = reqs[k]
+                old = now - r.arrival > self.max_wait_s
+                return (0, r.arrival, 0) if old else (1, remaining[k], r.arrival)
+
+            take, pairs = [], 0
+            for k in sorted(reqs, key=priority):
+                for it in items[k]:
                     if take and (len(take) >= self.max_batch_items or pairs + it.pairs > cap):
-                        full = True
                         break
                     take.append(it)
-                    taken.add(id(it))
                     pairs += it.pairs
-                    added = True
-                if not added:
-                    break
+                else:
+                    continue
+                break
             for it in take:
                 self._admitted.remove(it)
             stream = self._streams[s_idx]
