@@ -184,6 +184,7 @@ struct MinBlocks {
 template <bool BIDIR, int W>
 __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
     k_chamfer(Ws w) {
+    pdl_entry();
     constexpr int THREADS = 32 * W;
     constexpr int WARPS = W;
     constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * W;
@@ -415,19 +416,16 @@ cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, in
     if (grid > total_sub) grid = total_sub;
     prof_before(s);
     const bool bi = mode == DC_BIDIR_MEAN;
-    if (warps == 4) {
-        if (bi) k_chamfer<true, 4><<<grid, 128, 0, s>>>(w);
-        else k_chamfer<false, 4><<<grid, 128, 0, s>>>(w);
-    } else if (warps == 2) {
-        if (bi) k_chamfer<true, 2><<<grid, 64, 0, s>>>(w);
-        else k_chamfer<false, 2><<<grid, 64, 0, s>>>(w);
-    } else {
-        if (bi) k_chamfer<true, 1><<<grid, 32, 0, s>>>(w);
-        else k_chamfer<false, 1><<<grid, 32, 0, s>>>(w);
-    }
+    cudaError_t e;
+    if (warps == 4)
+        e = launch_pdl(bi ? k_chamfer<true, 4> : k_chamfer<false, 4>, grid, 128, 0, s, w);
+    else if (warps == 2)
+        e = launch_pdl(bi ? k_chamfer<true, 2> : k_chamfer<false, 2>, grid, 64, 0, s, w);
+    else
+        e = launch_pdl(bi ? k_chamfer<true, 1> : k_chamfer<false, 1>, grid, 32, 0, s, w);
     prof_after(s);
     count_launch();
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 void set_tuned_warps(int warps) { g_tuned_warps = warps; }

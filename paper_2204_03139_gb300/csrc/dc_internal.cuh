@@ -128,6 +128,35 @@ struct Ws {
 
 Ws make_ws(void* base, const Layout& L);
 
+// ---------------------------------------------------------------------------------------
+// Programmatic dependent launch. Every kernel of the library is launched with programmatic
+// stream serialisation and starts with pdl_entry(): it first waits until the grid before it
+// on the stream has completed and its memory is visible (so the stream order holds for every
+// access), then lets the next grid be launched. The next grid's launch latency thus overlaps
+// this grid's run instead of following its end. A kernel launched without the attribute (or
+// after a copy or an event) passes the wait at once.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 __host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
 

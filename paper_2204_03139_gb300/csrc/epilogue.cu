@@ -58,6 +58,7 @@ __device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
 }
 
 __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
+    pdl_entry();
     extern __shared__ float s_acc[];
     __shared__ float s_red[EPI_THREADS / 32];
     const int k = blockIdx.x / e.slices, sl = blockIdx.x - k * e.slices;
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
 
 // gradient of frame k = sum over its slices, in slice order
 __global__ void __launch_bounds__(256) k_grad_reduce(Ws w, int n_frames, int slices, int vstride) {
+    pdl_entry();
     const long long n = (long long)n_frames * vstride;
     for (long long t = blockIdx.x * 256LL + threadIdx.x; t < n; t += (long long)gridDim.x * 256) {
         const int k = (int)(t / vstride), v = (int)(t - (long long)k * vstride);
@@ -262,6 +264,7 @@ constexpr int LOSS_THREADS = 1024;
 
 __global__ void __launch_bounds__(LOSS_THREADS) k_frame_loss(Ws w, int n_frames, int slices,
                                                              int bidir, float* total) {
+    pdl_entry();
     __shared__ float s_red[LOSS_THREADS / 32];
     float t = 0.f, tc = 0.f;
     for (int k = threadIdx.x; k < n_frames; k += LOSS_THREADS) {
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_frame_loss(Ws w, int n_frames,
 __global__ void __launch_bounds__(256) k_cbwd_rows(const float* a, const float* b,
                                                    const int* nn_ab, int T, int N, int M,
                                                    int bidir, const float* g, float* grad) {
+    pdl_entry();
     const long long n = (long long)T * N;
     for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
         const int t = (int)(e / N);
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(256) k_cbwd_rows(const float* a, const float* 
 __global__ void __launch_bounds__(256) k_cbwd_cols(const float* a, const float* b,
                                                    const int* nn_ba, int T, int N, int M,
                                                    const float* g, float* grad) {
+    pdl_entry();
     const long long n = (long long)T * M;
     for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
         const int t = (int)(e / M);
@@ -352,32 +357,35 @@ cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, in
     const size_t need = (size_t)max_v * 3 * sizeof(float);
     a.use_smem = grad && need <= (size_t)g_smem_limit[dev];
     a.vstride = 3 * max_v;
-    k_epilogue<<<n_frames * slices, EPI_THREADS, a.use_smem ? need : 0, s>>>(w, a);
+    cudaError_t e = launch_pdl(k_epilogue, n_frames * slices, EPI_THREADS,
+                               a.use_smem ? need : 0, s, w, a);
     count_launch();
-    if (flags & EPI_LOSS) {
-        k_frame_loss<<<1, LOSS_THREADS, 0, s>>>(w, n_frames, slices, a.bidir, total);
+    if (!e && (flags & EPI_LOSS)) {
+        e = launch_pdl(k_frame_loss, 1, LOSS_THREADS, 0, s, w, n_frames, slices, (int)a.bidir,
+                       total);
         count_launch();
     }
-    if (a.use_smem && slices > 1) {
-        k_grad_reduce<<<grid_for((long long)n_frames * a.vstride, 256), 256, 0, s>>>(
-            w, n_frames, slices, a.vstride);
+    if (!e && a.use_smem && slices > 1) {
+        e = launch_pdl(k_grad_reduce, grid_for((long long)n_frames * a.vstride, 256), 256, 0, s,
+                       w, n_frames, slices, a.vstride);
         count_launch();
     }
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 cudaError_t launch_chamfer_bwd_points(const float* a, const float* b, const int* nn_ab,
                                       const int* nn_ba, int T, int N, int M, int mode,
                                       const float* g, float* grad_a, cudaStream_t s) {
     const int bidir = mode == DC_BIDIR_MEAN;
-    k_cbwd_rows<<<grid_for((long long)T * N, 256), 256, 0, s>>>(a, b, nn_ab, T, N, M, bidir, g,
-                                                                 grad_a);
+    cudaError_t e = launch_pdl(k_cbwd_rows, grid_for((long long)T * N, 256), 256, 0, s, a, b,
+                               nn_ab, T, N, M, bidir, g, grad_a);
     count_launch();
-    if (bidir) {
-        k_cbwd_cols<<<grid_for((long long)T * M, 256), 256, 0, s>>>(a, b, nn_ba, T, N, M, g,
-                                                                     grad_a);
+    if (!e && bidir) {
+        e = launch_pdl(k_cbwd_cols, grid_for((long long)T * M, 256), 256, 0, s, a, b, nn_ba, T,
+                       N, M, g, grad_a);
         count_launch();
     }
+    if (e) return e;
     return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ __device__ __forceinline__ bool coord_ok(float v) { return fabsf(v) <= COORD_MAX
 constexpr int BUILD_THREADS = 1024;
 
 __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, Ws w) {
+    pdl_entry();
     __shared__ int s_warp[BUILD_THREADS / 32];
     __shared__ int s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -201,6 +202,7 @@ __device__ __forceinline__ float face_weight(const float* __restrict__ verts,
 constexpr int CDF_THREADS = 1024;
 
 __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
+    pdl_entry();
     __shared__ FF s_w[32];
     const FrameDesc* fr = w.frames + blockIdx.x;
     const float* verts = fr->verts;
@@ -358,6 +360,7 @@ __device__ __forceinline__ void stage_target(const Ws& w, const FrameDesc* fr, i
 }
 
 __global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows) {
+    pdl_entry();
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.rowpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
@@ -366,6 +369,7 @@ __global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows) {
 }
 
 __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
+    pdl_entry();
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < cols; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.colpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
@@ -378,6 +382,7 @@ __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
 constexpr int STAGE_THREADS = 512;
 
 __global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int rows, int cols) {
+    pdl_entry();
     extern __shared__ float s_cdf[];
     const int k = blockIdx.x / slices, sl = blockIdx.x - k * slices;
     const FrameDesc* fr = w.frames + k;
@@ -410,9 +415,9 @@ int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s) {
-    k_build_uniform<<<1, BUILD_THREADS, 0, s>>>(a, w);
+    cudaError_t e = launch_pdl(k_build_uniform, 1, BUILD_THREADS, 0, s, a, w);
     count_launch();
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 cudaError_t launch_reset(const Ws& w, cudaStream_t s) {
@@ -420,21 +425,21 @@ cudaError_t launch_reset(const Ws& w, cudaStream_t s) {
 }
 
 cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s) {
-    k_area_cdf<<<n_frames, CDF_THREADS, 0, s>>>(w);
+    cudaError_t e = launch_pdl(k_area_cdf, n_frames, CDF_THREADS, 0, s, w);
     count_launch();
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s) {
-    k_sample<<<grid_for(rows, 256), 256, 0, s>>>(w, n_frames, rows);
+    cudaError_t e = launch_pdl(k_sample, grid_for(rows, 256), 256, 0, s, w, n_frames, rows);
     count_launch();
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s) {
-    k_targets<<<grid_for(cols, 256), 256, 0, s>>>(w, n_frames, cols);
+    cudaError_t e = launch_pdl(k_targets, grid_for(cols, 256), 256, 0, s, w, n_frames, cols);
     count_launch();
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
@@ -459,9 +464,10 @@ cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int r
         if (!e && cols) e = launch_targets(w, n_frames, cols, s);
         return e;
     }
-    k_stage<<<n_frames * slices, STAGE_THREADS, need, s>>>(w, slices, rows > 0, cols > 0);
+    cudaError_t e = launch_pdl(k_stage, n_frames * slices, STAGE_THREADS, need, s, w, slices,
+                               (int)(rows > 0), (int)(cols > 0));
     count_launch();
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 }  // namespace dc
