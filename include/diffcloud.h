@@ -250,6 +250,14 @@ int dc_loss_traj_noalloc(const float* verts, const int32_t* faces, const uint8_t
  */
 int dc_fp32_fma_rate(int packed, int iters, double* flop_per_s, dc_stream_t stream);
 
+/*
+ * dc_test_inject_stall -- for testing the failure detection (the paper has no counterpart).
+ * The next Chamfer launch in the process never requests the first target chunk of each CTA,
+ * so the bounded waits on it give up after 2 s: the call completes, its workspace reports
+ * DC_ETIMEOUT (dc_ws_status), and the device stays usable for the next call.
+ */
+int dc_test_inject_stall(void);
+
 /* Description of the last failure on the calling thread ("" if none). */
 const char* dc_last_error(void);
 

@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
                 "dc_loss_traj_noalloc": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P,
                                              P, P]),
                 "dc_tune_set": (I, [P]),
+                "dc_test_inject_stall": (I, []),
                 "dc_fp32_fma_rate": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
                 "dc_tune_get": (I, [P]),
             }
@@ -366,3 +367,8 @@ def fp32_fma_rate(packed: bool, iters: int = 20000, device=None) -> float:
         _check(lib().dc_fp32_fma_rate(int(bool(packed)), int(iters), ctypes.byref(r),
                                       _stream(dev)))
     return float(r.value)
+
+
+def test_inject_stall():
+    """Make the next Chamfer launch's bounded waits give up (DC_ETIMEOUT), for tests."""
+    _check(lib().dc_test_inject_stall())

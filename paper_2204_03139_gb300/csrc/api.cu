@@ -673,3 +673,11 @@ extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
     }
     return DC_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// test of the device-side failure detection
+// ---------------------------------------------------------------------------------------
+extern "C" int dc_test_inject_stall(void) {
+    dc::inject_stall();
+    return DC_OK;
+}

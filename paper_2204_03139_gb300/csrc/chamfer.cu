@@ -11,6 +11,8 @@
 // the one thread's 16-row group (columns) that holds it, with bit-identical arithmetic.
 #include <math.h>
 
+#include <atomic>
+
 #include "dc_internal.cuh"
 
 namespace dc {
@@ -183,7 +185,7 @@ struct MinBlocks {
 
 template <bool BIDIR, int W>
 __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
-    k_chamfer(Ws w) {
+    k_chamfer(Ws w, int stall) {
     pdl_entry();
     constexpr int THREADS = 32 * W;
     constexpr int WARPS = W;
@@ -240,6 +242,9 @@ __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
             const int c_hi = (s_u.sub_hi - 1) / SUBS_PER_CHUNK;
             for (int c = c_lo; c <= min(c_hi, c_lo + 1); ++c) {
                 const int b = (seq + c - c_lo) & 1;
+                // test of the bounded waits: the first chunk is never requested, so its
+                // barrier never completes and every wait on it gives up (DC_ETIMEOUT)
+                if (stall && seq == 0 && c == c_lo) continue;
                 mbar_expect_tx(&s_bar[b], 3 * PLANE_BYTES);
                 for (int p = 0; p < 3; ++p)
                     bulk_g2s(&s_t[b][p][0], s_u.tx + 2LL * p * s_u.Mpad + 2LL * c * CHUNK,
@@ -375,6 +380,8 @@ int occupancy() {
 
 int width_index(int warps) { return warps == 4 ? 2 : (warps == 2 ? 1 : 0); }
 
+std::atomic<int> g_stall_next{0};  // dc_test_inject_stall: the next launch stalls
+
 int g_tuned_warps = 0;  // process-wide CTA width set by dc_tune_set (0: automatic)
 
 }  // namespace
@@ -409,6 +416,7 @@ int choose_warps(int mode, long long sub_w4, long long sub_w2, long long sub_w1)
 
 cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, int warps,
                            cudaStream_t s) {
+    const int stall = g_stall_next.exchange(0);
     // total_sub is an upper bound here (frames skipped on the device carry no work); CTAs
     // beyond the work exit at once
     if (n_units <= 0 || total_sub <= 0) return cudaSuccess;
@@ -418,17 +426,21 @@ cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, in
     const bool bi = mode == DC_BIDIR_MEAN;
     cudaError_t e;
     if (warps == 4)
-        e = launch_pdl(bi ? k_chamfer<true, 4> : k_chamfer<false, 4>, grid, 128, 0, s, w);
+        e = launch_pdl(bi ? k_chamfer<true, 4> : k_chamfer<false, 4>, grid, 128, 0, s, w,
+                       stall);
     else if (warps == 2)
-        e = launch_pdl(bi ? k_chamfer<true, 2> : k_chamfer<false, 2>, grid, 64, 0, s, w);
+        e = launch_pdl(bi ? k_chamfer<true, 2> : k_chamfer<false, 2>, grid, 64, 0, s, w,
+                       stall);
     else
-        e = launch_pdl(bi ? k_chamfer<true, 1> : k_chamfer<false, 1>, grid, 32, 0, s, w);
+        e = launch_pdl(bi ? k_chamfer<true, 1> : k_chamfer<false, 1>, grid, 32, 0, s, w,
+                       stall);
     prof_after(s);
     count_launch();
     return e ? e : cudaGetLastError();
 }
 
 void set_tuned_warps(int warps) { g_tuned_warps = warps; }
+void inject_stall() { g_stall_next.store(1); }
 int tuned_warps() { return g_tuned_warps; }
 
 }  // namespace dc

@@ -199,6 +199,7 @@ int chamfer_grid(int mode, int warps);
 // every resident CTA at least a few sub-chunks; sub_w4 is the work at width 4
 int choose_warps(int mode, long long sub_w4, long long sub_w2, long long sub_w1);
 void set_tuned_warps(int warps);  // 0: automatic
+void inject_stall();              // the next Chamfer launch never gets its first chunk
 int tuned_warps();
 // epilogue: neighbour recovery (rescan), loss partials, gradient scatter
 enum : int { EPI_RESCAN = 1, EPI_LOSS = 2, EPI_GRAD = 4 };

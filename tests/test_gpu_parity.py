@@ -97,6 +97,26 @@ def test_trajectory_50x50_weights_total():
 
 
 # ---------------------------------------------------------------------------------------------
+# failure detection without a GPU fault
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.timeout(120)
+def test_bounded_wait_gives_up_with_a_timeout_status_and_the_device_stays_usable():
+    """The Chamfer kernel's waits for its target chunks are bounded (2 s). A launch whose
+    first chunk is never requested must end with DC_ETIMEOUT in the workspace status, and the
+    next call on the same context must produce the normal result."""
+    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=2, n=2000, m=2000))
+    v, f, d, y = to_dev(tr)
+    good = L().dc_loss_traj(v, f, d, y, check=True)
+    ref_loss = good["loss_frames"].cpu().numpy().copy()
+    L().test_inject_stall()
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj(v, f, d, y, check=True)
+    assert e.value.code == L().DC_ETIMEOUT
+    again = L().dc_loss_traj(v, f, d, y, check=True)
+    np.testing.assert_array_equal(again["loss_frames"].cpu().numpy(), ref_loss)
+
+
+# ---------------------------------------------------------------------------------------------
 # a1: the area CDF against the oracle
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("case", ["50x50", "100x100", "masked", "warped"])
