@@ -75,6 +75,15 @@ def make_workload(name, frames=None, rank=0):
     raise SystemExit(f"unknown workload {name}")
 
 
+def arm_config(tr, args, world):
+    """The workload's config, the same for the GB300 arm and the reference arm."""
+    return config_of(tr, {"parallelism": f"{world} independent trajectories"
+                          if world > 1 else "1 GPU",
+                          "mode": "Eq. 2 unidirectional sum, fwd + vertex grad"
+                          if args.mode == "eq2" else
+                          "Eq. 1 bidirectional mean, fwd + vertex grad"})
+
+
 def config_of(tr, extra=None):
     c = {"workload": tr.name, "frames": tr.T, "grid": f"{int(round(tr.V ** 0.5))}x"
          f"{int(round(tr.V ** 0.5))}", "V": tr.V, "F": tr.F, "N": tr.n(0), "M": tr.m(0),
@@ -130,23 +139,23 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle
 # ---------------------------------------------------------------------------------------------
-def oracle_sample_step(tr, k, n_s):
+def oracle_sample_step(tr, k, n_s, mode=0):
     """One bounded sample: frame k % T with its first n_s draws and first n_s targets."""
     import oracle
 
     t = k % tr.T
     oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t)[:n_s], tr.frame_targets(t)[:n_s],
-                 details=False)
+                 mode=mode, details=False)
     return n_s * n_s
 
 
-def calibrate_oracle(tr, seconds):
+def calibrate_oracle(tr, seconds, mode=0):
     """Largest sample size (up to a full frame) whose oracle step takes about `seconds`."""
     n_full = min(tr.n(0), tr.m(0))
     n_s = 1000
     while True:
         t0 = time.perf_counter()
-        oracle_sample_step(tr, 0, n_s)
+        oracle_sample_step(tr, 0, n_s, mode)
         el = time.perf_counter() - t0
         if el >= seconds or n_s >= n_full:
             return n_s, el
@@ -174,24 +183,24 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def cpu_baseline(tr, seconds):
+def cpu_baseline(tr, seconds, mode=0):
     import oracle
 
-    n_s, _ = calibrate_oracle(tr, min(seconds, 5.0))
+    n_s, _ = calibrate_oracle(tr, min(seconds, 5.0), mode)
     t0 = time.perf_counter()
     pairs, k = 0, 0
     while time.perf_counter() - t0 < seconds or k == 0:
-        pairs += oracle_sample_step(tr, k, n_s)
+        pairs += oracle_sample_step(tr, k, n_s, mode)
         k += 1
     el = time.perf_counter() - t0
     cores = oracle.num_threads()
     # the same on one core, on a shorter sample (about a tenth of the time)
     oracle.set_num_threads(1)
     try:
-        n1, _ = calibrate_oracle(tr, max(0.5, seconds / 20))
+        n1, _ = calibrate_oracle(tr, max(0.5, seconds / 20), mode)
         t1, p1, k1 = time.perf_counter(), 0, 0
         while time.perf_counter() - t1 < seconds / 10 or k1 == 0:
-            p1 += oracle_sample_step(tr, k1, n1)
+            p1 += oracle_sample_step(tr, k1, n1, mode)
             k1 += 1
         one = {"value": p1 / (time.perf_counter() - t1), "sample": f"{k1} frame evaluations, "
                f"first {n1} draws and targets each"}
@@ -212,16 +221,17 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
-    tr = make_workload(args.workload)
+    tr = make_workload(args.workload, args.frames)
+    mode = oracle.UNIDIR_SUM if args.mode == "eq2" else oracle.BIDIR_MEAN
     # size each step so that warmup + steps take about two minutes
     per_step = max(0.02, min(1.0, 120.0 / max(1, args.steps + args.warmup)))
-    n_s, _ = calibrate_oracle(tr, per_step)
+    n_s, _ = calibrate_oracle(tr, per_step, mode)
     for k in range(args.warmup):
-        oracle_sample_step(tr, k, n_s)
+        oracle_sample_step(tr, k, n_s, mode)
     t0 = time.perf_counter()
     pairs = 0
     for k in range(args.steps):
-        pairs += oracle_sample_step(tr, k, n_s)
+        pairs += oracle_sample_step(tr, k, n_s, mode)
     el = time.perf_counter() - t0
     value = pairs / el
     cores = oracle.num_threads()
@@ -231,9 +241,11 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config_of(tr, {"sample": sample}),
+            "config": arm_config(tr, args, world),
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model()},
+            "note": "the FP64 oracle on the host cores; each step is a bounded sample of the "
+                    "workload (see cpu_baseline.sample), timed on the host clock",
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -425,11 +437,7 @@ def run_gpu(args, rank, world, dist):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(tr, {"parallelism": f"{world} independent trajectories"
-                                     if world > 1 else "1 GPU",
-                                     "mode": "Eq. 2 unidirectional sum, fwd + vertex grad"
-                                     if mode == _lib.UNIDIR_SUM else
-                                     "Eq. 1 bidirectional mean, fwd + vertex grad"}),
+            "config": arm_config(tr, args, world),
             "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
                                                                     int(0.99 * len(srt)))]},
             "traj_loss_grad_per_s": world * 1e3 / ms_per_step,
@@ -440,7 +448,8 @@ def run_gpu(args, rank, world, dist):
             "e2e_other": e2e_other,
             "loss_total": float(r["loss_total"][0])}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(tr, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(tr, args.cpu_seconds,
+                                            1 if args.mode == "eq2" else 0)
     print(json.dumps(line), flush=True)
 
 
