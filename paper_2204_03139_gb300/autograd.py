@@ -48,3 +48,29 @@ def loss_traj(verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, frame_w=None,
     lf = DCLoss.apply(verts, faces, draws, targets, mode, face_mask, fw)
     w = torch.ones_like(lf) if fw is None else fw
     return (w * lf).sum(), lf
+
+
+class DiffCloudLoss(torch.nn.Module):
+    """The loss as a module: loss(verts) -> (sum_t w_t L_t, per-frame L_t), differentiable in
+    verts [T, V, 3]. Every call draws fresh samples (n per frame, from its own seeded
+    generator), as a sampler inside an optimisation loop does; the draws of the last call
+    are kept in `last_draws`.
+
+    faces [F, 3] int32, targets [T, M, 3] float32 on the device; mode BIDIR_MEAN (Eq. 1) or
+    UNIDIR_SUM (Eq. 2); frame_w [T] optional (frames of weight 0 cost nothing); face_mask [F]
+    optional (sample only these faces)."""
+
+    def __init__(self, faces, targets, n: int, mode=_lib.BIDIR_MEAN, frame_w=None,
+                 face_mask=None, seed: int = 0):
+        super().__init__()
+        self.faces, self.targets, self.n, self.mode = faces, targets, int(n), mode
+        self.frame_w, self.face_mask = frame_w, face_mask
+        self.gen = torch.Generator(device="cpu").manual_seed(seed)
+        self.last_draws = None
+
+    def forward(self, verts):
+        T = verts.shape[0]
+        draws = torch.rand((T, self.n, 3), generator=self.gen).clamp_(max=1 - 2 ** -24)
+        self.last_draws = draws.to(verts.device)
+        return loss_traj(verts.float().contiguous(), self.faces, self.last_draws, self.targets,
+                         mode=self.mode, frame_w=self.frame_w, face_mask=self.face_mask)

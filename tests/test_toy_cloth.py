@@ -4,7 +4,6 @@ The CPU tests check the toy cloth model and the paper's sigmoid reparameterisati
 tests check that the parameter gradient through this library equals the one built from the
 oracle's FP64 vertex gradient, and that Adam recovers the parameters of a synthetic target.
 """
-import copy
 
 import numpy as np
 import pytest
@@ -99,3 +98,26 @@ def test_real_to_sim_recovers_the_parameters():
     fw[-1] = 1.0
     r1 = real_to_sim(cl, Y, 8192, iters=30, lr=0.2, seed=8, frame_w=fw)
     assert r1["loss"] < r1["history"][0][1]
+
+
+@pytest.mark.gpu
+def test_loss_module_draws_fresh_samples_and_matches_the_function():
+    """DiffCloudLoss(verts) equals loss_traj on the draws it used, and draws new ones per call."""
+    from paper_2204_03139_gb300.autograd import DiffCloudLoss, loss_traj
+    from paper_2204_03139_gb300.toy_cloth import ToyCloth, sample_targets
+
+    dev = _gpu()
+    cl = ToyCloth(n=15, T=3, device=dev)
+    Y = sample_targets(cl, [2.0, 7.5], 2000, seed=3)
+    mod = DiffCloudLoss(cl.faces, Y, 2000, seed=5)
+    v = cl.verts(torch.tensor([3.0, 4.0], dtype=torch.float64, device=dev)).float()
+    v.requires_grad_(True)
+    t1, _ = mod(v)
+    d1 = mod.last_draws.clone()
+    (g1,) = torch.autograd.grad(t1, v)
+    t_ref, _ = loss_traj(v, cl.faces, d1, Y)
+    (g_ref,) = torch.autograd.grad(t_ref, v)
+    assert float(t1.detach()) == float(t_ref.detach())
+    assert parity.rel_l2(g1.cpu().numpy(), g_ref.cpu().numpy()) < 1e-6
+    mod(v)
+    assert not torch.equal(mod.last_draws, d1)
