@@ -78,6 +78,34 @@ class _Item:
     pairs: int
 
 
+def form_batch(items, now: float, cap: float, max_items: int, max_wait_s: float):
+    """The items of the next batch, from admitted items (objects with .req (having .arrival)
+    and .pairs). Requests are taken shortest remaining work first, those that waited longer
+    than max_wait_s first of all (oldest first), so that long requests cannot starve; each
+    request's items in order, until the batch holds `cap` pairs or `max_items` items (the
+    first item is always taken). Returns (items, pairs)."""
+    reqs, items_of = {}, collections.defaultdict(list)
+    for it in items:
+        reqs[id(it.req)] = it.req
+        items_of[id(it.req)].append(it)
+    remaining = {k: sum(it.pairs for it in v) for k, v in items_of.items()}
+
+    def priority(k):
+        r = reqs[k]
+        if now - r.arrival > max_wait_s:
+            return (0, r.arrival, 0)
+        return (1, remaining[k], r.arrival)
+
+    take, pairs = [], 0
+    for k in sorted(reqs, key=priority):
+        for it in items_of[k]:
+            if take and (len(take) >= max_items or pairs + it.pairs > cap):
+                return take, pairs
+            take.append(it)
+            pairs += it.pairs
+    return take, pairs
+
+
 def _slice(d: DeviceTrajectory, a: int, b: int) -> DeviceTrajectory:
     """Frames [a, b) of a device trajectory (views, no copies)."""
     n0, n1 = int(d.n_off[a]), int(d.n_off[b])
@@ -255,31 +283,9 @@ class Server:
             # (fewer launches per pair)
             waiting = len({id(it.req) for it in self._admitted})
             cap = self.max_batch_pairs * max(1, min(8, waiting // 8))
-            # shortest remaining work first; requests that waited past max_wait_s first of all
-            # (oldest first among them), so that long ones cannot starve
-            now = time.perf_counter()
-            reqs, items = {}, collections.defaultdict(list)
-            for it in self._admitted:
-                if it.req.mode == mode:
-                    reqs[id(it.req)] = it.req
-                    items[id(it.req)].append(it)
-            remaining = {k: sum(it.pairs for it in v) for k, v in items.items()}
-
-            def priority(k):
-                r = reqs[k]
-                old = now - r.arrival > self.max_wait_s
-                return (0, r.arrival, 0) if old else (1, remaining[k], r.arrival)
-
-            take, pairs = [], 0
-            for k in sorted(reqs, key=priority):
-                for it in items[k]:
-                    if take and (len(take) >= self.max_batch_items or pairs + it.pairs > cap):
-                        break
-                    take.append(it)
-                    pairs += it.pairs
-                else:
-                    continue
-                break
+            take, pairs = form_batch([it for it in self._admitted if it.req.mode == mode],
+                                     time.perf_counter(), cap, self.max_batch_items,
+                                     self.max_wait_s)
             for it in take:
                 self._admitted.remove(it)
             stream = self._streams[s_idx]
