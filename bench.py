@@ -564,8 +564,6 @@ def run_serving(args, rank, world, dist):
     """Poisson stream of loss+gradient requests: 90% at the 50x50 / 10 000-point size, 10% at
     the 100x100 / 32 768-point size, served with continuous batching under a 120 GB budget.
     Each rate runs a fixed arrival window; latencies include queueing."""
-    import threading
-
     import torch
 
     from paper_2204_03139_gb300.serve import Server, serve_plain

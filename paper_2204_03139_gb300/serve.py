@@ -26,7 +26,6 @@ per-slice loss partial sums may differ, within float32 rounding).
 from __future__ import annotations
 
 import collections
-import ctypes
 import threading
 import time
 from concurrent.futures import Future
