@@ -97,6 +97,36 @@ def test_trajectory_50x50_weights_total():
 
 
 # ---------------------------------------------------------------------------------------------
+# exact ties: the lowest index wins (R6), across sub-chunks, chunks, units and CTAs
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1])
+def test_exact_ties_go_to_the_lowest_index(mode):
+    rng = np.random.default_rng(31)
+    U = rng.random((500, 3)).astype(np.float32)
+    b = np.ascontiguousarray(U[np.arange(5000) % 500])      # copies 500 indices apart
+    a = np.ascontiguousarray(U[(np.arange(4000) * 7) % 500] + np.float32(1e-3) *
+                             rng.standard_normal((4000, 3)).astype(np.float32))
+    a[::5] = U[(np.arange(0, 4000, 5) * 3) % 500]           # some sim points on targets
+    a = np.ascontiguousarray(np.concatenate([a, a[:1000]]))  # and repeated sim points
+    A = torch.from_numpy(a[None]).to(DEV)
+    B = torch.from_numpy(b[None]).to(DEV)
+    loss, nab, nba = L().dc_chamfer_fwd(A, B, mode=mode, check=True)
+    ref = oracle.nn_pair(a, b)
+    np.testing.assert_array_equal(nab[0].cpu().numpy(), ref["nn_ab"])
+    assert np.all(nab[0].cpu().numpy() < 500)                # the first copy of each point
+    if mode == 0:
+        np.testing.assert_array_equal(nba[0].cpu().numpy(), ref["nn_ba"])
+    # every target the same point: every sim point's neighbour is target 0, and every
+    # target's neighbour is the first sim point at the least distance
+    b1 = np.ascontiguousarray(np.repeat(U[:1], 3000, axis=0))
+    loss, nab, nba = L().dc_chamfer_fwd(A, torch.from_numpy(b1[None]).to(DEV), mode=mode,
+                                        check=True)
+    assert np.all(nab[0].cpu().numpy() == 0)
+    if mode == 0:
+        np.testing.assert_array_equal(nba[0].cpu().numpy(), oracle.nn_pair(a, b1)["nn_ba"])
+
+
+# ---------------------------------------------------------------------------------------------
 # failure detection without a GPU fault
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.timeout(120)
