@@ -96,6 +96,16 @@ def test_trajectory_50x50_weights_total():
     compare_traj(tr, g, ref, list(range(tr.T)), weights=w)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_many_small_frames_one_epilogue_slice_each(mode):
+    """700 frames: one epilogue CTA per frame writes the gradient directly (no slice
+    reduction); every frame against the oracle."""
+    tr, _ = parity.nudge_draws(W.lift_trajectory(41, 8, 700, 96, 80, name="many"))
+    g = run_traj(tr, mode)
+    ref = oracle.loss_traj(tr, mode=mode)
+    compare_traj(tr, g, ref, list(range(tr.T)), mode)
+
+
 # ---------------------------------------------------------------------------------------------
 # exact ties: the lowest index wins (R6), across sub-chunks, chunks, units and CTAs
 # ---------------------------------------------------------------------------------------------
