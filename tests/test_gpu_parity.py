@@ -106,6 +106,18 @@ def test_many_small_frames_one_epilogue_slice_each(mode):
     compare_traj(tr, g, ref, list(range(tr.T)), mode)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_large_mesh_global_memory_paths(mode):
+    """A 175 x 175 grid (30 625 vertices, 60 552 faces): the V x 3 gradient accumulator does
+    not fit in shared memory (the scatter goes to global memory) and neither does the area
+    CDF (sampling and target staging search it in global memory)."""
+    tr, _ = parity.nudge_draws(W.lift_trajectory(43, 175, 2, 3000, 2500, name="big_mesh"))
+    assert tr.V * 12 > 227 * 1024 and tr.F * 4 > 227 * 1024
+    g = run_traj(tr, mode)
+    ref = oracle.loss_traj(tr, mode=mode)
+    compare_traj(tr, g, ref, list(range(tr.T)), mode)
+
+
 # ---------------------------------------------------------------------------------------------
 # exact ties: the lowest index wins (R6), across sub-chunks, chunks, units and CTAs
 # ---------------------------------------------------------------------------------------------
