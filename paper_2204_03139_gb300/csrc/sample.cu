@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, 
     const int n_units = a.T * upf;
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    // frames, in chunks of BUILD_THREADS, with a running count of live frames
-    for (int k0 = 0; k0 < a.T; k0 += BUILD_THREADS) {
+    const int nt = blockDim.x;  // a multiple of 32, at most BUILD_THREADS
+    // frames, in chunks of nt, with a running count of live frames
+    for (int k0 = 0; k0 < a.T; k0 += nt) {
         const int k = k0 + tid;
         bool live = false;
         if (k < a.T) {
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, 
         for (int q = 0; q < warp; ++q) before += s_warp[q];
         if (k < a.T) w.frames[k].unit0 = before + in_warp;
         __syncthreads();
-        if (tid == BUILD_THREADS - 1) s_carry = before + in_warp + (live ? 1 : 0);
+        if (tid == nt - 1) s_carry = before + in_warp + (live ? 1 : 0);
         __syncthreads();
     }
     if (tid == 0) {
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, 
     }
     __syncthreads();  // the frames' live counts are written
     // units: a skipped frame's units carry no sub-chunks
-    for (int u = tid; u <= n_units; u += BUILD_THREADS) {
+    for (int u = tid; u <= n_units; u += nt) {
         if (u == n_units) {
             w.unit_pre[u] = s_carry * upf * spu;
             continue;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, 
     }
     // unit0 now holds "live frames before"; restore its documented meaning
     __syncthreads();
-    for (int k = tid; k < a.T; k += BUILD_THREADS) w.frames[k].unit0 = k * upf;
+    for (int k = tid; k < a.T; k += nt) w.frames[k].unit0 = k * upf;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -415,7 +416,13 @@ int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s) {
-    cudaError_t e = launch_pdl(k_build_uniform, 1, BUILD_THREADS, 0, s, a, w);
+    // as many threads as frames or units (whichever is more), in whole warps: a block of
+    // 1024 threads costs several microseconds of barriers for a single frame
+    const long long n_units = (long long)a.T * a.units_per_frame;
+    long long nt = a.T > n_units + 1 ? a.T : n_units + 1;
+    nt = (nt + 31) / 32 * 32;
+    if (nt > BUILD_THREADS) nt = BUILD_THREADS;
+    cudaError_t e = launch_pdl(k_build_uniform, 1, (int)nt, 0, s, a, w);
     count_launch();
     return e ? e : cudaGetLastError();
 }
