@@ -109,6 +109,22 @@ constexpr int TPS = DC_TARGETS_PER_STEP;  // targets per inner step (2 or 4)
 
 // one sub-chunk: SUB targets against this thread's rows; row minima into cm, per-target warp
 // minima and the ballot of the lanes holding them into smv / smb
+// warp minimum of each of TPS targets and the lanes holding it; every lane stores the same
+// value (no divergent branch); the first lane is taken later
+__device__ __forceinline__ void column_merge(const unsigned (&v)[TPS], const unsigned (&m)[TPS],
+                                             unsigned* __restrict__ smv,
+                                             unsigned* __restrict__ smb) {
+#pragma unroll
+    for (int t = 0; t < TPS; t += 2) {
+        const unsigned q0 = __ballot_sync(0xffffffffu, v[t] == m[t]);
+        const unsigned q1 = __ballot_sync(0xffffffffu, v[t + 1] == m[t + 1]);
+        *reinterpret_cast<uint2*>(smv + t) = make_uint2(m[t], m[t + 1]);
+        *reinterpret_cast<uint2*>(smb + t) = make_uint2(q0, q1);
+    }
+}
+
+// one sub-chunk: SUB targets against this thread's rows; row minima into cm, per-target warp
+// minima and the ballot of the lanes holding them into smv / smb
 template <bool BIDIR>
 __device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const float* __restrict__ ty,
                                           const float* __restrict__ tz, const float2 (&rx)[PAIRS],
@@ -155,36 +171,42 @@ __device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const fl
             }
         }
         if (BIDIR) {
-            // warp minimum of each target and the lanes holding it; every lane stores the
-            // same value (no divergent branch); the first lane is taken later
+            unsigned v[TPS], m[TPS];
 #pragma unroll
-            for (int t = 0; t < TPS; t += 2) {
-                const unsigned v0 = __float_as_uint(c[t]), v1 = __float_as_uint(c[t + 1]);
-                const unsigned m0 = __reduce_min_sync(0xffffffffu, v0);
-                const unsigned m1 = __reduce_min_sync(0xffffffffu, v1);
-                const unsigned q0 = __ballot_sync(0xffffffffu, v0 == m0);
-                const unsigned q1 = __ballot_sync(0xffffffffu, v1 == m1);
-                *reinterpret_cast<uint2*>(smv + jj + t) = make_uint2(m0, m1);
-                *reinterpret_cast<uint2*>(smb + jj + t) = make_uint2(q0, q1);
+            for (int t = 0; t < TPS; ++t) {
+                v[t] = __float_as_uint(c[t]);
+                m[t] = __reduce_min_sync(0xffffffffu, v[t]);
             }
+            column_merge(v, m, smv + jj, smb + jj);
         }
     }
 }
 
+// Where a row's running minimum over the unit segment (and the sub-chunk holding it) lives:
+// in registers for the rows-only pass, which has the registers to spare at 8 warps per SM
+// (measured 1.7% faster than shared memory there); in shared memory for the bidirectional
+// pass, whose column minima take those registers (registers were 0.6% slower there).
+template <bool BIDIR>
+struct BestInRegs {
+    static constexpr bool value = !BIDIR;
+};
+
 // resident CTAs per SM the register budget is sized for, per CTA width: 12 warps per SM with
-// 16 rows per thread, 16 warps with fewer (fewer row registers)
-template <int W>
+// 16 rows per thread (8 when the running minima are kept in registers), 16 warps with fewer
+// rows (fewer row registers)
+template <bool BIDIR, int W>
 struct MinBlocks {
 #ifdef DC_WARPS_PER_SM
     static constexpr int warps_per_sm = DC_WARPS_PER_SM;
 #else
-    static constexpr int warps_per_sm = ROWS_PER_THREAD >= 16 ? 12 : 16;
+    static constexpr int warps_per_sm =
+        ROWS_PER_THREAD >= 16 ? (BestInRegs<BIDIR>::value ? 8 : 12) : 16;
 #endif
     static constexpr int value = warps_per_sm / W;
 };
 
 template <bool BIDIR, int W>
-__global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
+__global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
     k_chamfer(Ws w, int stall) {
     pdl_entry();
     constexpr int THREADS = 32 * W;
@@ -195,9 +217,11 @@ __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
     // per-warp column minima of the chunk and the ballot of the lanes that hold them
     __shared__ __align__(16) unsigned s_cv[BIDIR ? 2 : 1][BIDIR ? WARPS : 1][BIDIR ? CHUNK : 1];
     __shared__ __align__(16) unsigned s_cb[BIDIR ? 2 : 1][BIDIR ? WARPS : 1][BIDIR ? CHUNK : 1];
-    // per-row running minimum over the unit and the sub-chunk that holds it
-    __shared__ float s_best[ROWS_PER_THREAD][THREADS];
-    __shared__ unsigned s_bidx[ROWS_PER_THREAD][THREADS];
+    // per-row running minimum over the unit and the sub-chunk that holds it (shared-memory
+    // copy; unused and one element when it lives in registers)
+    constexpr bool REG_BEST = BestInRegs<BIDIR>::value;
+    __shared__ float s_best[REG_BEST ? 1 : ROWS_PER_THREAD][REG_BEST ? 1 : THREADS];
+    __shared__ unsigned s_bidx[REG_BEST ? 1 : ROWS_PER_THREAD][REG_BEST ? 1 : THREADS];
     __shared__ UnitState s_u;
     __shared__ __align__(8) u64 s_bar[2];
 
@@ -275,10 +299,18 @@ __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
                 rz[p].y = xs[8 * p + 6];
             }
         }
+        float r_best[REG_BEST ? ROWS_PER_THREAD : 1];
+        unsigned r_bidx[REG_BEST ? ROWS_PER_THREAD : 1];
+        auto best = [&](int r) -> float& {
+            if constexpr (REG_BEST) return r_best[r]; else return s_best[r][tid];
+        };
+        auto bidx = [&](int r) -> unsigned& {
+            if constexpr (REG_BEST) return r_bidx[r]; else return s_bidx[r][tid];
+        };
 #pragma unroll
         for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-            s_best[r][tid] = INFINITY;
-            s_bidx[r][tid] = 0u;
+            best(r) = INFINITY;
+            bidx(r) = 0u;
         }
 
         const int c_lo = s_u.sub_lo / SUBS_PER_CHUNK, c_hi = (s_u.sub_hi - 1) / SUBS_PER_CHUNK;
@@ -300,9 +332,9 @@ __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
                                      BIDIR ? &s_cb[b][warp][off] : nullptr);
 #pragma unroll
                     for (int r = 0; r < ROWS_PER_THREAD; ++r)
-                        if (cm[r] < s_best[r][tid]) {
-                            s_best[r][tid] = cm[r];
-                            s_bidx[r][tid] = (unsigned)sc;
+                        if (cm[r] < best(r)) {
+                            best(r) = cm[r];
+                            bidx(r) = (unsigned)sc;
                         }
                 }
             }
@@ -351,7 +383,7 @@ __global__ void __launch_bounds__(32 * W, MinBlocks<W>::value)
                 const int row = trow0 + r;
                 if (row < N)
                     atomicMin(&w.pab[s_u.row0 + row],
-                              ((u64)__float_as_uint(s_best[r][tid]) << 32) | (u64)s_bidx[r][tid]);
+                              ((u64)__float_as_uint(best(r)) << 32) | (u64)bidx(r));
             }
         }
         s = min(s_end, w.unit_pre[u + 1]);

@@ -25,7 +25,10 @@ constexpr int ROWS_PER_WARP = 32 * ROWS_PER_THREAD;       // 512
 // amortise the target staging and the column merges over more rows, narrow ones give
 // small problems enough work items to fill the GPU.
 constexpr int MAX_WARPS = 4;
-constexpr int SUB = 32;                                   // targets per tracked sub-chunk
+#ifndef DC_SUB
+#define DC_SUB 32
+#endif
+constexpr int SUB = DC_SUB;                               // targets per tracked sub-chunk
 constexpr int CHUNK = 256;                                // targets per staged chunk
 constexpr int SUBS_PER_CHUNK = CHUNK / SUB;
 constexpr int ROW_PAD = ROWS_PER_WARP;                    // sim points padded to this

@@ -92,11 +92,12 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
     const float cba = __fdiv_rn(__fmul_rn(2.0f, gs), (float)M);
 
     // ---- sim points of this slice, 8 rows per warp step, 4 lanes per row ----
-    // A row's minimum points at one sub-chunk of SUB (= 32) targets; lane q of the row's
-    // group checks candidates 8q..8q+7 with contiguous loads, and two xor-shuffles give the
-    // group the first candidate that matches. The three vertices of the gradient scatter go
-    // to lanes 0..2 of the group.
-    static_assert(SUB == 32, "four lanes of eight re-scan candidates per row");
+    // A row's minimum points at one sub-chunk of SUB targets; lane q of the row's group
+    // checks candidates CPL q .. CPL q + CPL - 1 with contiguous loads, and two xor-shuffles
+    // give the group the first candidate that matches. The three vertices of the gradient
+    // scatter go to lanes 0..2 of the group.
+    constexpr int CPL = SUB / 4;  // re-scan candidates per lane
+    static_assert(SUB % 16 == 0, "four lanes of whole float4 groups per row");
     const int lane = tid & 31, warp = tid >> 5, grp = lane >> 2, q = lane & 3;
     constexpr int NW = EPI_THREADS / 32;
     const float* PX = w.tpl + 3LL * col0;  // compact target planes X[Mpad], Y, Z
@@ -118,18 +119,19 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
             if (p != EMPTY) {
                 const unsigned dq = (unsigned)(p >> 32);
                 dmin = __uint_as_float(dq);
-                const int jb = (int)(p & 0xffffffffu) * SUB + 8 * q;
-                const float4 xa = *reinterpret_cast<const float4*>(PX + jb);
-                const float4 xb = *reinterpret_cast<const float4*>(PX + jb + 4);
-                const float4 ya = *reinterpret_cast<const float4*>(PY + jb);
-                const float4 yb = *reinterpret_cast<const float4*>(PY + jb + 4);
-                const float4 za = *reinterpret_cast<const float4*>(PZ + jb);
-                const float4 zb = *reinterpret_cast<const float4*>(PZ + jb + 4);
-                const float cx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-                const float cy[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
-                const float cz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+                const int jb = (int)(p & 0xffffffffu) * SUB + CPL * q;
+                float cx[CPL], cy[CPL], cz[CPL];
 #pragma unroll
-                for (int t = 7; t >= 0; --t)
+                for (int k = 0; k < CPL; k += 4) {
+                    const float4 a = *reinterpret_cast<const float4*>(PX + jb + k);
+                    const float4 b = *reinterpret_cast<const float4*>(PY + jb + k);
+                    const float4 c = *reinterpret_cast<const float4*>(PZ + jb + k);
+                    cx[k] = a.x, cx[k + 1] = a.y, cx[k + 2] = a.z, cx[k + 3] = a.w;
+                    cy[k] = b.x, cy[k + 1] = b.y, cy[k + 2] = b.z, cy[k + 3] = b.w;
+                    cz[k] = c.x, cz[k + 1] = c.y, cz[k + 2] = c.z, cz[k + 3] = c.w;
+                }
+#pragma unroll
+                for (int t = CPL - 1; t >= 0; --t)
                     if (jb + t < M &&
                         __float_as_uint(dist2(x.x, x.y, x.z, cx[t], cy[t], cz[t])) == dq)
                         first = jb + t;
