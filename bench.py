@@ -31,9 +31,10 @@ import workloads  # noqa: E402
 FLOP_PER_PAIR = 8        # 3 sub + 3 mul/fma products + 2 adds per distance, shared by both directions
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_chamfer launch on the default workload
-# (trajectory_50x50, 40 frames), from the one-pass ncu capture summarised in
-# profiles/k_chamfer_trajectory_50x50.md (22.84 MB read, 0 written); None for other workloads.
-CHAMFER_TRAFFIC_BYTES = {"trajectory_50x50": 22.84e6}
+# (trajectory_50x50, 40 frames) in each mode, from the one-pass ncu captures summarised in
+# profiles/k_chamfer_trajectory_50x50.md (nothing is written to DRAM); None for other workloads.
+CHAMFER_TRAFFIC_BYTES = {("trajectory_50x50", "eq1"): 22.85e6,
+                         ("trajectory_50x50", "eq2"): 19.63e6}
 
 
 def parse():
@@ -416,8 +417,8 @@ def run_gpu(args, rank, world, dist):
     achieved = FLOP_PER_PAIR * pairs / chamfer_avg_s / 1e12 if chamfer_n else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": (achieved / peak_tflops) if (achieved and peak_tflops) else None,
-            "traffic": (CHAMFER_TRAFFIC_BYTES.get(args.workload) if args.frames is None
-                        else None) if mode == _lib.BIDIR_MEAN else None,
+            "traffic": (CHAMFER_TRAFFIC_BYTES.get((args.workload, args.mode))
+                        if args.frames is None else None),
             "kernel": "k_chamfer<true>" if mode == _lib.BIDIR_MEAN else "k_chamfer<false>",
             "peak_basis": f"FP32 FMA peak 2 x {FP32_LANES_PER_SM} lanes x {sms} SMs x median "
                           f"SM clock under load ({sm_mhz:.0f} MHz); at the {sm_max:.0f} MHz "

@@ -29,7 +29,10 @@ constexpr int MAX_WARPS = 4;
 #define DC_SUB 32
 #endif
 constexpr int SUB = DC_SUB;                               // targets per tracked sub-chunk
-constexpr int CHUNK = 256;                                // targets per staged chunk
+#ifndef DC_CHUNK
+#define DC_CHUNK 256
+#endif
+constexpr int CHUNK = DC_CHUNK;                           // targets per staged chunk
 constexpr int SUBS_PER_CHUNK = CHUNK / SUB;
 constexpr int ROW_PAD = ROWS_PER_WARP;                    // sim points padded to this
 constexpr int COL_PAD = CHUNK;                            // target points padded to this
