@@ -63,7 +63,6 @@ Layout make_layout(const Sizes& s) {
     L.nnba = take(s.cols * 4);
     L.loss = take(s.n_frames * 4);
     L.part = take(s.n_frames * s.slices * 2 * 4);
-    L.gscr = take(s.gscr * 4);
     L.total = off;
     return L;
 }
@@ -89,7 +88,6 @@ Ws make_ws(void* base, const Layout& L) {
     w.nnba = reinterpret_cast<int*>(p + L.nnba);
     w.loss = reinterpret_cast<float*>(p + L.loss);
     w.part = reinterpret_cast<float*>(p + L.part);
-    w.gscr = reinterpret_cast<float*>(p + L.gscr);
     return w;
 }
 
@@ -128,10 +126,9 @@ bool uniform_sizes(int T, int V, int F, int N, int M, Sizes& s, long long sub[3]
     s.rows = (long long)T * Npad;
     s.cols = (long long)T * Mpad;
     s.slices = epilogue_slices(T);
-    s.gscr = s.slices > 1 ? (long long)T * s.slices * 3 * V : 0;
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
            sub[0] < INT_LIMIT && s.rows * 3 < INT_LIMIT * 16 && s.cols * 6 < INT_LIMIT * 16 &&
-           s.gscr < INT_LIMIT * 4;
+           3LL * V < INT_LIMIT;
 }
 
 enum : unsigned {
@@ -441,7 +438,7 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* fa
 // batches
 // ---------------------------------------------------------------------------------------
 static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long sub[3]) {
-    s = Sizes{n, 0, 0, 0, 0, epilogue_slices(n), 0};
+    s = Sizes{n, 0, 0, 0, 0, epilogue_slices(n)};
     sub[0] = sub[1] = sub[2] = 0;
     long long max_v = 0;
     for (int k = 0; k < n; ++k) {
@@ -453,10 +450,9 @@ static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long sub[3]) {
         s.cols += (long long)div_up(fr[k].M, COL_PAD) * COL_PAD;
         if (fr[k].grad_verts && fr[k].V > max_v) max_v = fr[k].V;
     }
-    s.gscr = s.slices > 1 ? (long long)n * s.slices * 3 * max_v : 0;
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
            sub[0] < INT_LIMIT && s.n_units < INT_LIMIT && s.cols * 6 < INT_LIMIT * 16 &&
-           s.gscr < INT_LIMIT * 4;
+           3 * max_v < INT_LIMIT;
 }
 
 size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames) {

@@ -38,7 +38,7 @@ constexpr int ROW_PAD = ROWS_PER_WARP;                    // sim points padded t
 constexpr int COL_PAD = CHUNK;                            // target points padded to this
 constexpr int EPI_THREADS = 256;                          // epilogue CTA size
 constexpr int EPI_CTAS = 608;                             // epilogue CTAs resident at once
-constexpr int MAX_SLICES = 16;                            // epilogue slices per frame
+constexpr int MAX_SLICES = 32;                            // epilogue slices per frame
 
 constexpr float COORD_MAX = 1e15f;
 constexpr unsigned long long EMPTY = ~0ull;
@@ -91,13 +91,12 @@ struct WsHeader {
 // Byte offsets of every region of a workspace (computed on the host).
 struct Layout {
     size_t hdr, frames, rowpre, colpre, unit_frame, unit_rb, unit_pre, cdf, x, fw, tsoa, tpl,
-        pab, pba, nnab, nnba, loss, part, gscr, total;
+        pab, pba, nnab, nnba, loss, part, total;
 };
 
 struct Sizes {
     long long n_frames, n_units, sum_f, rows, cols;
     long long slices;  // epilogue slices per frame
-    long long gscr;    // floats of per-slice gradient partials (0 when slices == 1)
 };
 
 // Epilogue slices per frame: as many as keep all (frame, slice) CTAs in one wave, at most
@@ -129,7 +128,6 @@ struct Ws {
     int* nnba;         // [cols]
     float* loss;       // [n_frames] fallback loss buffer
     float* part;       // [n_frames][slices][2] loss partial sums
-    float* gscr;       // [n_frames][slices][3 max_v] gradient partials (slices > 1)
 };
 
 Ws make_ws(void* base, const Layout& L);

@@ -8,8 +8,11 @@
 //     points at, with the same float32 operations as the Chamfer kernel, to find the first
 //     index attaining it (ties go to the lowest index);
 //   - sums its minimum distances (fixed order) into a per-slice partial;
-//   - scatters the gradient into a shared-memory copy of the frame's V x 3 gradient, then
-//     writes it out (one slice) or to a per-slice partial that k_grad_reduce sums in order.
+//   - scatters the gradient: with one slice per frame into a shared-memory copy of the
+//     frame's V x 3 gradient that it then writes out; with several slices straight into the
+//     output with global float atomics (the area kernel zeroed it), which costs the big
+//     frames nothing against per-slice copies and a reduction launch, and lets few frames
+//     use more slices.
 #include "dc_internal.cuh"
 
 namespace dc {
@@ -38,8 +41,7 @@ struct EpiArgs {
     int slices;
     int flags;     // EPI_RESCAN | EPI_LOSS | EPI_GRAD
     int bidir;
-    int use_smem;  // the V x 3 accumulator fits in shared memory
-    int vstride;   // floats per slice in gscr (3 * max V)
+    int use_smem;  // one slice per frame and the V x 3 accumulator fits in shared memory
 };
 
 __device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
@@ -240,23 +242,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(Ws w, EpiArgs e) {
     }
     if (grad && e.use_smem) {
         __syncthreads();
-        float* dst = e.slices == 1 ? fr->grad : w.gscr + (size_t)(k * e.slices + sl) * e.vstride;
-        for (int v = tid; v < 3 * V; v += EPI_THREADS) dst[v] = s_acc[v];
-    }
-}
-
-// gradient of frame k = sum over its slices, in slice order
-__global__ void __launch_bounds__(256) k_grad_reduce(Ws w, int n_frames, int slices, int vstride) {
-    pdl_entry();
-    const long long n = (long long)n_frames * vstride;
-    for (long long t = blockIdx.x * 256LL + threadIdx.x; t < n; t += (long long)gridDim.x * 256) {
-        const int k = (int)(t / vstride), v = (int)(t - (long long)k * vstride);
-        const FrameDesc* fr = w.frames + k;
-        if (!fr->grad || !fr->verts || fr->skip || v >= 3 * fr->V) continue;
-        const float* src = w.gscr + (size_t)k * slices * vstride + v;
-        float s = 0.f;
-        for (int q = 0; q < slices; ++q) s = __fadd_rn(s, src[(size_t)q * vstride]);
-        fr->grad[v] = s;
+        for (int v = tid; v < 3 * V; v += EPI_THREADS) fr->grad[v] = s_acc[v];
     }
 }
 
@@ -357,19 +343,13 @@ cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, in
     a.bidir = mode == DC_BIDIR_MEAN;
     const bool grad = (flags & EPI_GRAD) && max_v > 0;
     const size_t need = (size_t)max_v * 3 * sizeof(float);
-    a.use_smem = grad && need <= (size_t)g_smem_limit[dev];
-    a.vstride = 3 * max_v;
+    a.use_smem = grad && slices == 1 && need <= (size_t)g_smem_limit[dev];
     cudaError_t e = launch_pdl(k_epilogue, n_frames * slices, EPI_THREADS,
                                a.use_smem ? need : 0, s, w, a);
     count_launch();
     if (!e && (flags & EPI_LOSS)) {
         e = launch_pdl(k_frame_loss, 1, LOSS_THREADS, 0, s, w, n_frames, slices, (int)a.bidir,
                        total);
-        count_launch();
-    }
-    if (!e && a.use_smem && slices > 1) {
-        e = launch_pdl(k_grad_reduce, grid_for((long long)n_frames * a.vstride, 256), 256, 0, s,
-                       w, n_frames, slices, a.vstride);
         count_launch();
     }
     return e ? e : cudaGetLastError();

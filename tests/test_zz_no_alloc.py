@@ -15,6 +15,8 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+NOALLOC_SCRATCH_BYTES = 16 << 20  # the built-in scratch of dc_loss_traj_noalloc
+
 
 def _dev():
     if not torch.cuda.is_available():
@@ -54,8 +56,15 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
 
     _dev()
     L = _lib.lib()
-    fake = ctypes.c_void_p(0x100000)  # never touched: the size check comes first
-    rc = L.dc_loss_traj_noalloc(fake, fake, None, fake, fake, 16, 2500, 4802, 10000, 10000, 0,
+    # The pointers below are not device memory: the call must fail on the size check before
+    # any launch. So the problem is sized on the host first, well beyond the scratch, and the
+    # test refuses to make the call if it is not.
+    T, V, F, N, M = 16, 2500, 4802, 10000, 10000
+    while _lib.dc_workspace_size(T, V, F, N, M) <= 4 * NOALLOC_SCRATCH_BYTES:
+        T *= 2
+    assert _lib.dc_workspace_size(T, V, F, N, M) > 4 * NOALLOC_SCRATCH_BYTES
+    fake = ctypes.c_void_p(0x100000)
+    rc = L.dc_loss_traj_noalloc(fake, fake, None, fake, fake, T, V, F, N, M, 0,
                                 None, None, fake, None, None, None, None, None)
     assert rc == _lib.DC_ENOSPC
     assert "built-in scratch" in _lib.last_error()
