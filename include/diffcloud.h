@@ -180,7 +180,9 @@ size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames);
 /*
  * dc_batch_plan -- validate the frames (host array), lay them out in ws and copy the
  * descriptor tables into it (a host-to-device copy on `stream`). The plan stays valid
- * while the frames' buffers stay where they are; it can be run many times.
+ * while the frames' buffers stay where they are; it can be run many times. The layout
+ * orders the frames by decreasing N + M (ties keep the order of `frames`); every frame's
+ * outputs go to its own buffers, so the order shows only in the rounding of loss_total.
  */
 int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size_t ws_bytes,
                   dc_stream_t stream);

@@ -1,4 +1,5 @@
 // Host entry points of libdiffcloud.so (declared in include/diffcloud.h).
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -500,8 +501,17 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     int* urb = reinterpret_cast<int*>(img.data() + L.unit_rb);
     int* upre = reinterpret_cast<int*>(img.data() + L.unit_pre);
     int row0 = 0, col0 = 0, cdf0 = 0, unit = 0, subc = 0, any_grad = 0, max_v = 0, max_f = 0;
+    // The table lists the frames largest first (N + M, ties in the caller's order). The
+    // sampling and epilogue kernels run one CTA per (frame, slice) in table order, so the
+    // long CTAs of big frames start first and the small ones fill in behind them instead of
+    // leaving a tail (measured on 64 trajectories of uneven sizes).
+    std::vector<int> order(n_frames);
+    for (int k = 0; k < n_frames; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [frames](int a, int b) {
+        return (long long)frames[a].N + frames[a].M > (long long)frames[b].N + frames[b].M;
+    });
     for (int k = 0; k < n_frames; ++k) {
-        const dc_frame& f = frames[k];
+        const dc_frame& f = frames[order[k]];
         FrameDesc d{};
         d.verts = f.verts;
         d.faces = f.faces;
