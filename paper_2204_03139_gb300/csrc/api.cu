@@ -64,6 +64,7 @@ Layout make_layout(const Sizes& s) {
     L.nnba = take(s.cols * 4);
     L.loss = take(s.n_frames * 4);
     L.part = take(s.n_frames * s.slices * 2 * 4);
+    L.frame_err = take(s.n_frames * 4);
     L.total = off;
     return L;
 }
@@ -89,6 +90,7 @@ Ws make_ws(void* base, const Layout& L) {
     w.nnba = reinterpret_cast<int*>(p + L.nnba);
     w.loss = reinterpret_cast<float*>(p + L.loss);
     w.part = reinterpret_cast<float*>(p + L.part);
+    w.frame_err = reinterpret_cast<int*>(p + L.frame_err);
     return w;
 }
 
@@ -164,11 +166,13 @@ int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total
     if (rc) return rc;
     const Ws w = make_ws(ws, L);
     const int T = a.T, rows = (int)sz.rows, cols = (int)sz.cols;
-    cudaError_t e = launch_build_uniform(a, w, st);
-    if (!e && (phases & PH_AREA)) e = launch_area_cdf(w, T, st);
+    // with sampling to follow, the tables and the area CDFs share one launch
+    const bool fused = (phases & PH_AREA) && (phases & PH_SAMPLE);
+    cudaError_t e = fused ? launch_build_area(a, w, st) : launch_build_uniform(a, w, st);
+    if (!e && (phases & PH_AREA) && !fused) e = launch_area_cdf(w, T, st);
     if (!e && (phases & (PH_SAMPLE | PH_TARGETS)))
         e = launch_stage(w, T, (int)sz.slices, a.pts ? 0 : a.F, (phases & PH_SAMPLE) ? rows : 0,
-                         (phases & PH_TARGETS) ? cols : 0, st);
+                         (phases & PH_TARGETS) ? cols : 0, fused ? 1 : 0, st);
     if (!e && (phases & PH_CHAMFER)) {
         const long long units = (long long)T * a.units_per_frame;
         e = launch_chamfer(w, (int)units, (int)(units * spu), a.mode, warps, st);
@@ -602,7 +606,7 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
     const int n = (int)p.sz.n_frames, rows = (int)p.sz.rows, cols = (int)p.sz.cols;
     cudaError_t e = launch_reset(w, stream);
     if (!e) e = launch_area_cdf(w, n, stream);
-    if (!e) e = launch_stage(w, n, (int)p.sz.slices, p.max_f, rows, cols, stream);
+    if (!e) e = launch_stage(w, n, (int)p.sz.slices, p.max_f, rows, cols, 0, stream);
     if (!e) e = launch_chamfer(w, p.n_units, p.total_sub, p.mode, p.warps, stream);
     if (!e)
         e = launch_epilogue(w, n, (int)p.sz.slices, p.any_grad ? p.max_v : 0, p.mode,

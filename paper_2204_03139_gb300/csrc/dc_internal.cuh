@@ -91,7 +91,7 @@ struct WsHeader {
 // Byte offsets of every region of a workspace (computed on the host).
 struct Layout {
     size_t hdr, frames, rowpre, colpre, unit_frame, unit_rb, unit_pre, cdf, x, fw, tsoa, tpl,
-        pab, pba, nnab, nnba, loss, part, total;
+        pab, pba, nnab, nnba, loss, part, frame_err, total;
 };
 
 struct Sizes {
@@ -127,6 +127,7 @@ struct Ws {
     int* nnab;         // [rows] fallback neighbour buffers
     int* nnba;         // [cols]
     float* loss;       // [n_frames] fallback loss buffer
+    int* frame_err;    // [n_frames] error code of the fused build + area launch, per frame
     float* part;       // [n_frames][slices][2] loss partial sums
 };
 
@@ -187,14 +188,18 @@ struct UniformArgs {
 };
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s);
+// the frame tables and every frame's area CDF in one launch (block 0 builds the tables, block
+// 1 + t computes frame t's CDF from the arguments); the area errors go to w.frame_err, which
+// the sampling launch that follows (fold = 1) turns into the status word
+cudaError_t launch_build_area(const UniformArgs& a, const Ws& w, cudaStream_t s);
 cudaError_t launch_reset(const Ws& w, cudaStream_t s);
 cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s);
-cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s);
+cudaError_t launch_sample(const Ws& w, int n_frames, int rows, int fold, cudaStream_t s);
 cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s);
 // sampling + target staging in one (frame, slice) launch when the largest CDF (max_f
 // floats) fits in shared memory, else launch_sample + launch_targets
 cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
-                         cudaStream_t s);
+                         int fold, cudaStream_t s);
 cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, int warps,
                            cudaStream_t s);
 // resident Chamfer CTAs on the current device for a CTA width (persistent grid size)

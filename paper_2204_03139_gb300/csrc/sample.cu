@@ -34,8 +34,8 @@ __device__ __forceinline__ bool coord_ok(float v) { return fabsf(v) <= COORD_MAX
 // ---------------------------------------------------------------------------------------
 constexpr int BUILD_THREADS = 1024;
 
-__global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, Ws w) {
-    pdl_entry();
+// the whole block (blockDim.x threads, a multiple of 32, at most BUILD_THREADS) builds
+__device__ void build_uniform(const UniformArgs& a, const Ws& w) {
     __shared__ int s_warp[BUILD_THREADS / 32];
     __shared__ int s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -131,6 +131,11 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, 
     for (int k = tid; k < a.T; k += nt) w.frames[k].unit0 = k * upf;
 }
 
+__global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, Ws w) {
+    pdl_entry();
+    build_uniform(a, w);
+}
+
 // ---------------------------------------------------------------------------------------
 // area CDF: two-float (compensated) prefix sum of the float32 face areas, so that the
 // stored C_f is the float32 rounding of the exact prefix sum of those areas
@@ -202,21 +207,31 @@ __device__ __forceinline__ float face_weight(const float* __restrict__ verts,
 
 constexpr int CDF_THREADS = 1024;
 
-__global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
-    pdl_entry();
+// What the area step needs to know about one frame.
+struct AreaFrame {
+    const float* verts;   // [V][3]
+    const int* faces;     // [F][3]
+    const uint8_t* mask;  // [F] nullable
+    float* grad;          // [V][3] nullable: zeroed here for the epilogue's accumulation
+    float* cdf;           // [F] out
+    int F, V;
+    bool skip;            // weight 0: only the gradient (zero) is written
+};
+
+// One block (CDF_THREADS threads) computes one frame's area CDF; errors go to *err with
+// atomicCAS(DC_OK -> code), so the first one stays.
+__device__ void area_cdf(const AreaFrame& fr, int* err) {
     __shared__ FF s_w[32];
-    const FrameDesc* fr = w.frames + blockIdx.x;
-    const float* verts = fr->verts;
-    if (!verts) return;
-    if (fr->skip) {  // no sampling for this frame: only its gradient (zero) is written
-        if (fr->grad)
-            for (int e = threadIdx.x; e < 3 * fr->V; e += CDF_THREADS) fr->grad[e] = 0.0f;
+    if (fr.skip) {
+        if (fr.grad)
+            for (int e = threadIdx.x; e < 3 * fr.V; e += CDF_THREADS) fr.grad[e] = 0.0f;
         return;
     }
-    const int* faces = fr->faces;
-    const uint8_t* mask = fr->mask;
-    const int F = fr->F, V = fr->V;
-    float* cdf = w.cdf + fr->cdf0;
+    const float* verts = fr.verts;
+    const int* faces = fr.faces;
+    const uint8_t* mask = fr.mask;
+    const int F = fr.F, V = fr.V;
+    float* cdf = fr.cdf;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (F + CDF_THREADS - 1) / CDF_THREADS;
     const int f0 = min(F, tid * per), f1 = min(F, f0 + per);
@@ -256,14 +271,48 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
         run = ff_add1(run, cdf[f]);  // pass 2 reads back this thread's own area weights
         cdf[f] = run.hi;
     }
-    if (bad_idx || bad_val) set_status(&w.hdr->status, DC_EINVAL);
+    if (bad_idx || bad_val) set_status(err, DC_EINVAL);
     // the gradient of this frame starts from zero (accumulated by the epilogue)
-    if (fr->grad)
-        for (int e = tid; e < 3 * V; e += CDF_THREADS) fr->grad[e] = 0.0f;
+    if (fr.grad)
+        for (int e = tid; e < 3 * V; e += CDF_THREADS) fr.grad[e] = 0.0f;
     if (f1 == F && f0 < f1) {
         const float A = run.hi;
-        if (!(A > 0.0f) || !isfinite(A)) set_status(&w.hdr->status, DC_EDEGENERATE);
+        if (!(A > 0.0f) || !isfinite(A)) set_status(err, DC_EDEGENERATE);
     }
+}
+
+// one block per frame of the table
+__global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
+    pdl_entry();
+    const FrameDesc* fr = w.frames + blockIdx.x;
+    if (!fr->verts) return;
+    const AreaFrame af{fr->verts, fr->faces, fr->mask, fr->grad, w.cdf + fr->cdf0,
+                       fr->F, fr->V, fr->skip != 0};
+    area_cdf(af, &w.hdr->status);
+}
+
+// Uniform trajectory: block 0 builds the tables (as k_build_uniform) while block 1 + t
+// computes frame t's CDF from the arguments, which is where the table's entry would point.
+// The tables' builder resets the status word, so the area blocks keep their errors apart,
+// one code per frame in w.frame_err, for the sampling launch to report.
+__global__ void __launch_bounds__(CDF_THREADS) k_build_area(UniformArgs a, Ws w) {
+    pdl_entry();
+    if (blockIdx.x == 0) {
+        build_uniform(a, w);
+        return;
+    }
+    __shared__ int s_err;
+    const int t = blockIdx.x - 1;
+    if (threadIdx.x == 0) s_err = DC_OK;
+    __syncthreads();
+    const float wt = a.weight ? a.weight[t] : 1.0f;
+    const float gs = a.gscale ? a.gscale[t] : wt;
+    const AreaFrame af{a.verts + 3LL * t * a.V, a.faces, a.mask,
+                       a.grad ? a.grad + 3LL * t * a.V : nullptr, w.cdf + (long long)t * a.F,
+                       a.F, a.V, wt == 0.0f || gs == 0.0f};
+    area_cdf(af, &s_err);
+    __syncthreads();
+    if (threadIdx.x == 0) w.frame_err[t] = s_err;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -360,11 +409,18 @@ __device__ __forceinline__ void stage_target(const Ws& w, const FrameDesc* fr, i
     w.pba[g] = EMPTY;
 }
 
-__global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows) {
+// the area errors that a fused build + area launch left for frame k
+__device__ __forceinline__ void fold_area_err(const Ws& w, int k) {
+    const int code = w.frame_err[k];
+    if (code != DC_OK) set_status(&w.hdr->status, code);
+}
+
+__global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows, int fold) {
     pdl_entry();
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.rowpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
+        if (fold && g == fr->row0) fold_area_err(w, k);
         if (!fr->skip) sample_row(w, fr, g - fr->row0, g, w.cdf + fr->cdf0);
     }
 }
@@ -382,11 +438,13 @@ __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
 // copied to shared memory so that the binary searches stay on chip.
 constexpr int STAGE_THREADS = 512;
 
-__global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int rows, int cols) {
+__global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int rows, int cols,
+                                                        int fold) {
     pdl_entry();
     extern __shared__ float s_cdf[];
     const int k = blockIdx.x / slices, sl = blockIdx.x - k * slices;
     const FrameDesc* fr = w.frames + k;
+    if (fold && sl == 0 && threadIdx.x == 0) fold_area_err(w, k);
     if (fr->skip) return;
     const bool sampled = fr->verts && !fr->pts;
     if (sampled)
@@ -431,14 +489,20 @@ cudaError_t launch_reset(const Ws& w, cudaStream_t s) {
     return cudaMemsetAsync(&w.hdr->status, 0, sizeof(int), s);
 }
 
+cudaError_t launch_build_area(const UniformArgs& a, const Ws& w, cudaStream_t s) {
+    cudaError_t e = launch_pdl(k_build_area, a.T + 1, CDF_THREADS, 0, s, a, w);
+    count_launch();
+    return e ? e : cudaGetLastError();
+}
+
 cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s) {
     cudaError_t e = launch_pdl(k_area_cdf, n_frames, CDF_THREADS, 0, s, w);
     count_launch();
     return e ? e : cudaGetLastError();
 }
 
-cudaError_t launch_sample(const Ws& w, int n_frames, int rows, cudaStream_t s) {
-    cudaError_t e = launch_pdl(k_sample, grid_for(rows, 256), 256, 0, s, w, n_frames, rows);
+cudaError_t launch_sample(const Ws& w, int n_frames, int rows, int fold, cudaStream_t s) {
+    cudaError_t e = launch_pdl(k_sample, grid_for(rows, 256), 256, 0, s, w, n_frames, rows, fold);
     count_launch();
     return e ? e : cudaGetLastError();
 }
@@ -450,7 +514,7 @@ cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s) 
 }
 
 cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
-                         cudaStream_t s) {
+                         int fold, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
@@ -467,12 +531,12 @@ cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int r
     if (need > (size_t)g_stage_smem[dev]) {
         // the CDF does not fit on chip: one kernel per step, searching the CDF in global memory
         cudaError_t e = cudaSuccess;
-        if (rows) e = launch_sample(w, n_frames, rows, s);
+        if (rows) e = launch_sample(w, n_frames, rows, fold, s);
         if (!e && cols) e = launch_targets(w, n_frames, cols, s);
         return e;
     }
     cudaError_t e = launch_pdl(k_stage, n_frames * slices, STAGE_THREADS, need, s, w, slices,
-                               (int)(rows > 0), (int)(cols > 0));
+                               (int)(rows > 0), (int)(cols > 0), fold);
     count_launch();
     return e ? e : cudaGetLastError();
 }
