@@ -228,7 +228,7 @@ int dc_ws_status(const void* ws, dc_stream_t stream);
  *   status [1] device, nullable: receives the device-side error code of this call
  *   (DC_OK, DC_EINVAL, DC_EDEGENERATE, ...), since the scratch is not visible to the caller.
  *   Returns DC_ENOSPC, without launching anything, when dc_workspace_size(T, V, F, N, M)
- *   exceeds 16 MiB (about fifteen frames of 10 000 samples against 10 000 targets on a
+ *   exceeds 16 MiB (seventeen frames of 10 000 samples against 10 000 targets on a
  *   2 500-vertex mesh).
  *   It calls no allocator. Its first call on a device looks up the scratch array's device
  *   address with that device current; make that first call before any stream capture.
