@@ -457,6 +457,48 @@ def test_device_errors_are_reported():
     assert torch.isfinite(r["loss_frames"]).all()
 
 
+def test_area_errors_of_any_frame_reach_the_status():
+    """The area step of a uniform call runs in the launch that also builds the frame tables,
+    and keeps its errors per frame until the sampling launch reports them: a degenerate last
+    frame is reported by the forward call, the recomputing backward call and dc_sample; a bad
+    face index is reported when the CDF is too large for shared memory, where the sampling
+    runs from global memory."""
+    T, n = 3, 64
+    v = torch.tensor([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=torch.float32,
+                     device=DEV).repeat(T, 1, 1)
+    v[T - 1] = 0.25  # every vertex of the last frame at one point: zero total area
+    f = torch.tensor([[0, 1, 2]], dtype=torch.int32, device=DEV)
+    d = torch.full((T, n, 3), 0.5, device=DEV)
+    y = torch.zeros((T, n, 3), device=DEV)
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj(v, f, d, y, check=True)
+    assert e.value.code == L().DC_EDEGENERATE
+    nn_ab = torch.zeros((T, n), dtype=torch.int32, device=DEV)
+    nn_ba = torch.zeros((T, n), dtype=torch.int32, device=DEV)
+    g = torch.ones(T, device=DEV)
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj_bwd(v, f, d, y, nn_ab, nn_ba, g, check=True)
+    assert e.value.code == L().DC_EDEGENERATE
+    with pytest.raises(L().DCError) as e:
+        L().dc_sample(v, f, d, check=True)
+    assert e.value.code == L().DC_EDEGENERATE
+    # the same frames with a nonzero area pass
+    v[T - 1] = v[0]
+    r = L().dc_loss_traj(v, f, d, y, check=True)
+    assert torch.isfinite(r["loss_frames"]).all()
+    # 70 000 copies of one triangle (a CDF of 280 KB, beyond shared memory), the last one
+    # with a vertex index out of range
+    F = 70000
+    fb = torch.tensor([[0, 1, 2]], dtype=torch.int32, device=DEV).repeat(F, 1)
+    fb[F - 1, 2] = 3
+    with pytest.raises(L().DCError) as e:
+        L().dc_loss_traj(v[:1], fb, d[:1], y[:1], check=True)
+    assert e.value.code == L().DC_EINVAL
+    fb[F - 1, 2] = 2
+    r = L().dc_loss_traj(v[:1], fb, d[:1], y[:1], check=True)
+    assert torch.isfinite(r["loss_frames"]).all()
+
+
 @pytest.mark.parametrize("shape", [(2, 2048, 2048), (3, 5000, 7000)])
 def test_every_cta_width_gives_identical_results(shape):
     """The three Chamfer tile shapes (1, 2, 4 warps per CTA) split the same pairs differently;
