@@ -55,6 +55,8 @@ def parse():
                    help="serving: time slice of a long request, in point pairs")
     p.add_argument("--batch-pairs", type=float, default=16e9,
                    help="serving: batch size while the queue is short, in point pairs")
+    p.add_argument("--batch-trajectories", type=int, default=None,
+                   help="batched_uneven: only its first K trajectories (a small case for ncu)")
     p.add_argument("--frames", type=int, default=None,
                    help="use only the first FRAMES frames of the trajectory (profiling runs)")
     return p.parse_args()
@@ -466,6 +468,8 @@ def run_batched(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     trajs = make_workload("batched_uneven", rank=rank)
+    if args.batch_trajectories:
+        trajs = trajs[:args.batch_trajectories]
     pairs = sum(t.pairs() for t in trajs)
     frames = sum(t.T for t in trajs)
     dts = [DeviceTrajectory.from_host(t, dev) for t in trajs]
@@ -545,7 +549,7 @@ def run_batched(args, rank, world, dist):
             "unit": "pairs/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched_uneven_64traj", "trajectories": len(trajs),
+            "config": {"workload": f"batched_uneven_{len(trajs)}traj", "trajectories": len(trajs),
                        "frames": frames, "pairs_per_step": pairs,
                        "form": "one planned launch sequence replayed from a CUDA graph",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)"},
