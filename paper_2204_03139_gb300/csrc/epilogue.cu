@@ -59,10 +59,12 @@ __device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
     return r;  // valid in thread 0
 }
 
-// THREADS = 256 when frames are cut into slices; 512 when every frame is one CTA with a
-// shared-memory gradient copy (large batches), whose size caps the CTAs per SM: twice the
-// warps per CTA keep twice the loads in flight (measured 1.6% faster on 64 uneven
-// trajectories, 0.7% slower on the 40-frame trajectory had it been used there).
+// THREADS = 256 when frames are cut into slices; 1024 when every frame is one CTA with a
+// shared-memory gradient copy (large batches). The copy's size caps the CTAs per SM, and a
+// launch with more frames than resident CTAs ends with its largest frames: more warps per
+// CTA carry more independent load chains through each frame (on 64 uneven trajectories
+// 292.5 -> 287.7 ms per batch with 512 threads, 286.4 ms with 1024; the 40-frame
+// trajectory, cut into slices, was 0.7% slower with 512).
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiArgs e) {
     pdl_entry();
@@ -327,6 +329,9 @@ int g_smem_limit[64];
 
 }  // namespace
 
+// CTA size of the one-CTA-per-frame form (see k_epilogue)
+constexpr int EPI_THREADS_ONE_SLICE = 4 * EPI_THREADS;
+
 cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, int mode,
                             int flags, float* total, cudaStream_t s) {
     int dev = 0;
@@ -337,7 +342,7 @@ cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, in
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (optin <= 0) optin = 48 * 1024;
         optin -= 1024;  // room for the static reduction buffer
-        cudaError_t e = cudaFuncSetAttribute(k_epilogue<2 * EPI_THREADS>,
+        cudaError_t e = cudaFuncSetAttribute(k_epilogue<EPI_THREADS_ONE_SLICE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e != cudaSuccess) return e;
         g_smem_limit[dev] = optin;
@@ -349,8 +354,8 @@ cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, in
     const bool grad = (flags & EPI_GRAD) && max_v > 0;
     const size_t need = (size_t)max_v * 3 * sizeof(float);
     a.use_smem = grad && slices == 1 && need <= (size_t)g_smem_limit[dev];
-    cudaError_t e = a.use_smem ? launch_pdl(k_epilogue<2 * EPI_THREADS>, n_frames * slices,
-                                            2 * EPI_THREADS, need, s, w, a)
+    cudaError_t e = a.use_smem ? launch_pdl(k_epilogue<EPI_THREADS_ONE_SLICE>, n_frames * slices,
+                                            EPI_THREADS_ONE_SLICE, need, s, w, a)
                                : launch_pdl(k_epilogue<EPI_THREADS>, n_frames * slices,
                                             EPI_THREADS, 0, s, w, a);
     count_launch();
