@@ -125,61 +125,80 @@ __device__ __forceinline__ void column_merge(const unsigned (&v)[TPS], const uns
 
 // one sub-chunk: SUB targets against this thread's rows; row minima into cm, per-target warp
 // minima and the ballot of the lanes holding them into smv / smb
+// TPS targets jj..jj+TPS-1 against this thread's rows: row minima into cm (started from
+// this step's distances when FIRST, so that no sub-chunk has to fill cm with INFINITY
+// first: padded rows and targets carry finite sentinels, so no distance is NaN), per-target
+// warp minima and the ballot of the lanes holding them into smv / smb
+template <bool BIDIR, bool FIRST>
+__device__ __forceinline__ void step(const float* __restrict__ tx, const float* __restrict__ ty,
+                                     const float* __restrict__ tz, int jj,
+                                     const float2 (&rx)[PAIRS], const float2 (&ry)[PAIRS],
+                                     const float2 (&rz)[PAIRS], float (&cm)[ROWS_PER_THREAD],
+                                     unsigned* __restrict__ smv, unsigned* __restrict__ smb) {
+    // targets jj..jj+TPS-1 as {-X_j, -X_j} pairs
+    float2 X[TPS], Y[TPS], Z[TPS];
+#pragma unroll
+    for (int t = 0; t < TPS; t += 2) {
+        const float4 xq = *reinterpret_cast<const float4*>(tx + 2 * (jj + t));
+        const float4 yq = *reinterpret_cast<const float4*>(ty + 2 * (jj + t));
+        const float4 zq = *reinterpret_cast<const float4*>(tz + 2 * (jj + t));
+        X[t] = make_float2(xq.x, xq.y);
+        X[t + 1] = make_float2(xq.z, xq.w);
+        Y[t] = make_float2(yq.x, yq.y);
+        Y[t + 1] = make_float2(yq.z, yq.w);
+        Z[t] = make_float2(zq.x, zq.y);
+        Z[t + 1] = make_float2(zq.z, zq.w);
+    }
+    float c[TPS];
+#pragma unroll
+    for (int t = 0; t < TPS; ++t) c[t] = INFINITY;
+#pragma unroll
+    for (int p = 0; p < PAIRS; ++p) {
+        float2 d[TPS];
+#pragma unroll
+        for (int t = 0; t < TPS; ++t) {
+            // x + (-X) rounds exactly like x - X
+            const float2 dx = __fadd2_rn(rx[p], X[t]), dy = __fadd2_rn(ry[p], Y[t]),
+                         dz = __fadd2_rn(rz[p], Z[t]);
+            d[t] = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        }
+#pragma unroll
+        for (int t = 0; t < TPS; t += 2) {
+            if (FIRST && t == 0) {
+                cm[2 * p] = fminf(d[t].x, d[t + 1].x);
+                cm[2 * p + 1] = fminf(d[t].y, d[t + 1].y);
+            } else {
+                cm[2 * p] = min3(cm[2 * p], d[t].x, d[t + 1].x);
+                cm[2 * p + 1] = min3(cm[2 * p + 1], d[t].y, d[t + 1].y);
+            }
+        }
+        if (BIDIR) {
+#pragma unroll
+            for (int t = 0; t < TPS; ++t) c[t] = min3(c[t], d[t].x, d[t].y);
+        }
+    }
+    if (BIDIR) {
+        unsigned v[TPS], m[TPS];
+#pragma unroll
+        for (int t = 0; t < TPS; ++t) {
+            v[t] = __float_as_uint(c[t]);
+            m[t] = __reduce_min_sync(0xffffffffu, v[t]);
+        }
+        column_merge(v, m, smv + jj, smb + jj);
+    }
+}
+
+// one sub-chunk: SUB targets against this thread's rows; cm receives the rows' minima over it
 template <bool BIDIR>
 __device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const float* __restrict__ ty,
                                           const float* __restrict__ tz, const float2 (&rx)[PAIRS],
                                           const float2 (&ry)[PAIRS], const float2 (&rz)[PAIRS],
                                           float (&cm)[ROWS_PER_THREAD], unsigned* __restrict__ smv,
                                           unsigned* __restrict__ smb) {
+    step<BIDIR, true>(tx, ty, tz, 0, rx, ry, rz, cm, smv, smb);
 #pragma unroll(TPS == 2 ? 2 : 1)
-    for (int jj = 0; jj < SUB; jj += TPS) {
-        // targets jj..jj+TPS-1 as {-X_j, -X_j} pairs
-        float2 X[TPS], Y[TPS], Z[TPS];
-#pragma unroll
-        for (int t = 0; t < TPS; t += 2) {
-            const float4 xq = *reinterpret_cast<const float4*>(tx + 2 * (jj + t));
-            const float4 yq = *reinterpret_cast<const float4*>(ty + 2 * (jj + t));
-            const float4 zq = *reinterpret_cast<const float4*>(tz + 2 * (jj + t));
-            X[t] = make_float2(xq.x, xq.y);
-            X[t + 1] = make_float2(xq.z, xq.w);
-            Y[t] = make_float2(yq.x, yq.y);
-            Y[t + 1] = make_float2(yq.z, yq.w);
-            Z[t] = make_float2(zq.x, zq.y);
-            Z[t + 1] = make_float2(zq.z, zq.w);
-        }
-        float c[TPS];
-#pragma unroll
-        for (int t = 0; t < TPS; ++t) c[t] = INFINITY;
-#pragma unroll
-        for (int p = 0; p < PAIRS; ++p) {
-            float2 d[TPS];
-#pragma unroll
-            for (int t = 0; t < TPS; ++t) {
-                // x + (-X) rounds exactly like x - X
-                const float2 dx = __fadd2_rn(rx[p], X[t]), dy = __fadd2_rn(ry[p], Y[t]),
-                             dz = __fadd2_rn(rz[p], Z[t]);
-                d[t] = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            }
-#pragma unroll
-            for (int t = 0; t < TPS; t += 2) {
-                cm[2 * p] = min3(cm[2 * p], d[t].x, d[t + 1].x);
-                cm[2 * p + 1] = min3(cm[2 * p + 1], d[t].y, d[t + 1].y);
-            }
-            if (BIDIR) {
-#pragma unroll
-                for (int t = 0; t < TPS; ++t) c[t] = min3(c[t], d[t].x, d[t].y);
-            }
-        }
-        if (BIDIR) {
-            unsigned v[TPS], m[TPS];
-#pragma unroll
-            for (int t = 0; t < TPS; ++t) {
-                v[t] = __float_as_uint(c[t]);
-                m[t] = __reduce_min_sync(0xffffffffu, v[t]);
-            }
-            column_merge(v, m, smv + jj, smb + jj);
-        }
-    }
+    for (int jj = TPS; jj < SUB; jj += TPS)
+        step<BIDIR, false>(tx, ty, tz, jj, rx, ry, rz, cm, smv, smb);
 }
 
 // Where a row's running minimum over the unit segment (and the sub-chunk holding it) lives:
@@ -324,9 +343,7 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
             if (ok && wactive) {
                 for (int sc = sc0; sc < sc1; ++sc) {
                     const int off = (sc - c * SUBS_PER_CHUNK) * SUB;
-                    float cm[ROWS_PER_THREAD];
-#pragma unroll
-                    for (int r = 0; r < ROWS_PER_THREAD; ++r) cm[r] = INFINITY;
+                    float cm[ROWS_PER_THREAD];  // set by the sub-chunk's first step
                     sub_chunk<BIDIR>(&s_t[b][0][2 * off], &s_t[b][1][2 * off], &s_t[b][2][2 * off],
                                      rx, ry, rz, cm, BIDIR ? &s_cv[b][warp][off] : nullptr,
                                      BIDIR ? &s_cb[b][warp][off] : nullptr);
