@@ -107,8 +107,6 @@ struct UnitState {
 #endif
 constexpr int TPS = DC_TARGETS_PER_STEP;  // targets per inner step (2 or 4)
 
-// one sub-chunk: SUB targets against this thread's rows; row minima into cm, per-target warp
-// minima and the ballot of the lanes holding them into smv / smb
 // warp minimum of each of TPS targets and the lanes holding it; every lane stores the same
 // value (no divergent branch); the first lane is taken later
 __device__ __forceinline__ void column_merge(const unsigned (&v)[TPS], const unsigned (&m)[TPS],
@@ -123,8 +121,6 @@ __device__ __forceinline__ void column_merge(const unsigned (&v)[TPS], const uns
     }
 }
 
-// one sub-chunk: SUB targets against this thread's rows; row minima into cm, per-target warp
-// minima and the ballot of the lanes holding them into smv / smb
 // TPS targets jj..jj+TPS-1 against this thread's rows: row minima into cm (started from
 // this step's distances when FIRST, so that no sub-chunk has to fill cm with INFINITY
 // first: padded rows and targets carry finite sentinels, so no distance is NaN), per-target
