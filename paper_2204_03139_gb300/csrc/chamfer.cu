@@ -232,11 +232,11 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
     // per-warp column minima of the chunk and the ballot of the lanes that hold them
     __shared__ __align__(16) unsigned s_cv[BIDIR ? 2 : 1][BIDIR ? WARPS : 1][BIDIR ? CHUNK : 1];
     __shared__ __align__(16) unsigned s_cb[BIDIR ? 2 : 1][BIDIR ? WARPS : 1][BIDIR ? CHUNK : 1];
-    // per-row running minimum over the unit and the sub-chunk that holds it (shared-memory
-    // copy; unused and one element when it lives in registers)
+    // per-row running minimum over the unit and the sub-chunk that holds it, as the key the
+    // rows merge with, (distance bits << 32) | sub-chunk (shared-memory copy; one element,
+    // unused, when it lives in registers)
     constexpr bool REG_BEST = BestInRegs<BIDIR>::value;
-    __shared__ float s_best[REG_BEST ? 1 : ROWS_PER_THREAD][REG_BEST ? 1 : THREADS];
-    __shared__ unsigned s_bidx[REG_BEST ? 1 : ROWS_PER_THREAD][REG_BEST ? 1 : THREADS];
+    __shared__ u64 s_key[REG_BEST ? 1 : ROWS_PER_THREAD][REG_BEST ? 1 : THREADS];
     __shared__ UnitState s_u;
     __shared__ __align__(8) u64 s_bar[2];
 
@@ -316,16 +316,14 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
         }
         float r_best[REG_BEST ? ROWS_PER_THREAD : 1];
         unsigned r_bidx[REG_BEST ? ROWS_PER_THREAD : 1];
-        auto best = [&](int r) -> float& {
-            if constexpr (REG_BEST) return r_best[r]; else return s_best[r][tid];
-        };
-        auto bidx = [&](int r) -> unsigned& {
-            if constexpr (REG_BEST) return r_bidx[r]; else return s_bidx[r][tid];
-        };
 #pragma unroll
         for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-            best(r) = INFINITY;
-            bidx(r) = 0u;
+            if constexpr (REG_BEST) {
+                r_best[r] = INFINITY;
+                r_bidx[r] = 0u;
+            } else {
+                s_key[r][tid] = (u64)__float_as_uint(INFINITY) << 32;
+            }
         }
 
         const int c_lo = s_u.sub_lo / SUBS_PER_CHUNK, c_hi = (s_u.sub_hi - 1) / SUBS_PER_CHUNK;
@@ -343,12 +341,20 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
                     sub_chunk<BIDIR>(&s_t[b][0][2 * off], &s_t[b][1][2 * off], &s_t[b][2][2 * off],
                                      rx, ry, rz, cm, BIDIR ? &s_cv[b][warp][off] : nullptr,
                                      BIDIR ? &s_cb[b][warp][off] : nullptr);
+                    // distances are >= 0, so their bits order like the values
 #pragma unroll
-                    for (int r = 0; r < ROWS_PER_THREAD; ++r)
-                        if (cm[r] < best(r)) {
-                            best(r) = cm[r];
-                            bidx(r) = (unsigned)sc;
+                    for (int r = 0; r < ROWS_PER_THREAD; ++r) {
+                        if constexpr (REG_BEST) {
+                            if (cm[r] < r_best[r]) {
+                                r_best[r] = cm[r];
+                                r_bidx[r] = (unsigned)sc;
+                            }
+                        } else {
+                            const unsigned cb = __float_as_uint(cm[r]);
+                            if (cb < (unsigned)(s_key[r][tid] >> 32))
+                                s_key[r][tid] = ((u64)cb << 32) | (u64)(unsigned)sc;
                         }
+                    }
                 }
             }
             abort = __syncthreads_or(!ok) != 0;
@@ -394,9 +400,14 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
 #pragma unroll
             for (int r = 0; r < ROWS_PER_THREAD; ++r) {
                 const int row = trow0 + r;
-                if (row < N)
-                    atomicMin(&w.pab[s_u.row0 + row],
-                              ((u64)__float_as_uint(best(r)) << 32) | (u64)bidx(r));
+                if (row < N) {
+                    u64 key;
+                    if constexpr (REG_BEST)
+                        key = ((u64)__float_as_uint(r_best[r]) << 32) | (u64)r_bidx[r];
+                    else
+                        key = s_key[r][tid];
+                    atomicMin(&w.pab[s_u.row0 + row], key);
+                }
             }
         }
         s = min(s_end, w.unit_pre[u + 1]);
