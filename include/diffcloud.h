@@ -199,8 +199,9 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
  * Tuning of the Chamfer kernel's tile shape. A CTA of w warps (w = 1, 2 or 4) holds
  * w * 512 sim points in registers while target chunks stream through it: wide CTAs amortise
  * the target staging and the column merges over more points, narrow ones split small
- * problems into enough work items to fill the GPU. warps_per_cta = 0 (the default) picks the
- * widest width that still gives every resident CTA several work items. dc_tune_set sets the
+ * problems into enough work items to fill the GPU. warps_per_cta = 0 (the default) picks two
+ * warps when that gives every resident CTA several work items, else one (two measured as fast
+ * as four on uniform trajectories and faster on uneven batches). dc_tune_set sets the
  * width for every later call in the process (an autotuner times the widths per problem size
  * and sets the winner before its calls); batch plans keep the width they were planned with.
  */

@@ -470,8 +470,14 @@ int chamfer_grid(int mode, int warps) {
 
 int choose_warps(int mode, long long sub_w4, long long sub_w2, long long sub_w1) {
     if (g_tuned_warps == 1 || g_tuned_warps == 2 || g_tuned_warps == 4) return g_tuned_warps;
-    // at least 8 sub-chunks per resident CTA keeps the per-unit set-up small
-    if (sub_w4 >= 8LL * chamfer_grid(mode, 4)) return 4;
+    // Two warps per CTA whenever every resident CTA gets at least 8 sub-chunks (which keeps
+    // the per-unit set-up small), else one. Measured on GB300: width 2 is as fast as width 4
+    // on uniform trajectories (1.042 against 1.044 ms for 40 frames of 10 000 x 10 000,
+    // 24.81 against 24.85 ms for 100 of 32 768 x 32 768) and 2.5% faster on 64 uneven
+    // trajectories (271.2 against 278.1 ms), whose last unit per frame leaves fewer warps
+    // idle at width 2 (1.4% of the warp slots against 3.8%). Width 1 costs 22% more per-CTA
+    // overhead on the 40-frame trajectory. Width 4 stays available through dc_tune_set.
+    (void)sub_w4;
     if (sub_w2 >= 8LL * chamfer_grid(mode, 2)) return 2;
     return 1;
 }
