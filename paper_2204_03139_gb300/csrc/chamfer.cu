@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "dc_internal.cuh"
 
@@ -95,6 +96,14 @@ __device__ __forceinline__ bool mbar_wait(u64* bar, uint32_t parity) {
 // ---------------------------------------------------------------------------------------
 constexpr int PAIRS = ROWS_PER_THREAD / 2;  // packed row pairs per thread
 
+// Rows per lane of a warp whose frame has `left` rows from the warp's first row on: the full
+// 16, or 12 or 8 for a frame's last warp when 32 lanes of that many rows cover what is left
+// (the warp then computes 3/4 or 1/2 of a full tile instead of a tile of mostly padding).
+__device__ __forceinline__ int lane_rows(int left) {
+    static_assert(ROWS_PER_THREAD == 16, "the short tiles assume 16 rows per lane");
+    return left > 12 * 32 ? 16 : (left > 8 * 32 ? 12 : 8);
+}
+
 // What the CTA knows about the unit segment it is working on (kept in shared memory so that
 // the inner loop's registers go to the rows and the running minima).
 struct UnitState {
@@ -131,7 +140,7 @@ __device__ __forceinline__ void column_merge(const unsigned (&v)[TPS], const uns
 // this step's distances when FIRST, so that no sub-chunk has to fill cm with INFINITY
 // first: padded rows and targets carry finite sentinels, so no distance is NaN), per-target
 // warp minima and the ballot of the lanes holding them into smv / smb
-template <bool BIDIR, bool FIRST>
+template <bool BIDIR, bool FIRST, int NP>
 __device__ __forceinline__ void step(const float* __restrict__ tx, const float* __restrict__ ty,
                                      const float* __restrict__ tz, int jj,
                                      const float2 (&rx)[PAIRS], const float2 (&ry)[PAIRS],
@@ -155,7 +164,7 @@ __device__ __forceinline__ void step(const float* __restrict__ tx, const float* 
 #pragma unroll
     for (int t = 0; t < TPS; ++t) c[t] = INFINITY;
 #pragma unroll
-    for (int p = 0; p < PAIRS; ++p) {
+    for (int p = 0; p < NP; ++p) {
         float2 d[TPS];
 #pragma unroll
         for (int t = 0; t < TPS; ++t) {
@@ -190,17 +199,18 @@ __device__ __forceinline__ void step(const float* __restrict__ tx, const float* 
     }
 }
 
-// one sub-chunk: SUB targets against this thread's rows; cm receives the rows' minima over it
-template <bool BIDIR>
+// one sub-chunk: SUB targets against this thread's first 2 NP rows; cm[0 .. 2 NP) receives
+// the rows' minima over it
+template <bool BIDIR, int NP>
 __device__ __forceinline__ void sub_chunk(const float* __restrict__ tx, const float* __restrict__ ty,
                                           const float* __restrict__ tz, const float2 (&rx)[PAIRS],
                                           const float2 (&ry)[PAIRS], const float2 (&rz)[PAIRS],
                                           float (&cm)[ROWS_PER_THREAD], unsigned* __restrict__ smv,
                                           unsigned* __restrict__ smb) {
-    step<BIDIR, true>(tx, ty, tz, 0, rx, ry, rz, cm, smv, smb);
+    step<BIDIR, true, NP>(tx, ty, tz, 0, rx, ry, rz, cm, smv, smb);
 #pragma unroll(TPS == 2 ? STEP_UNROLL : 1)
     for (int jj = TPS; jj < SUB; jj += TPS)
-        step<BIDIR, false>(tx, ty, tz, jj, rx, ry, rz, cm, smv, smb);
+        step<BIDIR, false, NP>(tx, ty, tz, jj, rx, ry, rz, cm, smv, smb);
 }
 
 // Where a row's running minimum over the unit segment (and the sub-chunk holding it) lives:
@@ -301,7 +311,10 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
         const int N = s_u.N;
         const int wrow0 = s_u.rb * ROWS_PER_UNIT + warp * ROWS_PER_WARP;
         const bool wactive = wrow0 < N;
-        const int trow0 = wrow0 + lane * ROWS_PER_THREAD;
+        // rows per lane: 16, or 12 or 8 for a frame's last warp when that covers its rows, so
+        // that the warp does not compute a full tile of padding
+        const int rpl = lane_rows(N - wrow0);
+        const int trow0 = wrow0 + lane * rpl;
 
         // this thread's rows as packed pairs {x_2p, x_2p+1}, loaded straight into the pair
         // halves (inactive warps read valid rows of the frame and never use them); building
@@ -340,16 +353,19 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
             if (ok) par ^= 1u << b;
             const int sc0 = max(s_u.sub_lo, c * SUBS_PER_CHUNK);
             const int sc1 = min(s_u.sub_hi, (c + 1) * SUBS_PER_CHUNK);
-            if (ok && wactive) {
+            // the sub-chunks of this chunk with the first 2 NP rows of each lane
+            auto scan = [&](auto np) {
+                constexpr int NP = decltype(np)::value;
                 for (int sc = sc0; sc < sc1; ++sc) {
                     const int off = (sc - c * SUBS_PER_CHUNK) * SUB;
                     float cm[ROWS_PER_THREAD];  // set by the sub-chunk's first step
-                    sub_chunk<BIDIR>(&s_t[b][0][2 * off], &s_t[b][1][2 * off], &s_t[b][2][2 * off],
-                                     rx, ry, rz, cm, BIDIR ? &s_cv[b][warp][off] : nullptr,
-                                     BIDIR ? &s_cb[b][warp][off] : nullptr);
+                    sub_chunk<BIDIR, NP>(&s_t[b][0][2 * off], &s_t[b][1][2 * off],
+                                         &s_t[b][2][2 * off], rx, ry, rz, cm,
+                                         BIDIR ? &s_cv[b][warp][off] : nullptr,
+                                         BIDIR ? &s_cb[b][warp][off] : nullptr);
                     // distances are >= 0, so their bits order like the values
 #pragma unroll
-                    for (int r = 0; r < ROWS_PER_THREAD; ++r) {
+                    for (int r = 0; r < 2 * NP; ++r) {
                         if constexpr (REG_BEST) {
                             if (cm[r] < r_best[r]) {
                                 r_best[r] = cm[r];
@@ -362,6 +378,14 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
                         }
                     }
                 }
+            };
+            if (ok && wactive) {  // rpl is the same for the whole warp
+                if (rpl == 16)
+                    scan(std::integral_constant<int, 8>());
+                else if (rpl == 12)
+                    scan(std::integral_constant<int, 6>());
+                else
+                    scan(std::integral_constant<int, 4>());
             }
             abort = __syncthreads_or(!ok) != 0;
             if (abort) break;
@@ -383,7 +407,7 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
                 // warp and, within it, the lowest lane among equals), merged globally
                 const int n_active =
                     min(WARPS, div_up(N - s_u.rb * ROWS_PER_UNIT, ROWS_PER_WARP));
-                const unsigned rg0 = (unsigned)(s_u.rb * ROWS_PER_UNIT / ROWS_PER_THREAD);
+                const int urow0 = s_u.rb * ROWS_PER_UNIT;
                 const int j0 = sc0 * SUB - c * CHUNK;
                 const int jend = min(sc1 * SUB, s_u.M) - c * CHUNK;
                 for (int j = j0 + tid; j < jend; j += THREADS) {
@@ -395,9 +419,13 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
                             bw = q;
                         }
                     }
-                    const unsigned lane_first = __ffs(s_cb[b][bw][j]) - 1;
-                    const unsigned rg = rg0 + bw * 32 + lane_first;
-                    atomicMin(&w.pba[s_u.col0 + c * CHUNK + j], ((u64)bv << 32) | (u64)rg);
+                    // the target's row group: the first row of the lane holding the minimum
+                    // (groups are contiguous, so among equal minima the lowest first row
+                    // holds the lowest row index)
+                    const int lane_first = __ffs(s_cb[b][bw][j]) - 1;
+                    const int brow0 = urow0 + (int)bw * ROWS_PER_WARP;
+                    const unsigned g0 = (unsigned)(brow0 + lane_first * lane_rows(N - brow0));
+                    atomicMin(&w.pba[s_u.col0 + c * CHUNK + j], ((u64)bv << 32) | (u64)g0);
                 }
             }
         }
@@ -406,7 +434,7 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
 #pragma unroll
             for (int r = 0; r < ROWS_PER_THREAD; ++r) {
                 const int row = trow0 + r;
-                if (row < N) {
+                if (r < rpl && row < N) {
                     u64 key;
                     if constexpr (REG_BEST)
                         key = ((u64)__float_as_uint(r_best[r]) << 32) | (u64)r_bidx[r];

@@ -176,8 +176,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiA
     }
 
     // ---- target points of this slice (Eq. 1 only), 8 per warp step, 4 lanes per target ----
-    // A target's minimum points at one thread's group of ROWS_PER_THREAD sim points: lane q
-    // of the target's group checks rows RPL q .. RPL q + RPL - 1 of it.
+    // A target's minimum points at the first row of one lane's group of sim points (16 rows,
+    // or 12 or 8 in a frame's last warp): lane q of the target's group checks rows
+    // RPL q .. RPL q + RPL - 1 from there. A shorter group is followed by rows of the next
+    // group or padding, whose indices are higher, so the first match is still the lowest
+    // index attaining the minimum.
     static_assert(ROWS_PER_THREAD % 4 == 0, "four lanes share a row group");
     constexpr int RPL = ROWS_PER_THREAD / 4;
     float sba = 0.f, cba_c = 0.f;
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiA
                 if (p != EMPTY) {
                     const unsigned dq = (unsigned)(p >> 32);
                     dmin = __uint_as_float(dq);
-                    const int rb = (int)(p & 0xffffffffu) * ROWS_PER_THREAD + RPL * q;
+                    const int rb = (int)(p & 0xffffffffu) + RPL * q;
                     float4 xr[RPL];
 #pragma unroll
                     for (int t = 0; t < RPL; ++t)
