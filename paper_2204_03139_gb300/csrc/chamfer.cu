@@ -8,7 +8,7 @@
 // 64-bit atomicMin on (distance bits << 32 | position), which keeps the smallest distance
 // and, among equal distances, the lowest position. The inner loop tracks minima only; the
 // argmin is recovered afterwards (epilogue.cu) by re-scanning the one sub-chunk (rows) or
-// the one thread's 16-row group (columns) that holds it, with bit-identical arithmetic.
+// the one thread's group of rows (columns) that holds it, with bit-identical arithmetic.
 #include <math.h>
 
 #include <atomic>

@@ -123,7 +123,7 @@ struct Ws {
     float* tsoa;       // [6 * cols] per frame: X2[2 Mpad], Y2, Z2 = {-v, -v} pairs, sentinel beyond M
     float* tpl;        // [3 * cols] per frame: X[Mpad], Y, Z (the targets as given), 0 beyond M
     unsigned long long* pab;  // [rows] packed (d bits << 32 | sub-chunk)
-    unsigned long long* pba;  // [cols] packed (d bits << 32 | row group)
+    unsigned long long* pba;  // [cols] packed (d bits << 32 | first row of the lane group)
     int* nnab;         // [rows] fallback neighbour buffers
     int* nnba;         // [cols]
     float* loss;       // [n_frames] fallback loss buffer
