@@ -33,8 +33,8 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_chamfer launch on the default workload
 # (trajectory_50x50, 40 frames) in each mode, from the one-pass ncu captures summarised in
 # profiles/k_chamfer_trajectory_50x50.md (nothing is written to DRAM); None for other workloads.
-CHAMFER_TRAFFIC_BYTES = {("trajectory_50x50", "eq1"): 22.85e6,
-                         ("trajectory_50x50", "eq2"): 19.63e6}
+CHAMFER_TRAFFIC_BYTES = {("trajectory_50x50", "eq1"): 22.79e6,
+                         ("trajectory_50x50", "eq2"): 19.57e6}
 
 
 def parse():
