@@ -305,6 +305,19 @@ def test_ragged_sizes(n, m, mode):
     compare_traj(tr, g, ref, [0, 1], mode)
 
 
+@pytest.mark.parametrize("n", [768, 769, 896, 897, 1280, 1665])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tail_warp_tiles(n, mode):
+    """A frame's last warp of 512 rows takes 8 rows per lane when 256 or fewer rows are left,
+    12 when 384 or fewer, else the full 16: frames whose last warp sits on each side of both
+    boundaries (256 / 257, 384 / 385 rows left), and a short warp in a later unit."""
+    tr = W.lift_trajectory(11 + n, 9, 2, n, 900, name="tail")
+    tr, _ = parity.nudge_draws(tr)
+    g = run_traj(tr, mode)
+    ref = oracle.loss_traj(tr, mode=mode)
+    compare_traj(tr, g, ref, [0, 1], mode)
+
+
 def test_raw_draws_face_picks_and_neighbours():
     """Without moving any draw: face picks exact outside the 1e-6 window, neighbours exact
     except for points whose face pick fell inside it."""
