@@ -142,17 +142,27 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const uint8_t* face_m
                  dc_stream_t stream);
 
 /*
- * dc_loss_traj_bwd -- vertex gradient of sum_t g_t L_t given the neighbours a previous
- * dc_loss_traj returned. The sampled points are recomputed from the draws (nothing from
- * the forward is stored but nn_ab / nn_ba). face_mask as in that call.
- *   grad_frames [T]: g_t = dObjective/dL_t; frames with g_t = 0 are skipped (zero rows).
- *   grad_verts [T][V][3] out, overwritten.
+ * dc_loss_traj_bwd -- vertex gradient of an objective J(L_total, L_1 .. L_T) given the
+ * neighbours a previous dc_loss_traj returned: the derivative of Eq. 1 (or Eq. 2) with
+ * respect to each sampled point, 2 (x_i - y_nn(i)) / N for every sim point and
+ * 2 (x_nn(j) - y_j) / M for every target (Eq. 2: 2 (x_i - y_nn(i)) and no target term),
+ * scattered to the picked face's vertices with the barycentric weights of Eq. 3 as partial
+ * derivatives (Eq. 4). The face pick is piecewise constant in the vertices and contributes
+ * nothing. The sampled points are recomputed from the draws (nothing from the forward is
+ * stored but nn_ab / nn_ba). face_mask as in that call.
+ *   frame_w     [T] nullable (all ones): the weights w_t of the forward call.
+ *   grad_total  [1] nullable: dJ/dL_total, with L_total = sum_t w_t L_t.
+ *   grad_frames [T] nullable: dJ/dL_t through the per-frame losses directly.
+ *               The library forms g_t = w_t grad_total + grad_frames[t] (a missing one counts
+ *               as 0; at least one is required) and g_t = 0 for a frame of weight 0, whose
+ *               forward L_t is the constant 0. Frames with g_t = 0 are skipped (zero rows).
+ *   grad_verts [T][V][3] out, overwritten: g_t dL_t/dverts_t.
  */
 int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* face_mask,
                      const float* draws, const float* targets, int T, int V, int F, int N, int M,
-                     int mode,
-                     const int32_t* nn_ab, const int32_t* nn_ba, const float* grad_frames,
-                     float* grad_verts, void* ws, size_t ws_bytes, dc_stream_t stream);
+                     int mode, const int32_t* nn_ab, const int32_t* nn_ba, const float* frame_w,
+                     const float* grad_total, const float* grad_frames, float* grad_verts,
+                     void* ws, size_t ws_bytes, dc_stream_t stream);
 
 /*
  * Batched frames of uneven sizes (many trajectories, one launch sequence).
@@ -228,11 +238,14 @@ int dc_ws_status(const void* ws, dc_stream_t stream);
  *   until the process exits.
  *   status [1] device, nullable: receives the device-side error code of this call
  *   (DC_OK, DC_EINVAL, DC_EDEGENERATE, ...), since the scratch is not visible to the caller.
- *   Returns DC_ENOSPC, without launching anything, when dc_workspace_size(T, V, F, N, M)
- *   exceeds 16 MiB (seventeen frames of 10 000 samples against 10 000 targets on a
- *   2 500-vertex mesh).
- *   It calls no allocator. Its first call on a device looks up the scratch array's device
- *   address with that device current; make that first call before any stream capture.
+ *   Returns DC_ENOSPC when dc_workspace_size(T, V, F, N, M) exceeds 16 MiB (seventeen frames
+ *   of 10 000 samples against 10 000 targets on a 2 500-vertex mesh); that check comes
+ *   before any pointer is examined or any CUDA call is made.
+ *   It calls no allocator. Outside a stream capture every call looks up the scratch array's
+ *   device address with the current device (the lookup allocates nothing), so a context that
+ *   was reset is followed; a call inside a capture reuses the address of the last call made
+ *   outside one, so make the first call on a device before any stream capture (a capturing
+ *   first call returns DC_EINVAL).
  *   All calls on a device share the one array and each overwrites it: calls that may overlap
  *   on the GPU (different streams, or threads without ordering) race and must not be issued.
  */

@@ -68,7 +68,8 @@ def lib() -> ctypes.CDLL:
                 "dc_chamfer_bwd": (I, [P, P, P, P, I, I, I, I, P, P, P]),
                 "dc_loss_traj": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P, S,
                                      P]),
-                "dc_loss_traj_bwd": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, S, P]),
+                "dc_loss_traj_bwd": (I, [P, P, P, P, P, I, I, I, I, I, I, P, P, P, P, P, P, P,
+                                         S, P]),
                 "dc_batch_workspace_size": (S, [P, I]),
                 "dc_batch_plan": (I, [P, I, I, P, S, P]),
                 "dc_batch_run": (I, [P, P, P]),
@@ -110,32 +111,72 @@ def _stream(device) -> ctypes.c_void_p:
 
 
 def _dev(t: torch.Tensor):
-    if not t.is_cuda:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError("tensors must be on a CUDA device")
     return t.device
 
 
-def _f32(t, name):
-    if t.dtype != torch.float32 or not t.is_contiguous():
-        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+def _need(t, name, dtype, shape, dev):
+    """t must be a contiguous `dtype` tensor of exactly `shape` on `dev`: the kernels read
+    every element through raw device pointers, so anything else would make them read host
+    memory or past the end of the buffer."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device != dev:
+        raise ValueError(f"{name} must be on {dev} (it is on {t.device})")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype} (it is {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)} (it has {tuple(t.shape)})")
     return t
 
 
-def _i32(t, name):
-    if t.dtype != torch.int32 or not t.is_contiguous():
-        raise ValueError(f"{name} must be a contiguous int32 CUDA tensor")
-    return t
+def _cloud(t, name, dev, T=None):
+    """A [T, n, 3] float32 cloud; returns n."""
+    if not isinstance(t, torch.Tensor) or t.dim() != 3 or t.shape[2] != 3:
+        raise ValueError(f"{name} must be a [T, n, 3] tensor")
+    _need(t, name, torch.float32, (t.shape[0] if T is None else T, t.shape[1], 3), dev)
+    return t.shape[1]
 
 
-def _mask(m, F):
-    """face_mask: None, or a contiguous uint8 (or bool) CUDA tensor of one entry per face."""
+def _check_mesh(verts, faces, draws=None, targets=None, face_mask=None, frame_w=None,
+                nn_ab=None, nn_ba=None, grad_frames=None):
+    """Validate the tensors of a trajectory call; returns (device, T, V, F, N, M, mask)."""
+    dev = _dev(verts)
+    if verts.dim() != 3 or verts.shape[2] != 3:
+        raise ValueError("verts must be a [T, V, 3] tensor")
+    T, V = verts.shape[0], verts.shape[1]
+    _need(verts, "verts", torch.float32, (T, V, 3), dev)
+    if not isinstance(faces, torch.Tensor) or faces.dim() != 2 or faces.shape[1] != 3:
+        raise ValueError("faces must be an [F, 3] tensor")
+    F = faces.shape[0]
+    _need(faces, "faces", torch.int32, (F, 3), dev)
+    N = _cloud(draws, "draws", dev, T) if draws is not None else 0
+    M = _cloud(targets, "targets", dev, T) if targets is not None else 0
+    if frame_w is not None:
+        _need(frame_w, "frame_w", torch.float32, (T,), dev)
+    if grad_frames is not None:
+        _need(grad_frames, "grad_frames", torch.float32, (T,), dev)
+    if nn_ab is not None:
+        _need(nn_ab, "nn_ab", torch.int32, (T, N), dev)
+    if nn_ba is not None:
+        _need(nn_ba, "nn_ba", torch.int32, (T, M), dev)
+    return dev, T, V, F, N, M, _mask(face_mask, F, dev)
+
+
+def _mask(m, F, dev=None):
+    """face_mask: None, or a contiguous uint8 (or bool) tensor of one entry per face on the
+    call's device."""
     if m is None:
         return None
     if m.dtype == torch.bool:
         m = m.to(torch.uint8)
-    if m.dtype != torch.uint8 or not m.is_contiguous() or not m.is_cuda or m.numel() != F:
+    if (m.dtype != torch.uint8 or not m.is_contiguous() or not m.is_cuda or m.numel() != F
+            or (dev is not None and m.device != dev)):
         raise ValueError("face_mask must be a contiguous uint8 CUDA tensor with one entry per "
-                         "face")
+                         "face, on the device of verts")
     return m
 
 
@@ -171,10 +212,7 @@ def dc_workspace_size(T, V, F, N, M) -> int:
 def dc_area_cdf(verts, faces, face_mask=None, check=False):
     """Per-frame area CDF (Sec. III-B): [T, F] float32 inclusive prefix sums of the face areas
     (0 outside face_mask); the last entry of each row is the frame's total area."""
-    dev = _dev(verts)
-    _f32(verts, "verts"), _i32(faces, "faces")
-    T, V, F = verts.shape[0], verts.shape[1], faces.shape[0]
-    fm = _mask(face_mask, F)
+    dev, T, V, F, _, _, fm = _check_mesh(verts, faces, face_mask=face_mask)
     cdf = torch.empty((T, F), dtype=torch.float32, device=dev)
     nb = dc_workspace_size(T, V, F, 1, 0)
     if nb == 0:
@@ -191,10 +229,7 @@ def dc_sample(verts, faces, draws, face_idx=True, bary=True, check=False, face_m
     """Area-weighted sampling (Sec. III-B, Eq. 3). verts [T,V,3], faces [F,3], draws [T,N,3];
     face_mask [F] (optional): sample only the faces with a nonzero entry.
     Returns points [T,N,3], face_idx [T,N] and bary [T,N,3] (or None)."""
-    dev = _dev(verts)
-    _f32(verts, "verts"), _i32(faces, "faces"), _f32(draws, "draws")
-    T, V, F, N = verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1]
-    fm = _mask(face_mask, F)
+    dev, T, V, F, N, _, fm = _check_mesh(verts, faces, draws=draws, face_mask=face_mask)
     pts = torch.empty((T, N, 3), dtype=torch.float32, device=dev)
     fi = torch.empty((T, N), dtype=torch.int32, device=dev) if face_idx else None
     bc = torch.empty((T, N, 3), dtype=torch.float32, device=dev) if bary else None
@@ -213,8 +248,9 @@ def dc_chamfer_fwd(a, b, mode=BIDIR_MEAN, check=False):
     """Chamfer distance per frame (Eq. 1 / Eq. 2). a [T,N,3], b [T,M,3].
     Returns loss [T], nn_ab [T,N], nn_ba [T,M] (None in Eq. 2)."""
     dev = _dev(a)
-    _f32(a, "a"), _f32(b, "b")
-    T, N, M = a.shape[0], a.shape[1], b.shape[1]
+    N = _cloud(a, "a", dev)
+    T = a.shape[0]
+    M = _cloud(b, "b", dev, T)
     loss = torch.empty(T, dtype=torch.float32, device=dev)
     nn_ab = torch.empty((T, N), dtype=torch.int32, device=dev)
     nn_ba = torch.empty((T, M), dtype=torch.int32, device=dev) if mode == BIDIR_MEAN else None
@@ -232,10 +268,17 @@ def dc_chamfer_fwd(a, b, mode=BIDIR_MEAN, check=False):
 def dc_chamfer_bwd(a, b, nn_ab, nn_ba, grad_loss, mode=BIDIR_MEAN):
     """Gradient of sum_t g_t L_t w.r.t. a. Returns grad_a [T,N,3]."""
     dev = _dev(a)
-    T, N, M = a.shape[0], a.shape[1], b.shape[1]
+    N = _cloud(a, "a", dev)
+    T = a.shape[0]
+    M = _cloud(b, "b", dev, T)
+    _need(nn_ab, "nn_ab", torch.int32, (T, N), dev)
+    if mode == BIDIR_MEAN:
+        _need(nn_ba, "nn_ba", torch.int32, (T, M), dev)
+    _need(grad_loss, "grad_loss", torch.float32, (T,), dev)
     g = torch.empty_like(a)
-    _check(lib().dc_chamfer_bwd(_ptr(a), _ptr(b), _ptr(nn_ab), _ptr(nn_ba), T, N, M, mode,
-                                _ptr(_f32(grad_loss, "grad_loss")), _ptr(g), _stream(dev)))
+    _check(lib().dc_chamfer_bwd(_ptr(a), _ptr(b), _ptr(nn_ab),
+                                _ptr(nn_ba if mode == BIDIR_MEAN else None), T, N, M, mode,
+                                _ptr(grad_loss), _ptr(g), _stream(dev)))
     return g
 
 
@@ -244,13 +287,10 @@ def dc_loss_traj(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None, gr
     """The whole loss over a trajectory (Sec. III-B, Eq. 1-4).
 
     verts [T,V,3], faces [F,3], draws [T,N,3], targets [T,M,3] (CUDA, contiguous); face_mask
-    [F] (optional): sample only the faces with a nonzero entry.
+    [F] (optional): sample only the faces with a nonzero entry; frame_w [T] float32 (optional).
     Returns a dict with loss_total [1] (or None), loss_frames [T], grad_verts [T,V,3] (or
     None), nn_ab [T,N], nn_ba [T,M] (or None). `out` may supply preallocated outputs."""
-    dev = _dev(verts)
-    _f32(verts, "verts"), _i32(faces, "faces"), _f32(draws, "draws"), _f32(targets, "targets")
-    T, V, F, N, M = (verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1],
-                     targets.shape[1])
+    dev, T, V, F, N, M, fm = _check_mesh(verts, faces, draws, targets, face_mask, frame_w)
     o = out if out is not None else {}
     lt = o.get("loss_total") if total else None
     if total and lt is None:
@@ -270,13 +310,21 @@ def dc_loss_traj(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None, gr
             nba = o.get("nn_ba")
             if nba is None:
                 nba = torch.empty((T, M), dtype=torch.int32, device=dev)
+    if lt is not None:
+        _need(lt, "loss_total", torch.float32, (1,), dev)
+    _need(lf, "loss_frames", torch.float32, (T,), dev)
+    if gv is not None:
+        _need(gv, "grad_verts", torch.float32, (T, V, 3), dev)
+    if nab is not None:
+        _need(nab, "nn_ab", torch.int32, (T, N), dev)
+    if nba is not None:
+        _need(nba, "nn_ba", torch.int32, (T, M), dev)
     nb = dc_workspace_size(T, V, F, N, M)
     if nb == 0:
         raise DCError(DC_EINVAL, "bad sizes")
     ws = o.get("ws")
     if ws is None or ws.numel() < nb:
         ws = workspace(nb, dev)
-    fm = _mask(face_mask, F)
     _check(lib().dc_loss_traj(_ptr(verts), _ptr(faces), _ptr(fm), _ptr(draws), _ptr(targets), T,
                               V, F, N, M, mode, _ptr(frame_w), _ptr(lt), _ptr(lf), _ptr(gv),
                               _ptr(nab), _ptr(nba), _ptr(ws), ws.numel(), _stream(dev)))
@@ -285,19 +333,30 @@ def dc_loss_traj(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=None, gr
     return {"loss_total": lt, "loss_frames": lf, "grad_verts": gv, "nn_ab": nab, "nn_ba": nba}
 
 
-def dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab, nn_ba, grad_frames,
-                     mode=BIDIR_MEAN, check=False, grad_verts=None, face_mask=None):
-    """Vertex gradient of sum_t g_t L_t, recomputing the samples from the draws."""
-    dev = _dev(verts)
-    T, V, F, N, M = (verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1],
-                     targets.shape[1])
+def dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab, nn_ba, grad_frames=None,
+                     mode=BIDIR_MEAN, check=False, grad_verts=None, face_mask=None,
+                     frame_w=None, grad_total=None):
+    """Vertex gradient of an objective J(L_total, L_1..L_T), recomputing the samples from the
+    draws. The library forms g_t = dJ/dL_t = w_t grad_total + grad_frames[t] (w_t from
+    frame_w, default 1; a missing grad_total or grad_frames counts as 0; a frame of weight 0
+    gets g_t = 0, as its forward L_t is the constant 0)."""
+    dev, T, V, F, N, M, fm = _check_mesh(
+        verts, faces, draws, targets, face_mask, frame_w, nn_ab,
+        nn_ba if mode == BIDIR_MEAN else None, grad_frames)
+    if grad_total is None and grad_frames is None:
+        raise ValueError("grad_total or grad_frames is required")
+    if grad_total is not None:
+        _need(grad_total, "grad_total", torch.float32, (1,), dev)
     gv = grad_verts if grad_verts is not None else torch.empty_like(verts)
+    _need(gv, "grad_verts", torch.float32, (T, V, 3), dev)
     nb = dc_workspace_size(T, V, F, N, M)
+    if nb == 0:
+        raise DCError(DC_EINVAL, "bad sizes")
     ws = workspace(nb, dev)
-    fm = _mask(face_mask, F)
     _check(lib().dc_loss_traj_bwd(_ptr(verts), _ptr(faces), _ptr(fm), _ptr(draws), _ptr(targets),
-                                  T, V, F, N, M, mode, _ptr(nn_ab), _ptr(nn_ba),
-                                  _ptr(_f32(grad_frames, "grad_frames")), _ptr(gv), _ptr(ws),
+                                  T, V, F, N, M, mode, _ptr(nn_ab),
+                                  _ptr(nn_ba if mode == BIDIR_MEAN else None), _ptr(frame_w),
+                                  _ptr(grad_total), _ptr(grad_frames), _ptr(gv), _ptr(ws),
                                   ws.numel(), _stream(dev)))
     if check:
         check_ws(ws)
@@ -325,17 +384,13 @@ def dc_loss_traj_noalloc(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=
     for callers that cannot allocate device memory when they need the loss. The outputs are
     allocated here for convenience; a caller that cannot allocate passes its own buffers to
     the C function directly. check=True reads the device-side status the call wrote."""
-    dev = _dev(verts)
-    _f32(verts, "verts"), _i32(faces, "faces"), _f32(draws, "draws"), _f32(targets, "targets")
-    T, V, F, N, M = (verts.shape[0], verts.shape[1], faces.shape[0], draws.shape[1],
-                     targets.shape[1])
+    dev, T, V, F, N, M, fm = _check_mesh(verts, faces, draws, targets, face_mask, frame_w)
     lt = torch.empty(1, dtype=torch.float32, device=dev)
     lf = torch.empty(T, dtype=torch.float32, device=dev)
     gv = torch.empty((T, V, 3), dtype=torch.float32, device=dev) if grad else None
     nab = torch.empty((T, N), dtype=torch.int32, device=dev)
     nba = torch.empty((T, M), dtype=torch.int32, device=dev) if mode == BIDIR_MEAN else None
     st = torch.zeros(1, dtype=torch.int32, device=dev)
-    fm = _mask(face_mask, F)
     _check(lib().dc_loss_traj_noalloc(_ptr(verts), _ptr(faces), _ptr(fm), _ptr(draws),
                                       _ptr(targets), T, V, F, N, M, mode, _ptr(frame_w),
                                       _ptr(lt), _ptr(lf), _ptr(gv), _ptr(nab), _ptr(nba),

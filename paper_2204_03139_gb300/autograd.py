@@ -12,42 +12,48 @@ from . import _lib
 
 
 class DCLoss(torch.autograd.Function):
-    """loss_frames[t] = L_t(verts[t]); differentiable with respect to verts only. Frames
-    whose entry of frame_w is 0 are skipped (their L_t is reported as 0)."""
+    """(L_total, loss_frames): L_total = sum_t w_t L_t and L_t(verts[t]), both computed by the
+    library; differentiable with respect to verts only. Frames whose entry of frame_w is 0
+    are skipped (their L_t is reported as the constant 0 and gets no gradient)."""
 
     @staticmethod
     def forward(ctx, verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, face_mask=None,
                 frame_w=None):
         verts = verts.detach().contiguous()
-        r = _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode, grad=False, total=False,
+        r = _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode, grad=False, total=True,
                               nn=True, face_mask=face_mask, frame_w=frame_w)
         ctx.mode = mode
         ctx.face_mask = face_mask
+        ctx.frame_w = frame_w
+        ctx.set_materialize_grads(False)
         nn_ba = r["nn_ba"] if r["nn_ba"] is not None else r["nn_ab"]
         ctx.save_for_backward(verts, faces, draws, targets, r["nn_ab"], nn_ba)
-        return r["loss_frames"]
+        return r["loss_total"].reshape(()), r["loss_frames"]
 
     @staticmethod
-    def backward(ctx, grad_frames):
+    def backward(ctx, grad_total, grad_frames):
         verts, faces, draws, targets, nn_ab, nn_ba = ctx.saved_tensors
+        if grad_total is None and grad_frames is None:
+            return None, None, None, None, None, None, None
+        # the library forms g_t = w_t grad_total + grad_frames[t] itself
+        gt = None if grad_total is None else grad_total.detach().reshape(1).float().contiguous()
+        gf = None if grad_frames is None else grad_frames.detach().float().contiguous()
         g = _lib.dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab,
-                                  nn_ba if ctx.mode == _lib.BIDIR_MEAN else None,
-                                  grad_frames.detach().float().contiguous(), mode=ctx.mode,
-                                  face_mask=ctx.face_mask)
+                                  nn_ba if ctx.mode == _lib.BIDIR_MEAN else None, gf,
+                                  mode=ctx.mode, face_mask=ctx.face_mask, frame_w=ctx.frame_w,
+                                  grad_total=gt)
         return g, None, None, None, None, None, None
 
 
 def loss_traj(verts, faces, draws, targets, mode=_lib.BIDIR_MEAN, frame_w=None,
               face_mask=None):
-    """Differentiable sum_t w_t L_t (w_t = 1 by default) and the per-frame losses.
-    face_mask [F] (optional): sample only the faces with a nonzero entry. Frames of weight 0
-    do no work in either direction (their L_t is reported as 0)."""
+    """Differentiable sum_t w_t L_t (w_t = 1 by default) and the per-frame losses, both from
+    the library. face_mask [F] (optional): sample only the faces with a nonzero entry. Frames
+    of weight 0 do no work in either direction (their L_t is reported as 0)."""
     fw = None
     if frame_w is not None:
         fw = torch.as_tensor(frame_w, dtype=torch.float32, device=verts.device).contiguous()
-    lf = DCLoss.apply(verts, faces, draws, targets, mode, face_mask, fw)
-    w = torch.ones_like(lf) if fw is None else fw
-    return (w * lf).sum(), lf
+    return DCLoss.apply(verts, faces, draws, targets, mode, face_mask, fw)
 
 
 class DiffCloudLoss(torch.nn.Module):

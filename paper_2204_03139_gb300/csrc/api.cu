@@ -408,16 +408,17 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const uint8_t* face_m
 
 int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* face_mask,
                      const float* draws, const float* targets, int T, int V, int F, int N, int M,
-                     int mode,
-                     const int32_t* nn_ab, const int32_t* nn_ba, const float* grad_frames,
-                     float* grad_verts, void* ws, size_t ws_bytes, dc_stream_t stream) {
+                     int mode, const int32_t* nn_ab, const int32_t* nn_ba, const float* frame_w,
+                     const float* grad_total, const float* grad_frames, float* grad_verts,
+                     void* ws, size_t ws_bytes, dc_stream_t stream) {
     int rc = check_common(T, N, M, mode);
     if (rc) return rc;
     if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
-    rc = check_ptrs({verts, faces, draws, targets, nn_ab, grad_frames, grad_verts},
-                    "dc_loss_traj_bwd");
+    rc = check_ptrs({verts, faces, draws, targets, nn_ab, grad_verts}, "dc_loss_traj_bwd");
     if (rc) return rc;
     if (mode == DC_BIDIR_MEAN && !nn_ba) return fail(DC_EINVAL, "nn_ba is required in Eq. 1");
+    if (!grad_total && !grad_frames)
+        return fail(DC_EINVAL, "dc_loss_traj_bwd: grad_total or grad_frames is required");
     UniformArgs a{};
     a.verts = verts;
     a.faces = faces;
@@ -427,7 +428,10 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* fa
     a.nn_ab = const_cast<int32_t*>(nn_ab);
     a.nn_ba = mode == DC_BIDIR_MEAN ? const_cast<int32_t*>(nn_ba) : nullptr;
     a.grad = grad_verts;
-    a.gscale = grad_frames;
+    a.weight = frame_w;
+    a.gtotal = grad_total;
+    a.gframes = grad_frames;
+    a.bwd = 1;
     a.T = T;
     a.V = V;
     a.F = F;
@@ -645,8 +649,8 @@ extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
     int rc = check_common(T, N, M, mode);
     if (rc) return rc;
     if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
-    rc = check_ptrs({verts, faces, draws, targets, loss_frames}, "dc_loss_traj_noalloc");
-    if (rc) return rc;
+    // the size check comes first: a problem that does not fit is refused before any pointer
+    // is looked at or any CUDA call is made
     const size_t need = dc_workspace_size(T, V, F, N, M);
     if (need == 0) return fail(DC_EINVAL, "problem too large for 32-bit offsets");
     if (need > DC_NOALLOC_SCRATCH_BYTES)
@@ -654,15 +658,26 @@ extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
                     "dc_loss_traj_noalloc: this problem needs %zu bytes of scratch; the built-in "
                     "scratch holds %u bytes (use dc_loss_traj with a workspace)",
                     need, DC_NOALLOC_SCRATCH_BYTES);
+    rc = check_ptrs({verts, faces, draws, targets, loss_frames}, "dc_loss_traj_noalloc");
+    if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(DC_EINVAL, "device index %d out of range", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap);
+    if (e) return cuda_fail(e, "cudaStreamIsCapturing");
     void* ws = nullptr;
     {
-        // first call on this device (with it current): look up the array's device address
+        // The array's device address, with this device current. It is looked up again on every
+        // call outside a stream capture (the lookup allocates nothing), so that a context that
+        // was reset and reloaded the module is followed; inside a capture the address from the
+        // last call outside one is used, so the first call on a device must precede any capture.
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
+            if (cap != cudaStreamCaptureStatusNone)
+                return fail(DC_EINVAL, "dc_loss_traj_noalloc: the first call on a device must "
+                                       "come before any stream capture");
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");

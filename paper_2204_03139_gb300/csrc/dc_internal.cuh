@@ -182,8 +182,10 @@ struct UniformArgs {
     float* out_pts;
     int* out_face;
     float* out_bary;
-    const float* weight;   // [T] nullable
-    const float* gscale;   // [T] nullable: defaults to weight
+    const float* weight;   // [T] nullable: w_t, default 1
+    const float* gtotal;   // [1] nullable (backward only): dJ/dL_total
+    const float* gframes;  // [T] nullable (backward only): dJ/dL_t directly
+    int bwd;               // 1: gradient multipliers g_t = w_t gtotal + gframes[t]
     int T, V, F, N, M, mode, units_per_frame, subs_per_unit, slices, warps;
 };
 

@@ -27,6 +27,21 @@ __device__ __forceinline__ int last_le(const int* pre, int n, int g) {
 
 __device__ __forceinline__ bool coord_ok(float v) { return fabsf(v) <= COORD_MAX; }
 
+// Frame k's weight w_t in the total and the multiplier of its gradient. The forward uses w_t
+// for both. The recomputing backward gets the objective's derivatives: g_t = dJ/dL_t =
+// w_t dJ/dL_total + dJ/dL_t(direct), and 0 for a frame of weight 0, whose forward L_t is the
+// constant 0.
+__device__ __forceinline__ void frame_scales(const UniformArgs& a, int k, float& w, float& gs) {
+    w = a.weight ? a.weight[k] : 1.0f;
+    if (a.bwd) {
+        const float gt = a.gtotal ? a.gtotal[0] : 0.0f;
+        const float gf = a.gframes ? a.gframes[k] : 0.0f;
+        gs = w == 0.0f ? 0.0f : __fadd_rn(__fmul_rn(w, gt), gf);
+    } else {
+        gs = w;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // uniform trajectory -> frame table, row/column prefixes and Chamfer units. One block: the
 // Chamfer work of a frame whose weight (or gradient multiplier) is 0 is left out, which
@@ -71,8 +86,7 @@ __device__ void build_uniform(const UniformArgs& a, const Ws& w) {
             f.M = a.M;
             f.Npad = Npad;
             f.Mpad = Mpad;
-            f.weight = a.weight ? a.weight[k] : 1.0f;
-            f.gscale = a.gscale ? a.gscale[k] : f.weight;
+            frame_scales(a, k, f.weight, f.gscale);
             f.skip = f.weight == 0.0f || f.gscale == 0.0f;
             live = !f.skip;
             f.row0 = k * Npad;
@@ -305,8 +319,8 @@ __global__ void __launch_bounds__(CDF_THREADS) k_build_area(UniformArgs a, Ws w)
     const int t = blockIdx.x - 1;
     if (threadIdx.x == 0) s_err = DC_OK;
     __syncthreads();
-    const float wt = a.weight ? a.weight[t] : 1.0f;
-    const float gs = a.gscale ? a.gscale[t] : wt;
+    float wt, gs;
+    frame_scales(a, t, wt, gs);
     const AreaFrame af{a.verts + 3LL * t * a.V, a.faces, a.mask,
                        a.grad ? a.grad + 3LL * t * a.V : nullptr, w.cdf + (long long)t * a.F,
                        a.F, a.V, wt == 0.0f || gs == 0.0f};

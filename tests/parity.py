@@ -49,6 +49,37 @@ def nudge_draws(traj, window: float = WINDOW):
     return tr, moved
 
 
+def expected_moves(traj, window: float = WINDOW) -> float:
+    """How many draws nudge_draws is expected to move: a uniform r_f falls within `window` of
+    one of the frame's interior CDF boundaries with probability 2 window (F+ - 1), where F+
+    counts the faces of positive area weight (faces outside a subset add no boundary)."""
+    mask = getattr(traj, "face_mask", None)
+    e = 0.0
+    for t in range(traj.T):
+        a = oracle.face_areas(traj.verts[t], traj.faces, mask)
+        e += traj.n(t) * 2.0 * window * max(int(np.count_nonzero(a > 0)) - 1, 0)
+    return e
+
+
+def check_moves(traj, moved: int, window: float = WINDOW):
+    """The number of draws nudge_draws moved is near its expectation: far fewer would mean a
+    margin that comes out too large (draws on a boundary left in place), far more one that
+    comes out too small (draws moved for nothing). Poisson-distributed, so 3x either way is
+    many standard deviations once the expectation reaches a few tens."""
+    e = expected_moves(traj, window)
+    assert moved <= 3.0 * e + 6.0, f"{moved} draws moved, {e:.1f} expected"
+    if e >= 20.0:
+        assert moved >= e / 3.0, f"{moved} draws moved, {e:.1f} expected"
+    return e
+
+
+def nudged(traj, window: float = WINDOW):
+    """nudge_draws with its count of moved draws checked against the expectation."""
+    tr, moved = nudge_draws(traj, window)
+    check_moves(traj, moved, window)
+    return tr
+
+
 def rel_l2(a, b) -> float:
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)

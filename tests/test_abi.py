@@ -87,6 +87,53 @@ def test_host_side_validation(L):
     assert rc == _lib.DC_EINVAL
 
 
+NOALLOC_SCRATCH_BYTES = 16 << 20  # the built-in scratch of dc_loss_traj_noalloc
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch(L):
+    """dc_loss_traj_noalloc refuses a problem whose workspace exceeds its built-in scratch
+    before it looks at any pointer or makes any CUDA call: every pointer here is NULL, so a
+    regression of that order would fail with DC_EINVAL instead, and nothing would launch."""
+    from paper_2204_03139_gb300 import _lib
+
+    T, V, F, N, M = 16, 2500, 4802, 10000, 10000
+    while _lib.dc_workspace_size(T, V, F, N, M) <= 4 * NOALLOC_SCRATCH_BYTES:
+        T *= 2
+    rc = L.dc_loss_traj_noalloc(None, None, None, None, None, T, V, F, N, M, 0,
+                                None, None, None, None, None, None, None, None)
+    assert rc == _lib.DC_ENOSPC
+    assert "built-in scratch" in _lib.last_error()
+    # one that fits gets as far as the pointer checks
+    rc = L.dc_loss_traj_noalloc(None, None, None, None, None, 1, 625, 1152, 2048, 2048, 0,
+                                None, None, None, None, None, None, None, None)
+    assert rc == _lib.DC_EINVAL and "NULL" in _lib.last_error()
+
+
+def test_loss_traj_bwd_needs_an_upstream_gradient(L):
+    from paper_2204_03139_gb300 import _lib
+
+    rc = L.dc_loss_traj_bwd(FAKE, FAKE, None, FAKE, FAKE, 1, 3, 1, 4, 4, 0, FAKE, FAKE,
+                            None, None, None, FAKE, FAKE, 1 << 20, None)
+    assert rc == _lib.DC_EINVAL and "grad_total or grad_frames" in _lib.last_error()
+
+
+def test_binding_validates_tensors():
+    """The Python binding refuses tensors of the wrong device, dtype, shape or layout before
+    any pointer reaches the library (checked with CPU tensors, which are refused first)."""
+    import torch
+
+    from paper_2204_03139_gb300 import _lib
+
+    v = torch.zeros((2, 3, 3))
+    f = torch.zeros((1, 3), dtype=torch.int32)
+    with pytest.raises(ValueError):
+        _lib._check_mesh(v, f)
+    meta = torch.device("meta")
+    vm = torch.zeros((2, 3, 3), device=meta)
+    with pytest.raises(ValueError):  # not CUDA
+        _lib._check_mesh(vm, f.to(meta))
+
+
 def test_batch_validation(L):
     from paper_2204_03139_gb300 import _lib
 

@@ -18,7 +18,7 @@ def trajs():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     tr = W.batched_uneven(n_traj=4, grid=(12, 30), T=(3, 5), m=(300, 3000))
-    return [parity.nudge_draws(t)[0] for t in tr]
+    return [parity.nudged(t) for t in tr]
 
 
 @pytest.mark.parametrize("graph", [False, True])
@@ -80,7 +80,7 @@ def test_batch_with_face_subsets(trajs):
         t = copy.copy(t)
         n = int(round(t.V ** 0.5))
         t.face_mask = W.upper_half_mask(n) if k % 2 == 0 else None
-        mtr.append(parity.nudge_draws(t)[0])
+        mtr.append(parity.nudged(t))
     b = BatchedLoss([DeviceTrajectory.from_host(t, DEV) for t in mtr], grad=True)
     b.run(check=True)
     torch.cuda.synchronize()
@@ -114,7 +114,7 @@ def test_batched_uneven_full_size_sampled_frames():
 
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    trajs = [parity.nudge_draws(t)[0] for t in W.batched_uneven()]
+    trajs = [parity.nudged(t) for t in W.batched_uneven()]
     dts = [DeviceTrajectory.from_host(t, DEV) for t in trajs]
     b = BatchedLoss(dts, grad=True, graph=True, nn=True)
     b.run(check=True)

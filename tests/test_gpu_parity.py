@@ -71,7 +71,7 @@ def compare_traj(tr, g, ref, frames, mode=0, weights=None):
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("mode", [0, 1])
 def test_single_frame_25x25(mode):
-    tr, moved = parity.nudge_draws(W.single_frame())
+    tr = parity.nudged(W.single_frame())
     g = run_traj(tr, mode)
     ref = oracle.loss_traj(tr, mode=mode)
     compare_traj(tr, g, ref, [0], mode)
@@ -80,7 +80,7 @@ def test_single_frame_25x25(mode):
 def test_trajectory_50x50_full_size_sampled_frames():
     """The 40-frame 50x50 trajectory at full size (10 000 x 10 000 per frame), in the launch
     configuration the bench times; the oracle checks frames 0, 19 and 39."""
-    tr, moved = parity.nudge_draws(W.trajectory_50x50())
+    tr = parity.nudged(W.trajectory_50x50())
     g = run_traj(tr)
     frames = [0, 19, 39]
     ref = oracle.loss_traj(tr, frames=frames)
@@ -89,7 +89,7 @@ def test_trajectory_50x50_full_size_sampled_frames():
 
 
 def test_trajectory_50x50_weights_total():
-    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=4, n=3000, m=2500))
+    tr = parity.nudged(W.trajectory_50x50(T=4, n=3000, m=2500))
     w = [0.25, 0.5, 1.0, 2.0]
     g = run_traj(tr, frame_w=w)
     ref = oracle.loss_traj(tr, weights=w)
@@ -100,7 +100,7 @@ def test_trajectory_50x50_weights_total():
 def test_many_small_frames_one_epilogue_slice_each(mode):
     """700 frames: one epilogue CTA per frame writes the gradient directly (no slice
     reduction); every frame against the oracle."""
-    tr, _ = parity.nudge_draws(W.lift_trajectory(41, 8, 700, 96, 80, name="many"))
+    tr = parity.nudged(W.lift_trajectory(41, 8, 700, 96, 80, name="many"))
     g = run_traj(tr, mode)
     ref = oracle.loss_traj(tr, mode=mode)
     compare_traj(tr, g, ref, list(range(tr.T)), mode)
@@ -111,7 +111,7 @@ def test_large_mesh_global_memory_paths(mode):
     """A 175 x 175 grid (30 625 vertices, 60 552 faces): the V x 3 gradient accumulator does
     not fit in shared memory (the scatter goes to global memory) and neither does the area
     CDF (sampling and target staging search it in global memory)."""
-    tr, _ = parity.nudge_draws(W.lift_trajectory(43, 175, 2, 3000, 2500, name="big_mesh"))
+    tr = parity.nudged(W.lift_trajectory(43, 175, 2, 3000, 2500, name="big_mesh"))
     assert tr.V * 12 > 227 * 1024 and tr.F * 4 > 227 * 1024
     g = run_traj(tr, mode)
     ref = oracle.loss_traj(tr, mode=mode)
@@ -156,7 +156,7 @@ def test_bounded_wait_gives_up_with_a_timeout_status_and_the_device_stays_usable
     """The Chamfer kernel's waits for its target chunks are bounded (2 s). A launch whose
     first chunk is never requested must end with DC_ETIMEOUT in the workspace status, and the
     next call on the same context must produce the normal result."""
-    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=2, n=2000, m=2000))
+    tr = parity.nudged(W.trajectory_50x50(T=2, n=2000, m=2000))
     v, f, d, y = to_dev(tr)
     good = L().dc_loss_traj(v, f, d, y, check=True)
     ref_loss = good["loss_frames"].cpu().numpy().copy()
@@ -213,7 +213,7 @@ def test_face_subset_matches_oracle(mode):
     neighbours, loss and gradient against the oracle with the same mask; no sample lands on a
     masked face and vertices touched only by masked faces get no gradient."""
     mask = W.upper_half_mask(50)
-    tr, _ = parity.nudge_draws(masked(W.trajectory_50x50(T=3, n=4000, m=3000), mask))
+    tr = parity.nudged(masked(W.trajectory_50x50(T=3, n=4000, m=3000), mask))
     g = run_traj(tr, mode)
     ref = oracle.loss_traj(tr, mode=mode)
     compare_traj(tr, g, ref, list(range(tr.T)), mode)
@@ -238,7 +238,7 @@ def test_face_subset_matches_oracle(mode):
 
 
 def test_full_mask_changes_nothing_and_empty_subset_is_degenerate():
-    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=2, n=2000, m=2000))
+    tr = parity.nudged(W.trajectory_50x50(T=2, n=2000, m=2000))
     a = run_traj(tr)
     b = run_traj(masked(tr, np.ones(tr.F, np.uint8)))
     np.testing.assert_array_equal(a["nn_ab"], b["nn_ab"])
@@ -254,7 +254,7 @@ def test_full_mask_changes_nothing_and_empty_subset_is_degenerate():
 def test_zero_weight_frames_are_skipped(w):
     """Frames of weight 0 (e.g. last-frame-only, as the paper mostly optimises) do no work:
     their L_t is reported as 0 and their gradient is 0; the other frames are unchanged."""
-    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=4, n=3000, m=2500))
+    tr = parity.nudged(W.trajectory_50x50(T=4, n=3000, m=2500))
     g = run_traj(tr, frame_w=w)
     live = [t for t in range(4) if w[t] != 0.0]
     dead = [t for t in range(4) if w[t] == 0.0]
@@ -282,7 +282,7 @@ def test_zero_weight_frames_are_skipped(w):
 @pytest.mark.slow
 def test_trajectory_100x100_full_size_sampled_frames():
     """100x100 grid, T = 100, 32 768 x 32 768 per frame; the oracle checks two frames."""
-    tr, moved = parity.nudge_draws(W.trajectory_100x100())
+    tr = parity.nudged(W.trajectory_100x100())
     g = run_traj(tr)
     frames = [0, 99]
     ref = oracle.loss_traj(tr, frames=frames)
@@ -299,7 +299,7 @@ def test_trajectory_100x100_full_size_sampled_frames():
 @pytest.mark.parametrize("mode", [0, 1])
 def test_ragged_sizes(n, m, mode):
     tr = W.lift_trajectory(7 + n + 3 * m, 9, 2, n, m, name="ragged")
-    tr, _ = parity.nudge_draws(tr)
+    tr = parity.nudged(tr)
     g = run_traj(tr, mode)
     ref = oracle.loss_traj(tr, mode=mode)
     compare_traj(tr, g, ref, [0, 1], mode)
@@ -312,7 +312,7 @@ def test_tail_warp_tiles(n, mode):
     12 when 384 or fewer, else the full 16: frames whose last warp sits on each side of both
     boundaries (256 / 257, 384 / 385 rows left), and a short warp in a later unit."""
     tr = W.lift_trajectory(11 + n, 9, 2, n, 900, name="tail")
-    tr, _ = parity.nudge_draws(tr)
+    tr = parity.nudged(tr)
     g = run_traj(tr, mode)
     ref = oracle.loss_traj(tr, mode=mode)
     compare_traj(tr, g, ref, [0, 1], mode)
@@ -339,7 +339,7 @@ def test_raw_draws_face_picks_and_neighbours():
 # the individual entry points
 # ---------------------------------------------------------------------------------------------
 def test_dc_sample_matches_oracle():
-    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=2, n=5000, m=1))
+    tr = parity.nudged(W.trajectory_50x50(T=2, n=5000, m=1))
     v, f, d, _ = to_dev(tr)
     pts, fi, bc = L().dc_sample(v, f, d, check=True)
     torch.cuda.synchronize()
@@ -394,7 +394,7 @@ def test_chamfer_self_zero_and_shift():
 
 
 def test_loss_traj_bwd_recompute_equals_fused():
-    tr, _ = parity.nudge_draws(W.trajectory_50x50(T=3, n=4000, m=3500))
+    tr = parity.nudged(W.trajectory_50x50(T=3, n=4000, m=3500))
     v, f, d, y = to_dev(tr)
     r = L().dc_loss_traj(v, f, d, y, check=True)
     gf = torch.ones(3, device=DEV)
@@ -408,7 +408,7 @@ def test_autograd_matches_oracle_and_fd():
     the oracle's own FP64 central differences on 200 random vertex coordinates."""
     from paper_2204_03139_gb300.autograd import loss_traj
 
-    tr, _ = parity.nudge_draws(W.lift_trajectory(99, 100, 2, 2048, 2048, name="fd"))
+    tr = parity.nudged(W.lift_trajectory(99, 100, 2, 2048, 2048, name="fd"))
     v, f, d, y = to_dev(tr)
     vv = v.clone().requires_grad_(True)
     total, lf = loss_traj(vv, f, d, y)

@@ -25,8 +25,8 @@ def _mix(n, seed=7):
         g = int(rng.integers(10, 40))
         T = int(rng.integers(2, 6))
         m = int(rng.integers(300, 4000))
-        out.append(parity.nudge_draws(
-            W.lift_trajectory(int(rng.integers(1 << 30)), g, T, m, m, name=f"mix{k}"))[0])
+        out.append(parity.nudged(
+            W.lift_trajectory(int(rng.integers(1 << 30)), g, T, m, m, name=f"mix{k}")))
     return out
 
 

@@ -67,6 +67,65 @@ def test_equal_area_pick_is_floor():
     np.testing.assert_array_equal(r["face_idx"], expect)
 
 
+def test_pick_margin_closed_form_equal_area_grid():
+    """The margin returned with each pick is the distance of r_f to the nearer interior CDF
+    boundary, in units of A. On the exactly-equal-area 17x17 grid the interior boundaries are
+    k/F for k = 1 .. F-1, so r = k/F + e has margin |e| (for |e| < 1/(2F)), a draw exactly on
+    a boundary has margin 0, and the first and last faces have only one boundary each. The
+    parity tests rely on it to decide which draws are ill-posed."""
+    tr = W.flat_square(17, 10, seed=11)
+    F = tr.F
+    cdf = oracle.area_cdf(oracle.face_areas(tr.verts[0], tr.faces))
+    rng = np.random.default_rng(5)
+    k = rng.integers(1, F, size=600)
+    e = rng.uniform(0.0, 0.49 / F, size=600) * np.where(rng.random(600) < 0.5, -1.0, 1.0)
+    r = np.concatenate([(k / F + e), np.arange(1, F) / F, [0.0, 0.3 / F, 1.0 - 0.3 / F]])
+    r = r.astype(np.float32)
+    for ri in r:
+        f, m = oracle.pick_face(cdf, float(ri))
+        rd = float(ri)
+        j = min(max(int(np.rint(rd * F)), 1), F - 1)  # nearest interior boundary j/F
+        assert f == int(np.floor(rd * F))
+        assert m == abs(rd - j / F), (rd, f, m)
+    # draws close to a boundary: the margin is the offset itself
+    for kk in (1, 7, 255, 511):
+        for off in (2.0 ** -20, 2.0 ** -16, 2.0 ** -12):
+            _, m = oracle.pick_face(cdf, float(np.float32(kk / F + off)))
+            assert m == off
+            _, m = oracle.pick_face(cdf, float(np.float32(kk / F - off)))
+            assert m == off
+
+
+def test_pick_margin_two_triangles():
+    """The worked example's CDF is (1, 1.5): one interior boundary at 2/3, so draw A (r = 1/2)
+    has margin 1/6 and draw B (r = 3/4) margin 1/12."""
+    g = _golden()
+    v = np.array(g["verts"], np.float32)
+    f = np.array(g["faces"], np.int32)
+    cdf = oracle.area_cdf(oracle.face_areas(v, f))
+    d = np.array(g["draws"], np.float32)
+    r = oracle.frame(v, f, d, np.array(g["targets"], np.float32))
+    np.testing.assert_allclose(r["margin"], [1 / 6, 1 / 12], rtol=1e-15)
+    assert oracle.pick_face(cdf, 0.5)[1] == pytest.approx(1 / 6, rel=1e-15)
+
+
+def test_nudge_moves_the_expected_number_of_draws():
+    """parity.nudge_draws moves exactly the draws whose margin is below the window, to the
+    middle of their face's interval, and their number matches 2 w (F - 1) per draw."""
+    import parity
+
+    tr = W.trajectory_50x50(T=3, n=20000, m=10)
+    moved_tr, moved = parity.nudge_draws(tr, window=2e-6)
+    parity.check_moves(tr, moved, window=2e-6)
+    assert moved > 0
+    for t in range(tr.T):
+        _, mg = parity.frame_margins(moved_tr.verts[t], moved_tr.faces, moved_tr.frame_draws(t))
+        assert np.all(mg >= 2e-6)
+        changed = np.nonzero(moved_tr.frame_draws(t)[:, 0] != tr.frame_draws(t)[:, 0])[0]
+        _, mg0 = parity.frame_margins(tr.verts[t], tr.faces, tr.frame_draws(t))
+        np.testing.assert_array_equal(changed, np.nonzero(mg0 < 2e-6)[0])
+
+
 def test_zero_area_faces_never_picked():
     tr = W.flat_square(9, 5000, seed=12)
     v = tr.verts[0].copy()

@@ -66,7 +66,7 @@ def test_parameter_gradient_through_the_library_matches_the_oracle(mode):
                       draws=draws, targets=Y.cpu().numpy().reshape(-1, 3),
                       n_off=np.arange(cl.T + 1, dtype=np.int64) * n,
                       m_off=np.arange(cl.T + 1, dtype=np.int64) * Y.shape[1])
-    tr, _ = parity.nudge_draws(tr)
+    tr = parity.nudged(tr)
     d = torch.from_numpy(tr.draws.reshape(cl.T, n, 3)).to(dev)
     total, lf = loss_traj(verts, cl.faces, d, Y, mode=mode)
     (g_lib,) = torch.autograd.grad(total, s)

@@ -4,8 +4,6 @@ that forbids allocator calls after start-up). It runs on the library's built-in 
 array; here it is checked, through the C ABI, against dc_loss_traj with a workspace, on two
 calls in a row (the scratch keeps the previous call's contents). This file sorts last so
 that a failure here comes after every other test has run."""
-import ctypes
-
 import numpy as np
 import pytest
 import torch
@@ -14,8 +12,6 @@ import parity
 import workloads as W
 
 pytestmark = pytest.mark.gpu
-
-NOALLOC_SCRATCH_BYTES = 16 << 20  # the built-in scratch of dc_loss_traj_noalloc
 
 
 def _dev():
@@ -32,42 +28,39 @@ def _inputs(dev, tr):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_noalloc_matches_workspace_entry_point_twice(mode):
+    """Two calls in a row per case, the larger problem first, so that the smaller one runs on
+    scratch still holding the larger one's data; then the smaller one again with other draws
+    and targets and a frame of weight 0. Each result equals dc_loss_traj's on a workspace of
+    its own."""
     from paper_2204_03139_gb300 import _lib
 
     dev = _dev()
-    cases = [W.single_frame(), W.trajectory_50x50(T=3, n=4000, m=3000)]
-    for tr in cases:
+    big = W.trajectory_50x50(T=3, n=4000, m=3000)
+    small = W.single_frame()
+    other = W.lift_trajectory(5, 25, 2, 2048, 2048, name="other")
+    cases = [(big, None), (small, None), (other, [0.0, 1.0]), (big, [1.0, 0.0, 2.0])]
+    for tr, w in cases:
         v, f, d, y = _inputs(dev, tr)
-        ref = _lib.dc_loss_traj(v, f, d, y, mode=mode, check=True)
+        fw = None if w is None else torch.tensor(w, dtype=torch.float32, device=dev)
+        fresh = torch.empty(_lib.dc_workspace_size(tr.T, tr.V, tr.F, tr.n(0), tr.m(0)),
+                            dtype=torch.uint8, device=dev)
+        ref = _lib.dc_loss_traj(v, f, d, y, mode=mode, frame_w=fw, check=True,
+                                out={"ws": fresh})
         for _ in range(2):  # two calls in a row on the shared scratch
-            got = _lib.dc_loss_traj_noalloc(v, f, d, y, mode=mode, check=True)
+            got = _lib.dc_loss_traj_noalloc(v, f, d, y, mode=mode, frame_w=fw, check=True)
             torch.cuda.synchronize()
-            parity.check_loss(got["loss_frames"].cpu().numpy(), ref["loss_frames"].cpu().numpy())
+            np.testing.assert_array_equal(got["loss_frames"].cpu().numpy(),
+                                          ref["loss_frames"].cpu().numpy())
             parity.check_loss(got["loss_total"].cpu().numpy(), ref["loss_total"].cpu().numpy())
             parity.check_grad(got["grad_verts"].cpu().numpy(), ref["grad_verts"].cpu().numpy())
             np.testing.assert_array_equal(got["nn_ab"].cpu().numpy(), ref["nn_ab"].cpu().numpy())
             if mode == 0:
                 np.testing.assert_array_equal(got["nn_ba"].cpu().numpy(),
                                               ref["nn_ba"].cpu().numpy())
-
-
-def test_noalloc_rejects_problems_beyond_its_scratch():
-    from paper_2204_03139_gb300 import _lib
-
-    _dev()
-    L = _lib.lib()
-    # The pointers below are not device memory: the call must fail on the size check before
-    # any launch. So the problem is sized on the host first, well beyond the scratch, and the
-    # test refuses to make the call if it is not.
-    T, V, F, N, M = 16, 2500, 4802, 10000, 10000
-    while _lib.dc_workspace_size(T, V, F, N, M) <= 4 * NOALLOC_SCRATCH_BYTES:
-        T *= 2
-    assert _lib.dc_workspace_size(T, V, F, N, M) > 4 * NOALLOC_SCRATCH_BYTES
-    fake = ctypes.c_void_p(0x100000)
-    rc = L.dc_loss_traj_noalloc(fake, fake, None, fake, fake, T, V, F, N, M, 0,
-                                None, None, fake, None, None, None, None, None)
-    assert rc == _lib.DC_ENOSPC
-    assert "built-in scratch" in _lib.last_error()
+            if w is not None:
+                dead = [t for t in range(tr.T) if w[t] == 0.0]
+                assert np.all(got["loss_frames"].cpu().numpy()[dead] == 0.0)
+                assert np.all(got["grad_verts"].cpu().numpy()[dead] == 0.0)
 
 
 def test_noalloc_reports_device_errors_in_status():
