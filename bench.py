@@ -1,15 +1,18 @@
 """Throughput of the DiffCloud loss + vertex gradient on GB300.
 
-One step = one dc_loss_traj call with the gradient (area CDF, sampling, fused bidirectional
-Chamfer, neighbour recovery, loss, adjoint scatter) over the 40-frame 50x50 cloth trajectory
-(10 000 samples against 10 000 target points per frame, 4.0e9 point pairs). The metric is
-point pairs per second (one pair = one (sim point, target point) distance of Eq. 1).
+One step (the default workload, batched_uneven) = the loss and every vertex gradient of 64
+cloth trajectories of uneven sizes (grids 15x15 to 80x80, 20 to 100 frames, 2 000 to 30 000
+target points per frame): area CDFs, sampling, one persistent nearest-neighbour launch over
+all frames, neighbour recovery, losses and the adjoint scatter, planned once at the
+autotuned shape and replayed from a CUDA graph. The metric is point pairs per second (one
+pair = one (sim point, target point) distance of Eq. 1). `--workload trajectory_50x50`
+times one dc_loss_traj call over the 40-frame 50x50 trajectory instead.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 
-N > 1 runs under torchrun, one independent trajectory per GPU (weak scaling, no collective
-on the data path). `--impl reference` times the FP64 CPU oracle on a bounded sample of the
-same workload.
+N > 1 runs under torchrun, one independent copy of the workload per GPU (weak scaling, no
+collective on the data path). `--impl reference` times the FP64 CPU oracle on bounded
+samples of the same workload.
 """
 from __future__ import annotations
 
@@ -30,11 +33,15 @@ import workloads  # noqa: E402
 
 FLOP_PER_PAIR = 8        # 3 sub + 3 mul/fma products + 2 adds per distance, shared by both directions
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_chamfer launch on the default workload
-# (trajectory_50x50, 40 frames) in each mode, from the one-pass ncu captures summarised in
-# profiles/k_chamfer_trajectory_50x50.md (nothing is written to DRAM); None for other workloads.
-CHAMFER_TRAFFIC_BYTES = {("trajectory_50x50", "eq1"): 22.79e6,
-                         ("trajectory_50x50", "eq2"): 19.57e6}
+# mma.sync m16n8k16 f16 -> f32 throughput of the GB300, measured with independent MMA chains
+# on every SM (TFLOP/s): the ceiling of the legacy warp-level tensor path
+MMA_SYNC_TFLOPS = 600.0
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the nearest-neighbour kernel,
+# keyed by (workload, kernel, mode), from one-pass ncu captures of one launch:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:<kernel>
+#       -c 1 python bench.py --workload <workload> --steps 1 --warmup 1 --no-cpu-baseline
+CHAMFER_TRAFFIC_BYTES = {("trajectory_50x50", "k_chamfer<true>", "eq1"): 22.79e6,
+                         ("trajectory_50x50", "k_chamfer<false>", "eq2"): 19.57e6}
 
 
 def parse():
@@ -43,11 +50,13 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--workload", default="trajectory_50x50",
+    p.add_argument("--workload", default="batched_uneven",
                    choices=["trajectory_50x50", "trajectory_100x100", "single_frame",
                             "batched_uneven", "serving"])
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="batched_uneven: skip the 40-frame trajectory line kept beside it")
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--mode", default="eq1", choices=["eq1", "eq2"],
                    help="eq1: Eq. 1 bidirectional mean (default); eq2: Eq. 2 unidirectional sum")
@@ -218,33 +227,61 @@ def cpu_baseline(tr, seconds, mode=0):
                       f"vertex gradient, FP64 with float32 neighbour decisions, {el:.1f} s"}
 
 
+def batched_config(trajs, args, world):
+    """The batched workload's config, the same for the GB300 arm and the reference arm."""
+    return {"workload": f"batched_uneven_{len(trajs)}traj", "trajectories": len(trajs),
+            "frames": sum(t.T for t in trajs), "pairs_per_step": sum(t.pairs() for t in trajs),
+            "mode": "Eq. 2 unidirectional sum, fwd + vertex grad"
+            if args.mode == "eq2" else "Eq. 1 bidirectional mean, fwd + vertex grad",
+            "parallelism": f"{world} independent batches" if world > 1 else "1 GPU",
+            "seed": workloads.SEED_BASE + 3}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
 
     oracle.build()
-    tr = make_workload(args.workload, args.frames)
     mode = oracle.UNIDIR_SUM if args.mode == "eq2" else oracle.BIDIR_MEAN
+    if args.workload == "batched_uneven":
+        trajs = make_workload("batched_uneven")
+        # the frames of the fixed 8-trajectory subset, in order, one per step
+        frames = [(tr, t) for tr in batch_cpu_subset(trajs) for t in range(tr.T)]
+        tr0 = frames[0][0]
+        config = batched_config(trajs, args, world)
+    else:
+        tr0 = make_workload(args.workload, args.frames)
+        frames = [(tr0, t) for t in range(tr0.T)]
+        config = arm_config(tr0, args, world)
     # size each step so that warmup + steps take about two minutes
     per_step = max(0.02, min(1.0, 120.0 / max(1, args.steps + args.warmup)))
-    n_s, _ = calibrate_oracle(tr, per_step, mode)
+    n_s, _ = calibrate_oracle(tr0, per_step, mode)
+
+    def step(k):
+        tr, t = frames[k % len(frames)]
+        n = min(n_s, tr.n(t), tr.m(t))
+        oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t)[:n], tr.frame_targets(t)[:n],
+                     mode=mode, details=False)
+        return n * n
+
     for k in range(args.warmup):
-        oracle_sample_step(tr, k, n_s, mode)
+        step(k)
     t0 = time.perf_counter()
     pairs = 0
     for k in range(args.steps):
-        pairs += oracle_sample_step(tr, k, n_s, mode)
+        pairs += step(args.warmup + k)
     el = time.perf_counter() - t0
     value = pairs / el
     cores = oracle.num_threads()
-    sample = (f"each step: one frame of {tr.name} cut to its first {n_s} draws and {n_s} "
-              f"targets (full frame: {tr.n(0)} x {tr.m(0)})")
+    sample = (f"each step: one frame of the workload (in order"
+              f"{', over the trajectories 0, 8, ..., 56 of the batch' if args.workload == 'batched_uneven' else ''}"
+              f") cut to its first {n_s} draws and {n_s} targets (fewer if the frame has fewer)")
     line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s", "value": value, "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": arm_config(tr, args, world),
+            "config": config,
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": sample, "cpu_model": cpu_model()},
             "note": "the FP64 oracle on the host cores; each step is a bounded sample of the "
@@ -417,11 +454,15 @@ def run_gpu(args, rank, world, dist):
     peak_tflops = 2 * FP32_LANES_PER_SM * sms * sm_mhz * 1e6 / 1e12 if sm_mhz else None
     chamfer_avg_s = chamfer_ms / max(1, chamfer_n) / 1e3
     achieved = FLOP_PER_PAIR * pairs / chamfer_avg_s / 1e12 if chamfer_n else None
+    engine = _lib.tune_get()[1]
+    tc_fits = max(N, M) <= 524288
+    kernel = ("k_tcpass" if engine != _lib.ENGINE_DIRECT and tc_fits else
+              ("k_chamfer<true>" if mode == _lib.BIDIR_MEAN else "k_chamfer<false>"))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": (achieved / peak_tflops) if (achieved and peak_tflops) else None,
-            "traffic": (CHAMFER_TRAFFIC_BYTES.get((args.workload, args.mode))
+            "traffic": (CHAMFER_TRAFFIC_BYTES.get((args.workload, kernel, args.mode))
                         if args.frames is None else None),
-            "kernel": "k_chamfer<true>" if mode == _lib.BIDIR_MEAN else "k_chamfer<false>",
+            "kernel": kernel,
             "peak_basis": f"FP32 FMA peak 2 x {FP32_LANES_PER_SM} lanes x {sms} SMs x median "
                           f"SM clock under load ({sm_mhz:.0f} MHz); at the {sm_max:.0f} MHz "
                           f"maximum it is "
@@ -456,12 +497,48 @@ def run_gpu(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def batch_cpu_subset(trajs):
+    """The fixed subset of the batch that the CPU baseline times: every eighth trajectory
+    (8 of 64), whole, in order."""
+    return trajs[::8]
+
+
+def batch_cpu_baseline(trajs, seconds_cap=60.0):
+    """The FP64 oracle over whole frames of the fixed 8-trajectory subset (stops early, at a
+    frame boundary, if it passes seconds_cap)."""
+    import oracle
+
+    sub = batch_cpu_subset(trajs)
+    t0 = time.perf_counter()
+    pairs, frames, done = 0, 0, 0
+    for tr in sub:
+        for t in range(tr.T):
+            oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t), tr.frame_targets(t),
+                         details=False)
+            pairs += tr.n(t) * tr.m(t)
+            frames += 1
+            if time.perf_counter() - t0 > seconds_cap:
+                break
+        else:
+            done += 1
+            continue
+        break
+    el = time.perf_counter() - t0
+    return {"value": pairs / el, "unit": "pairs/s", "cores": oracle.num_threads(),
+            "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"subset of the batch: trajectories 0, 8, ..., 56 ({len(sub)} of "
+                      f"{len(trajs)}); {frames} whole frames ({done} whole trajectories), "
+                      f"{pairs:.3e} pairs, loss + vertex gradient, FP64 with float32 neighbour "
+                      f"decisions, {el:.1f} s"}
+
+
 def run_batched(args, rank, world, dist):
-    """64 trajectories of uneven sizes: the batched form (one planned launch sequence replayed
-    from a CUDA graph) against the plain per-frame form (one dc_loss_traj call per frame)."""
+    """64 trajectories of uneven sizes (the headline): the batched form (one planned launch
+    sequence at the autotuned shape, replayed from a CUDA graph) against the plain per-frame
+    form (one dc_loss_traj call per frame)."""
     import torch
 
-    from paper_2204_03139_gb300 import _lib
+    from paper_2204_03139_gb300 import _lib, autotune
     from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory, per_frame_loss
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -473,7 +550,11 @@ def run_batched(args, rank, world, dist):
     pairs = sum(t.pairs() for t in trajs)
     frames = sum(t.T for t in trajs)
     dts = [DeviceTrajectory.from_host(t, dev) for t in trajs]
-    b = BatchedLoss(dts, grad=True, graph=True)
+    mode = _lib.UNIDIR_SUM if args.mode == "eq2" else _lib.BIDIR_MEAN
+    # the autotuner times every shape on this batch and plans with the fastest
+    tuning = autotune.tune_batch(dts, mode=mode, grad=True, reps=2, save=False)
+    shape = tuning["best"]
+    b = BatchedLoss(dts, mode=mode, grad=True, graph=True, shape=shape)
     b.run(check=True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     clocks = ClockSampler(local)
@@ -496,12 +577,14 @@ def run_batched(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
+    _lib.check_ws(b.ws)
     # graph replays launch nothing from the host: count and time the Chamfer kernel on the
-    # same launch sequence issued eagerly
+    # same launch sequence issued eagerly on the batch's stream
     launches0 = _lib.launch_count()
     _lib.prof_start(3)
-    for _ in range(3):
-        b._launch()
+    with torch.cuda.stream(b.stream):
+        for _ in range(3):
+            b._launch()
     torch.cuda.synchronize()
     chamfer_ms, chamfer_n = _lib.prof_stop()
     launches = (_lib.launch_count() - launches0) // 3 * steps
@@ -509,14 +592,15 @@ def run_batched(args, rank, world, dist):
 
     per = [a.elapsed_time(c) for a, c in ev]
     ms = max_over_ranks(statistics.mean(per), dist)
-    # the plain per-frame form on the same inputs
-    per_frame_loss(dts)
-    torch.cuda.synchronize()
-    pf_steps = 2
-    t0 = time.perf_counter()
-    for _ in range(pf_steps):
-        per_frame_loss(dts)
-    torch.cuda.synchronize()
+    # the plain per-frame form on the same inputs, at the same shape
+    with autotune.tuned(shape):
+        per_frame_loss(dts, mode=mode)
+        torch.cuda.synchronize()
+        pf_steps = 2
+        t0 = time.perf_counter()
+        for _ in range(pf_steps):
+            per_frame_loss(dts, mode=mode)
+        torch.cuda.synchronize()
     pf_ms = 1e3 * (time.perf_counter() - t0) / pf_steps
     # end to end: the batch's inputs from pinned host memory each step, gradients back
     host = [(torch.from_numpy(t.verts).pin_memory(), torch.from_numpy(t.draws).pin_memory(),
@@ -542,27 +626,100 @@ def run_batched(args, rank, world, dist):
         return
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk.get("sm_mhz") or 0.0
-    peak = 2 * FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6 / 1e12 if sm_mhz else None
+    sm_max = clk.get("sm_max_mhz") or 0.0
+    peak = (2 * FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6 / 1e12
+            if sm_mhz else None)
     ck = chamfer_ms / max(1, chamfer_n) / 1e3
     ach = FLOP_PER_PAIR * pairs / ck / 1e12 if chamfer_n else None
+    tc = shape[0] == "tensor"
+    kernel = "k_tcpass" if tc else ("k_chamfer<true>" if mode == _lib.BIDIR_MEAN
+                                    else "k_chamfer<false>")
+    traffic = CHAMFER_TRAFFIC_BYTES.get(("batched_uneven", kernel, args.mode))
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if (ach and peak) else None,
+            "traffic": traffic if not args.batch_trajectories else None,
+            "kernel": kernel, "kernel_ms": ck * 1e3,
+            "pairs_per_s_kernel": pairs / ck if chamfer_n else None,
+            "accounting": "8 flop per unique (sim point, target) pair, the distance shared by "
+                          "both directions, against the FP32 CUDA-core FMA peak 2 x "
+                          f"{FP32_LANES_PER_SM} lanes x {props.multi_processor_count} SMs x "
+                          f"median SM clock under load ({sm_mhz:.0f} MHz; {sm_max:.0f} MHz max)"}
+    if tc:
+        # the pass evaluates each pair once per direction on the tensor cores: one m16n8k16
+        # MMA (4096 flop) per 128 pairs, in both directions for Eq. 1
+        dirs = 2 if mode == _lib.BIDIR_MEAN else 1
+        mma_tflops = dirs * 32.0 * pairs / ck / 1e12 if chamfer_n else None
+        roof["note"] = ("the nearest-neighbour pass runs on the tensor cores (split-fp16 "
+                        "expanded form, exact direct-form re-check of the candidates), so the "
+                        "8-flop FP32 accounting can exceed the CUDA-core peak; the tensor "
+                        "view is below")
+        roof["tensor"] = {"achieved": mma_tflops, "unit": "TFLOP/s (f16 MMA, 32 flop per pair "
+                          "per direction)", "peak_mma_sync_measured": MMA_SYNC_TFLOPS,
+                          "frac_of_mma_sync": (mma_tflops / MMA_SYNC_TFLOPS) if mma_tflops else None}
     line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s", "value": world * pairs / (ms / 1e3),
             "unit": "pairs/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched_uneven_{len(trajs)}traj", "trajectories": len(trajs),
-                       "frames": frames, "pairs_per_step": pairs,
+            "config": {**batched_config(trajs, args, world),
                        "form": "one planned launch sequence replayed from a CUDA graph",
+                       "shape": {"engine": shape[0], "warps_per_cta": shape[1],
+                                 "tuned_ms": {f"{k[0]}:{k[1]}": v
+                                              for k, v in tuning["ms"].items()}},
                        "l2": "flushed between timed steps (256 MiB write outside the step events)"},
             "comparison": {"plain_per_frame_ms_per_step": pf_ms,
                            "plain_per_frame_pairs_per_s": pairs / (pf_ms / 1e3),
                            "batched_over_plain": pf_ms / ms},
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                         "frac": ach / peak if (ach and peak) else None, "traffic": None,
-                         "kernel": "k_chamfer<true>", "kernel_ms": ck * 1e3},
+            "traj_loss_grad_per_s": world * len(trajs) * 1e3 / ms,
+            "roofline": roof,
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": world * pairs / statistics.mean(e2e), "unit": "pairs/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * statistics.mean(e2e),
+                    "api": "BatchedLoss.run (CUDA graph) with every trajectory's verts, draws "
+                           "and targets copied in from pinned host memory and every gradient "
+                           "and the total copied out each step"}}
+    if not args.no_extra:
+        line["trajectory_50x50"] = quick_trajectory_line(args, dev, mode)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(trajs)
     print(json.dumps(line), flush=True)
+
+
+def quick_trajectory_line(args, dev, mode):
+    """The 40-frame 50x50 trajectory (one dc_loss_traj with the gradient per step), a short
+    run kept beside the batched headline."""
+    import torch
+
+    from paper_2204_03139_gb300 import _lib
+
+    tr = make_workload("trajectory_50x50")
+    T, V, F, N, M = tr.T, tr.V, tr.F, tr.n(0), tr.m(0)
+    v = torch.from_numpy(tr.verts).to(dev)
+    f = torch.from_numpy(tr.faces).to(dev)
+    d = torch.from_numpy(np.ascontiguousarray(tr.draws_tn3())).to(dev)
+    y = torch.from_numpy(np.ascontiguousarray(tr.targets_tm3())).to(dev)
+    out = {"ws": torch.empty(_lib.dc_workspace_size(T, V, F, N, M), dtype=torch.uint8,
+                             device=dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(5):
+        _lib.dc_loss_traj(v, f, d, y, mode=mode, out=out)
+    torch.cuda.synchronize()
+    steps = 50
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    _lib.prof_start(steps)
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record()
+        _lib.dc_loss_traj(v, f, d, y, mode=mode, out=out)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    kms, kn = _lib.prof_stop()
+    _lib.check_ws(out["ws"])
+    ms = statistics.mean(a.elapsed_time(c) for a, c in ev)
+    return {"workload": tr.name, "ms_per_step": ms, "pairs_per_s": tr.pairs() / (ms / 1e3),
+            "chamfer_kernel_ms": kms / max(kn, 1),
+            "chamfer_pairs_per_s": tr.pairs() / (kms / max(kn, 1) / 1e3)}
 
 
 def run_serving(args, rank, world, dist):

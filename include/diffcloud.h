@@ -206,17 +206,26 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
 int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
 
 /*
- * Tuning of the Chamfer kernel's tile shape. A CTA of w warps (w = 1, 2 or 4) holds
- * w * 512 sim points in registers while target chunks stream through it: wide CTAs amortise
- * the target staging and the column merges over more points, narrow ones split small
- * problems into enough work items to fill the GPU. warps_per_cta = 0 (the default) picks two
- * warps when that gives every resident CTA several work items, else one (two measured as fast
- * as four on uniform trajectories and faster on uneven batches). dc_tune_set sets the
- * width for every later call in the process (an autotuner times the widths per problem size
- * and sets the winner before its calls); batch plans keep the width they were planned with.
+ * Tuning of the nearest-neighbour search. Two engines compute the same neighbours and losses
+ * (the float32 direct form, lowest index among equal distances):
+ *   DC_ENGINE_TENSOR -- a tensor-core filter: the expanded form |p|^2 - 2 p.q + |q|^2 on
+ *     split-fp16 operands (one MMA per 16 x 8 pairs) keeps, per point, the three best blocks
+ *     of 128 candidates, and the direct form re-checks only the blocks that a proven error
+ *     bound cannot exclude (all candidates when it cannot certify two). Frames of at most
+ *     524 288 points per side. The default (DC_ENGINE_AUTO) wherever it applies.
+ *   DC_ENGINE_DIRECT -- every pair in the direct form on the CUDA cores; a CTA of w warps
+ *     (w = 1, 2 or 4) holds w * 512 sim points in registers while target chunks stream
+ *     through it. warps_per_cta = 0 picks two warps when that gives every resident CTA
+ *     several work items, else one.
+ * dc_tune_set sets both for every later call and plan in the process (an autotuner times
+ * them per problem size and sets the winner before its calls); batch plans keep the choice
+ * they were planned with.
  */
+enum { DC_ENGINE_AUTO = 0, DC_ENGINE_DIRECT = 1, DC_ENGINE_TENSOR = 2 };
+
 typedef struct dc_tune {
-    int32_t warps_per_cta; /* 0: automatic, else 1, 2 or 4 */
+    int32_t warps_per_cta; /* direct engine: 0 (automatic), 1, 2 or 4 */
+    int32_t engine;        /* DC_ENGINE_AUTO, DC_ENGINE_DIRECT or DC_ENGINE_TENSOR */
 } dc_tune;
 
 int dc_tune_set(const dc_tune* tune); /* NULL restores automatic */

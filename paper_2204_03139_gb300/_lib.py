@@ -31,8 +31,11 @@ class DCError(RuntimeError):
         self.code = code
 
 
+ENGINE_AUTO, ENGINE_DIRECT, ENGINE_TENSOR = 0, 1, 2
+
+
 class dc_tune(ctypes.Structure):
-    _fields_ = [("warps_per_cta", ctypes.c_int32)]
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("engine", ctypes.c_int32)]
 
 
 class dc_frame(ctypes.Structure):
@@ -402,16 +405,18 @@ def dc_loss_traj_noalloc(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=
     return {"loss_total": lt, "loss_frames": lf, "grad_verts": gv, "nn_ab": nab, "nn_ba": nba}
 
 
-def tune_set(warps_per_cta: int = 0):
-    """Chamfer CTA width (1, 2 or 4 warps; 0: automatic) for every later call."""
-    t = dc_tune(int(warps_per_cta))
+def tune_set(warps_per_cta: int = 0, engine: int = ENGINE_AUTO):
+    """Nearest-neighbour engine (ENGINE_AUTO, ENGINE_DIRECT or ENGINE_TENSOR) and the direct
+    engine's CTA width (1, 2 or 4 warps; 0: automatic) for every later call and plan."""
+    t = dc_tune(int(warps_per_cta), int(engine))
     _check(lib().dc_tune_set(ctypes.byref(t)))
 
 
-def tune_get() -> int:
-    t = dc_tune(0)
+def tune_get() -> tuple[int, int]:
+    """(warps_per_cta, engine) currently set."""
+    t = dc_tune(0, 0)
     _check(lib().dc_tune_get(ctypes.byref(t)))
-    return int(t.warps_per_cta)
+    return int(t.warps_per_cta), int(t.engine)
 
 
 def fp32_fma_rate(packed: bool, iters: int = 20000, device=None) -> float:

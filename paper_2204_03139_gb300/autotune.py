@@ -1,11 +1,15 @@
-"""Autotuner of the Chamfer kernel's tile shape.
+"""Autotuner of the nearest-neighbour search's engine and tile shape.
 
-The tile shape is the number of warps per Chamfer CTA (1, 2 or 4; each warp holds 512 sim
-points). The best width depends on the problem size: wide CTAs amortise the target staging
-and the column merges, narrow ones split small problems into enough work items. tune() times
-every width on the caller's own inputs and records the fastest per size bucket in a JSON cache
-(path from DC_AUTOTUNE_CACHE, default ~/.cache/diffcloud/autotune.json); best() looks a
-bucket up; tuned() sets the width around a block of calls.
+The shapes it chooses between:
+  ("tensor", 0)  the tensor-core filter (frames of at most 524 288 points per side);
+  ("direct", w)  the CUDA-core direct form with CTAs of w = 1, 2 or 4 warps (w x 512 sim
+                 points held in registers; wide CTAs amortise the target staging and the
+                 column merges, narrow ones split small problems into enough work items).
+tune() times every shape on the caller's own inputs and records the fastest per size bucket
+in a JSON cache (path from DC_AUTOTUNE_CACHE, default ~/.cache/diffcloud/autotune.json);
+best() looks a bucket up; tuned() sets a shape around a block of calls (and of batch plans,
+which keep the shape they were planned with); tune_batch() does the same for a list of
+trajectories planned as one batch.
 """
 from __future__ import annotations
 
@@ -19,6 +23,7 @@ import torch
 
 from . import _lib
 
+SHAPES = (("tensor", 0), ("direct", 1), ("direct", 2), ("direct", 4))
 WIDTHS = (1, 2, 4)
 _lock = threading.Lock()
 _cache: dict | None = None
@@ -50,64 +55,123 @@ def _save():
     os.replace(tmp, path)
 
 
+def _lg(x) -> int:
+    return int(math.floor(math.log2(max(1, x))))
+
+
 def bucket(T: int, N: int, M: int, mode: int, device=None) -> str:
     """Size bucket: device, mode, and powers of two of frames, sim points and targets."""
     name = torch.cuda.get_device_name(device)
-    lg = lambda x: int(math.floor(math.log2(max(1, x))))  # noqa: E731
-    return f"{name}|m{mode}|T{lg(T)}|N{lg(N)}|M{lg(M)}"
+    return f"{name}|m{mode}|T{_lg(T)}|N{_lg(N)}|M{_lg(M)}"
 
 
-def best(T: int, N: int, M: int, mode: int = _lib.BIDIR_MEAN, device=None) -> int | None:
+def batch_bucket(trajs, mode: int, device=None) -> str:
+    """Size bucket of a batch: frames, mean points per side and total pairs (powers of two)."""
+    frames = sum(t.T for t in trajs)
+    n = sum(int(t.n_off[-1]) for t in trajs) / max(frames, 1)
+    m = sum(int(t.m_off[-1]) for t in trajs) / max(frames, 1)
+    pairs = sum(t.pairs() for t in trajs)
+    name = torch.cuda.get_device_name(device)
+    return f"{name}|batch|m{mode}|F{_lg(frames)}|N{_lg(n)}|M{_lg(m)}|P{_lg(pairs)}"
+
+
+def _norm(shape):
+    """A shape as (engine name, warps); an int w means ("direct", w)."""
+    if shape is None:
+        return None
+    if isinstance(shape, int):
+        return ("direct", shape)
+    e, w = shape
+    return (str(e), int(w))
+
+
+def best(T: int, N: int, M: int, mode: int = _lib.BIDIR_MEAN, device=None):
     with _lock:
-        return _load().get(bucket(T, N, M, mode, device))
+        s = _load().get(bucket(T, N, M, mode, device))
+    return None if s is None else _norm(s)
 
 
 @contextlib.contextmanager
-def tuned(warps: int | None):
-    """Use CTA width `warps` (None: leave the current setting) for the calls in the block."""
-    if warps is None:
+def tuned(shape):
+    """Use `shape` (("tensor", 0), ("direct", w), or an int w for the direct engine; None
+    leaves the current setting) for the calls and plans in the block."""
+    shape = _norm(shape)
+    if shape is None:
         yield
         return
     old = _lib.tune_get()
-    _lib.tune_set(warps)
+    eng = _lib.ENGINE_TENSOR if shape[0] == "tensor" else _lib.ENGINE_DIRECT
+    _lib.tune_set(shape[1] if shape[0] == "direct" else 0, eng)
     try:
         yield
     finally:
-        _lib.tune_set(old)
+        _lib.tune_set(*old)
+
+
+def _time(fn, dev, reps: int) -> float:
+    fn()  # warm-up
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / reps
 
 
 def tune(verts, faces, draws, targets, mode: int = _lib.BIDIR_MEAN, reps: int = 3,
-         save: bool = True) -> dict:
-    """Time dc_loss_traj (forward + gradient) at every width on these inputs; record and
-    return {"best": w, "ms": {w: ms}}."""
+         save: bool = True, shapes=SHAPES) -> dict:
+    """Time dc_loss_traj (forward + gradient) at every shape on these inputs; record and
+    return {"best": shape, "ms": {shape: ms}}."""
     dev = verts.device
     T, N, M = verts.shape[0], draws.shape[1], targets.shape[1]
     times = {}
-    for w in WIDTHS:
-        with tuned(w):
-            _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode)  # warm-up
-            torch.cuda.synchronize(dev)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(reps):
-                _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode)
-            b.record()
-            torch.cuda.synchronize(dev)
-            times[w] = a.elapsed_time(b) / reps
-    w_best = min(times, key=times.get)
+    for sh in shapes:
+        with tuned(sh):
+            times[sh] = _time(lambda: _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode),
+                              dev, reps)
+    s_best = min(times, key=times.get)
     with _lock:
-        _load()[bucket(T, N, M, mode, dev)] = w_best
+        _load()[bucket(T, N, M, mode, dev)] = list(s_best)
         if save:
             _save()
-    return {"best": w_best, "ms": times}
+    return {"best": s_best, "ms": times}
+
+
+def tune_batch(trajs, mode: int = _lib.BIDIR_MEAN, weights=None, grad: bool = True,
+               reps: int = 2, save: bool = True, shapes=SHAPES) -> dict:
+    """Plan the batch of DeviceTrajectory objects at every shape, time its run, record the
+    fastest for the batch's size bucket and return {"best": shape, "ms": {shape: ms}}."""
+    from .batch import BatchedLoss
+
+    dev = trajs[0].verts.device
+    times = {}
+    for sh in shapes:
+        with tuned(sh):
+            b = BatchedLoss(trajs, mode=mode, weights=weights, grad=grad)
+        times[sh] = _time(b.run, dev, reps)
+        del b
+    s_best = min(times, key=times.get)
+    with _lock:
+        _load()[batch_bucket(trajs, mode, dev)] = list(s_best)
+        if save:
+            _save()
+    return {"best": s_best, "ms": times}
+
+
+def best_batch(trajs, mode: int = _lib.BIDIR_MEAN, device=None):
+    with _lock:
+        s = _load().get(batch_bucket(trajs, mode, device))
+    return None if s is None else _norm(s)
 
 
 def loss_traj(verts, faces, draws, targets, mode: int = _lib.BIDIR_MEAN, **kw):
-    """dc_loss_traj at the tuned width of its size bucket (tuning the bucket first if it has
+    """dc_loss_traj at the tuned shape of its size bucket (tuning the bucket first if it has
     no entry yet)."""
     T, N, M = verts.shape[0], draws.shape[1], targets.shape[1]
-    w = best(T, N, M, mode, verts.device)
-    if w is None:
-        w = tune(verts, faces, draws, targets, mode)["best"]
-    with tuned(w):
+    s = best(T, N, M, mode, verts.device)
+    if s is None:
+        s = tune(verts, faces, draws, targets, mode)["best"]
+    with tuned(s):
         return _lib.dc_loss_traj(verts, faces, draws, targets, mode=mode, **kw)

@@ -73,16 +73,27 @@ class BatchedLoss:
     """
 
     def __init__(self, trajs, mode=_lib.BIDIR_MEAN, weights=None, grad=True, graph=False,
-                 nn=False, stream=None):
+                 nn=False, stream=None, tune=False, shape=None):
+        """tune=True: plan with the shape the autotuner found fastest for this batch's size
+        bucket (timing every shape first if the bucket has no entry); shape: plan with this
+        shape (autotune.SHAPES); otherwise the library's default."""
+        from . import autotune
+
         self.trajs = list(trajs)
         self.mode = mode
         dev = self.trajs[0].verts.device
         self.device = dev
         # the stream the plan is uploaded on and the batch runs on (default: current stream)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        if tune and shape is None:
+            shape = autotune.best_batch(self.trajs, mode, dev)
+            if shape is None:
+                shape = autotune.tune_batch(self.trajs, mode=mode, weights=weights,
+                                            grad=grad)["best"]
+        self.shape = shape
         # outputs and workspace belong to the batch's stream (the caching allocator reuses
-        # memory per stream)
-        with torch.cuda.stream(self.stream):
+        # memory per stream); the plan keeps the shape it was made with
+        with torch.cuda.stream(self.stream), autotune.tuned(shape):
             self._build(mode, weights, grad, nn)
         if graph:
             self._capture()

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdiffcloud.so")
-SOURCES = ["sample.cu", "chamfer.cu", "epilogue.cu", "api.cu", "peak.cu"]
+SOURCES = ["sample.cu", "chamfer.cu", "tcpass.cu", "epilogue.cu", "api.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--ftz=false", "--prec-div=true", "--prec-sqrt=true", "--fmad=true"]

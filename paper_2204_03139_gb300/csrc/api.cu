@@ -65,6 +65,18 @@ Layout make_layout(const Sizes& s) {
     L.loss = take(s.n_frames * 4);
     L.part = take(s.n_frames * s.slices * 2 * 4);
     L.frame_err = take(s.n_frames * 4);
+    L.fbox = take(s.n_frames * 16);
+    const long long tcp = s.tc_units > 0 ? s.rows + s.cols : 0;  // points with forms
+    L.tc_ufr = take(s.tc_units * 4);
+    L.tc_urb = take(s.tc_units * 4);
+    L.tc_upre = take(s.tc_units > 0 ? (s.tc_units + 1) * 4 : 0);
+    L.tca = take(tcp * 32);
+    L.tcb = take(tcp * 32);
+    L.kab = take(s.tc_units > 0 ? s.rows * TC_KEYS * 4 : 0);
+    L.kba = take(s.tc_units > 0 ? s.cols * TC_KEYS * 4 : 0);
+    L.kpart = take(s.tc_units > 0 ? s.tc_slots * 2 * TC_UNIT_ROWS * TC_KEYS * 4 : 0);
+    L.tcfb = take(tcp * 4);
+    L.tcfn = take(s.tc_units > 0 ? s.n_frames * 8 : 0);
     L.total = off;
     return L;
 }
@@ -91,6 +103,17 @@ Ws make_ws(void* base, const Layout& L) {
     w.loss = reinterpret_cast<float*>(p + L.loss);
     w.part = reinterpret_cast<float*>(p + L.part);
     w.frame_err = reinterpret_cast<int*>(p + L.frame_err);
+    w.fbox = reinterpret_cast<float4*>(p + L.fbox);
+    w.tc_ufr = reinterpret_cast<int*>(p + L.tc_ufr);
+    w.tc_urb = reinterpret_cast<int*>(p + L.tc_urb);
+    w.tc_upre = reinterpret_cast<int*>(p + L.tc_upre);
+    w.tca = reinterpret_cast<uint4*>(p + L.tca);
+    w.tcb = reinterpret_cast<uint4*>(p + L.tcb);
+    w.kab = reinterpret_cast<unsigned*>(p + L.kab);
+    w.kba = reinterpret_cast<unsigned*>(p + L.kba);
+    w.kpart = reinterpret_cast<unsigned*>(p + L.kpart);
+    w.tcfb = reinterpret_cast<int*>(p + L.tcfb);
+    w.tcfn = reinterpret_cast<int*>(p + L.tcfn);
     return w;
 }
 
@@ -117,7 +140,8 @@ constexpr long long INT_LIMIT = 0x7fffffffLL;
 // Sizes of a uniform trajectory; false if any derived count overflows int32. The unit
 // arrays are sized for the narrowest CTA (the most units); sub[w] is the Chamfer work
 // (sub-chunks) at CTA width 1, 2 and 4 (indices 0, 1, 2).
-bool uniform_sizes(int T, int V, int F, int N, int M, Sizes& s, long long sub[3], int& spu) {
+bool uniform_sizes(int T, int V, int F, int N, int M, Sizes& s, long long sub[3], int& spu,
+                   bool with_tc = true) {
     const long long Npad = (long long)div_up(N, ROW_PAD) * ROW_PAD;
     const long long Mpad = M > 0 ? (long long)div_up(M, COL_PAD) * COL_PAD : 0;
     spu = M > 0 ? div_up(M, SUB) : 0;
@@ -129,9 +153,19 @@ bool uniform_sizes(int T, int V, int F, int N, int M, Sizes& s, long long sub[3]
     s.rows = (long long)T * Npad;
     s.cols = (long long)T * Mpad;
     s.slices = epilogue_slices(T);
+    // tensor-core regions, sized for both sides (the mode is not known here), when the frame
+    // fits the key format; none for calls without targets
+    s.tc_units = s.tc_slots = 0;
+    if (with_tc && M > 0 && Npad <= TC_MAX_COLS && Mpad <= TC_MAX_COLS) {
+        const long long u0 = div_up(N, TC_UNIT_ROWS), u1 = div_up(M, TC_UNIT_ROWS);
+        s.tc_units = (long long)T * (u0 + u1);
+        const long long chunks = (long long)T * (u0 * (Mpad / TC_CHUNK) + u1 * (Npad / TC_CHUNK));
+        if (chunks >= INT_LIMIT) return false;
+        s.tc_slots = tc_grid(chunks);  // the pass's CTAs (partial-key slots are per CTA)
+    }
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
            sub[0] < INT_LIMIT && s.rows * 3 < INT_LIMIT * 16 && s.cols * 6 < INT_LIMIT * 16 &&
-           3LL * V < INT_LIMIT;
+           3LL * V < INT_LIMIT && (s.rows + s.cols) * 2 < INT_LIMIT;
 }
 
 enum : unsigned {
@@ -149,14 +183,27 @@ int check_ws(void* ws, size_t ws_bytes, size_t need) {
     return DC_OK;
 }
 
+int g_engine = ENGINE_AUTO;  // process-wide engine set by dc_tune_set
+
+// The Chamfer engine of a call: the tensor-core filter when the problem fits its key format
+// (the default), else, or when the direct engine is requested, the CUDA-core direct form.
+int choose_engine(bool tc_fits) {
+    if (g_engine == ENGINE_DIRECT) return ENGINE_DIRECT;
+    return tc_fits ? ENGINE_TC : ENGINE_DIRECT;
+}
+
 int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total, void* ws,
-                size_t ws_bytes, cudaStream_t st) {
+                size_t ws_bytes, cudaStream_t st, bool direct_only = false) {
     Sizes sz;
     long long sub[3];
     int spu = 0;
-    if (!uniform_sizes(a.T, a.V, a.F, a.N, a.M, sz, sub, spu))
+    if (!uniform_sizes(a.T, a.V, a.F, a.N, a.M, sz, sub, spu, !direct_only))
         return fail(DC_EINVAL, "problem too large for 32-bit offsets");
-    const int warps = (phases & PH_CHAMFER) ? choose_warps(a.mode, sub[2], sub[1], sub[0]) : 1;
+    const bool chamfer = (phases & PH_CHAMFER) != 0;
+    const int engine = chamfer && !direct_only ? choose_engine(sz.tc_units > 0) : ENGINE_DIRECT;
+    const int warps =
+        (chamfer && engine == ENGINE_DIRECT) ? choose_warps(a.mode, sub[2], sub[1], sub[0]) : 1;
+    a.engine = engine;
     a.warps = warps;
     a.units_per_frame = div_up(a.N, ROWS_PER_WARP * warps);
     a.subs_per_unit = spu;
@@ -166,20 +213,37 @@ int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total
     if (rc) return rc;
     const Ws w = make_ws(ws, L);
     const int T = a.T, rows = (int)sz.rows, cols = (int)sz.cols;
-    // with sampling to follow, the tables and the area CDFs share one launch
+    const bool tc = chamfer && engine == ENGINE_TC;
+    // with sampling to follow, the tables and the area CDFs (and the frame boxes of the
+    // tensor-core forms) share one launch
     const bool fused = (phases & PH_AREA) && (phases & PH_SAMPLE);
     cudaError_t e = fused ? launch_build_area(a, w, st) : launch_build_uniform(a, w, st);
     if (!e && (phases & PH_AREA) && !fused) e = launch_area_cdf(w, T, st);
+    if (!e && tc && !fused) e = launch_bbox(w, T, st);
     if (!e && (phases & (PH_SAMPLE | PH_TARGETS)))
         e = launch_stage(w, T, (int)sz.slices, a.pts ? 0 : a.F, (phases & PH_SAMPLE) ? rows : 0,
-                         (phases & PH_TARGETS) ? cols : 0, fused ? 1 : 0, st);
-    if (!e && (phases & PH_CHAMFER)) {
-        const long long units = (long long)T * a.units_per_frame;
-        e = launch_chamfer(w, (int)units, (int)(units * spu), a.mode, warps, st);
+                         (phases & PH_TARGETS) ? cols : 0, fused ? 1 : 0, tc ? 1 : 0, st);
+    int grid = 0;
+    if (!e && chamfer) {
+        if (tc) {
+            const long long Npad = (long long)div_up(a.N, ROW_PAD) * ROW_PAD;
+            const long long Mpad = (long long)div_up(a.M, COL_PAD) * COL_PAD;
+            const long long u1 = a.mode == DC_BIDIR_MEAN ? div_up(a.M, TC_UNIT_ROWS) : 0;
+            const long long chunks =
+                (long long)T * (div_up(a.N, TC_UNIT_ROWS) * (Mpad / TC_CHUNK) + u1 * (Npad / TC_CHUNK));
+            grid = tc_grid(chunks);
+            const int units =
+                T * (div_up(a.N, TC_UNIT_ROWS) +
+                     (a.mode == DC_BIDIR_MEAN ? div_up(a.M, TC_UNIT_ROWS) : 0));
+            e = launch_tcpass(w, grid, chunks, units, rows, cols, a.mode, T, st);
+        } else {
+            const long long units = (long long)T * a.units_per_frame;
+            e = launch_chamfer(w, (int)units, (int)(units * spu), a.mode, warps, st);
+        }
     }
     if (!e && epi_flags)
         e = launch_epilogue(w, T, (int)sz.slices, a.grad ? a.V : 0, a.mode, epi_flags,
-                            loss_total, st);
+                            loss_total, tc ? grid : 0, st);
     if (e) return cuda_fail(e, "kernel launch");
     return DC_OK;
 }
@@ -198,10 +262,57 @@ int check_ptrs(std::initializer_list<const void*> ps, const char* what) {
     return DC_OK;
 }
 
+// dc_loss_traj; direct_only runs the direct engine on a workspace laid out without the
+// tensor-core regions (the smaller footprint of the built-in scratch of the no-allocation
+// entry point)
+int loss_traj_impl(const float* verts, const int32_t* faces, const uint8_t* face_mask,
+                   const float* draws, const float* targets, int T, int V, int F, int N, int M,
+                   int mode, const float* frame_w, float* loss_total, float* loss_frames,
+                   float* grad_verts, int32_t* nn_ab, int32_t* nn_ba, void* ws,
+                   size_t ws_bytes, dc_stream_t stream, bool direct_only) {
+    int rc = check_common(T, N, M, mode);
+    if (rc) return rc;
+    if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
+    rc = check_ptrs({verts, faces, draws, targets, loss_frames}, "dc_loss_traj");
+    if (rc) return rc;
+    UniformArgs a{};
+    a.verts = verts;
+    a.faces = faces;
+    a.mask = face_mask;
+    a.draws = draws;
+    a.tgt = targets;
+    a.loss = loss_frames;
+    a.nn_ab = nn_ab;
+    a.nn_ba = mode == DC_BIDIR_MEAN ? nn_ba : nullptr;
+    a.grad = grad_verts;
+    a.weight = frame_w;
+    a.T = T;
+    a.V = V;
+    a.F = F;
+    a.N = N;
+    a.M = M;
+    a.mode = mode;
+    const unsigned ph = PH_AREA | PH_SAMPLE | PH_TARGETS | PH_CHAMFER;
+    const int epi = EPI_RESCAN | EPI_LOSS | (grad_verts ? EPI_GRAD : 0);
+    return run_uniform(a, ph, epi, loss_total, ws, ws_bytes, static_cast<cudaStream_t>(stream),
+                       direct_only);
+}
+
+// bytes of a uniform workspace laid out for the direct engine only
+size_t direct_workspace_size(int T, int V, int F, int N, int M) {
+    if (T <= 0 || V <= 0 || F <= 0 || N <= 0 || M < 0) return 0;
+    Sizes sz;
+    long long sub[3];
+    int spu;
+    if (!uniform_sizes(T, V, F, N, M, sz, sub, spu, false)) return 0;
+    return make_layout(sz).total;
+}
+
 // ---- batch plans (host copy of what dc_batch_run needs to launch) ----
 struct Plan {
     Sizes sz;
-    int mode, any_grad, max_v, max_f, total_sub, n_units, warps;
+    int mode, any_grad, max_v, max_f, total_sub, n_units, warps, engine, tc_grid, tc_units;
+    long long tc_chunks;
     size_t bytes;
 };
 std::mutex g_plan_mu;
@@ -252,15 +363,24 @@ int dc_prof_stop(float* total_ms, int* launches) {
 
 int dc_tune_set(const dc_tune* tune) {
     const int w = tune ? tune->warps_per_cta : 0;
+    const int en = tune ? tune->engine : DC_ENGINE_AUTO;
     if (w != 0 && w != 1 && w != 2 && w != 4)
         return fail(DC_EINVAL, "warps_per_cta must be 0 (automatic), 1, 2 or 4");
+    if (en != DC_ENGINE_AUTO && en != DC_ENGINE_DIRECT && en != DC_ENGINE_TENSOR)
+        return fail(DC_EINVAL, "engine must be DC_ENGINE_AUTO, DC_ENGINE_DIRECT or "
+                               "DC_ENGINE_TENSOR");
     set_tuned_warps(w);
+    g_engine = en == DC_ENGINE_DIRECT ? ENGINE_DIRECT : (en == DC_ENGINE_TENSOR ? ENGINE_TC
+                                                                                : ENGINE_AUTO);
     return DC_OK;
 }
 
 int dc_tune_get(dc_tune* tune) {
     if (!tune) return fail(DC_EINVAL, "tune is NULL");
     tune->warps_per_cta = tuned_warps();
+    tune->engine = g_engine == ENGINE_DIRECT ? DC_ENGINE_DIRECT
+                                             : (g_engine == ENGINE_TC ? DC_ENGINE_TENSOR
+                                                                      : DC_ENGINE_AUTO);
     return DC_OK;
 }
 
@@ -379,31 +499,9 @@ int dc_loss_traj(const float* verts, const int32_t* faces, const uint8_t* face_m
                  const float* frame_w, float* loss_total, float* loss_frames, float* grad_verts,
                  int32_t* nn_ab, int32_t* nn_ba, void* ws, size_t ws_bytes,
                  dc_stream_t stream) {
-    int rc = check_common(T, N, M, mode);
-    if (rc) return rc;
-    if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
-    rc = check_ptrs({verts, faces, draws, targets, loss_frames}, "dc_loss_traj");
-    if (rc) return rc;
-    UniformArgs a{};
-    a.verts = verts;
-    a.faces = faces;
-    a.mask = face_mask;
-    a.draws = draws;
-    a.tgt = targets;
-    a.loss = loss_frames;
-    a.nn_ab = nn_ab;
-    a.nn_ba = mode == DC_BIDIR_MEAN ? nn_ba : nullptr;
-    a.grad = grad_verts;
-    a.weight = frame_w;
-    a.T = T;
-    a.V = V;
-    a.F = F;
-    a.N = N;
-    a.M = M;
-    a.mode = mode;
-    const unsigned ph = PH_AREA | PH_SAMPLE | PH_TARGETS | PH_CHAMFER;
-    const int epi = EPI_RESCAN | EPI_LOSS | (grad_verts ? EPI_GRAD : 0);
-    return run_uniform(a, ph, epi, loss_total, ws, ws_bytes, stream);
+    return loss_traj_impl(verts, faces, face_mask, draws, targets, T, V, F, N, M, mode, frame_w,
+                          loss_total, loss_frames, grad_verts, nn_ab, nn_ba, ws, ws_bytes,
+                          stream, false);
 }
 
 int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* face_mask,
@@ -447,21 +545,32 @@ int dc_loss_traj_bwd(const float* verts, const int32_t* faces, const uint8_t* fa
 // batches
 // ---------------------------------------------------------------------------------------
 static bool batch_sizes(const dc_frame* fr, int n, Sizes& s, long long sub[3]) {
-    s = Sizes{n, 0, 0, 0, 0, epilogue_slices(n)};
+    s = Sizes{n, 0, 0, 0, 0, epilogue_slices(n), 0, 0};
     sub[0] = sub[1] = sub[2] = 0;
-    long long max_v = 0;
+    long long max_v = 0, tc_units = 0, tc_chunks = 0;
+    bool tc_fits = true;
     for (int k = 0; k < n; ++k) {
         const long long spu = div_up(fr[k].M, SUB);
         s.n_units += div_up(fr[k].N, ROWS_PER_WARP);
         for (int i = 0; i < 3; ++i) sub[i] += (long long)div_up(fr[k].N, ROWS_PER_WARP << i) * spu;
         s.sum_f += fr[k].F;
-        s.rows += (long long)div_up(fr[k].N, ROW_PAD) * ROW_PAD;
-        s.cols += (long long)div_up(fr[k].M, COL_PAD) * COL_PAD;
+        const long long Npad = (long long)div_up(fr[k].N, ROW_PAD) * ROW_PAD;
+        const long long Mpad = (long long)div_up(fr[k].M, COL_PAD) * COL_PAD;
+        s.rows += Npad;
+        s.cols += Mpad;
         if (fr[k].grad_verts && fr[k].V > max_v) max_v = fr[k].V;
+        tc_fits = tc_fits && Npad <= TC_MAX_COLS && Mpad <= TC_MAX_COLS;
+        const long long u0 = div_up(fr[k].N, TC_UNIT_ROWS), u1 = div_up(fr[k].M, TC_UNIT_ROWS);
+        tc_units += u0 + u1;
+        tc_chunks += u0 * (Mpad / TC_CHUNK) + u1 * (Npad / TC_CHUNK);
+    }
+    if (tc_fits && tc_chunks < INT_LIMIT) {
+        s.tc_units = tc_units;
+        s.tc_slots = tc_grid(tc_chunks);
     }
     return s.rows < INT_LIMIT && s.cols < INT_LIMIT && s.sum_f < INT_LIMIT &&
            sub[0] < INT_LIMIT && s.n_units < INT_LIMIT && s.cols * 6 < INT_LIMIT * 16 &&
-           3 * max_v < INT_LIMIT;
+           3 * max_v < INT_LIMIT && tc_chunks < INT_LIMIT && (s.rows + s.cols) * 2 < INT_LIMIT;
 }
 
 size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames) {
@@ -493,7 +602,8 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     long long sub[3];
     if (!batch_sizes(frames, n_frames, sz, sub))
         return fail(DC_EINVAL, "batch too large for 32-bit offsets");
-    const int warps = choose_warps(mode, sub[2], sub[1], sub[0]);
+    const int engine = choose_engine(sz.tc_units > 0);
+    const int warps = engine == ENGINE_DIRECT ? choose_warps(mode, sub[2], sub[1], sub[0]) : 1;
     const Layout L = make_layout(sz);
     int rc = check_ws(ws, ws_bytes, L.total);
     if (rc) return rc;
@@ -508,6 +618,13 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     int* ufr = reinterpret_cast<int*>(img.data() + L.unit_frame);
     int* urb = reinterpret_cast<int*>(img.data() + L.unit_rb);
     int* upre = reinterpret_cast<int*>(img.data() + L.unit_pre);
+    // the tensor-core unit tables follow in the workspace; they get a host image of their own
+    const size_t tc_beg = L.tc_ufr, tc_end = L.tca;
+    std::vector<char> tcimg(engine == ENGINE_TC ? tc_end - tc_beg : 0, 0);
+    int* tufr = reinterpret_cast<int*>(tcimg.data() + (L.tc_ufr - tc_beg));
+    int* turb = reinterpret_cast<int*>(tcimg.data() + (L.tc_urb - tc_beg));
+    int* tupre = reinterpret_cast<int*>(tcimg.data() + (L.tc_upre - tc_beg));
+    int tunit = 0, tchunk = 0;
     int row0 = 0, col0 = 0, cdf0 = 0, unit = 0, subc = 0, any_grad = 0, max_v = 0, max_f = 0;
     // The table lists the frames largest first (N + M, ties in the caller's order). The
     // sampling and epilogue kernels run one CTA per (frame, slice) in table order, so the
@@ -543,7 +660,20 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
         d.col0 = col0;
         d.cdf0 = cdf0;
         d.unit0 = unit;
+        d.tc_unit0 = tunit;
         fd[k] = d;
+        if (engine == ENGINE_TC) {
+            // sim rows against the targets, then (Eq. 1) the targets against the sim points
+            const int u0 = div_up(f.N, TC_UNIT_ROWS);
+            const int u1 = mode == DC_BIDIR_MEAN ? div_up(f.M, TC_UNIT_ROWS) : 0;
+            for (int r = 0; r < u0 + u1; ++r, ++tunit) {
+                const int side = r >= u0 ? 1 : 0, rb = side ? r - u0 : r;
+                tufr[tunit] = k;
+                turb[tunit] = (side << 30) | rb;
+                tupre[tunit] = tchunk;
+                if (!d.skip) tchunk += (side ? d.Npad : d.Mpad) / TC_CHUNK;
+            }
+        }
         rowpre[k] = row0;
         colpre[k] = col0;
         const int upf = div_up(f.N, ROWS_PER_WARP * warps);
@@ -566,6 +696,7 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     rowpre[n_frames] = row0;
     colpre[n_frames] = col0;
     upre[unit] = subc;
+    if (engine == ENGINE_TC) tupre[tunit] = tchunk;
     h->status = DC_OK;
     h->n_frames = n_frames;
     h->n_units = unit;
@@ -579,7 +710,14 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     h->max_v = max_v;
     h->slices = (int)sz.slices;
     h->warps = warps;
+    h->engine = engine;
+    h->tc_units = engine == ENGINE_TC ? tunit : 0;
+    h->tc_total = engine == ENGINE_TC ? tchunk : 0;
+    h->tc_fallback = 0;
     cudaError_t e = cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, stream);
+    if (!e && !tcimg.empty())
+        e = cudaMemcpyAsync(static_cast<char*>(ws) + tc_beg, tcimg.data(), tcimg.size(),
+                            cudaMemcpyHostToDevice, stream);
     if (!e) e = cudaStreamSynchronize(stream);
     if (e) return cuda_fail(e, "dc_batch_plan copy");
     Plan p;
@@ -591,6 +729,10 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     p.total_sub = subc;
     p.n_units = unit;
     p.warps = warps;
+    p.engine = engine;
+    p.tc_grid = engine == ENGINE_TC ? tc_grid(tchunk) : 0;
+    p.tc_units = engine == ENGINE_TC ? tunit : 0;
+    p.tc_chunks = tchunk;
     p.bytes = L.total;
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_plans[ws] = p;
@@ -608,14 +750,18 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
     const Layout L = make_layout(p.sz);
     const Ws w = make_ws(ws, L);
     const int n = (int)p.sz.n_frames, rows = (int)p.sz.rows, cols = (int)p.sz.cols;
+    const bool tc = p.engine == ENGINE_TC;
     cudaError_t e = launch_reset(w, stream);
-    if (!e) e = launch_area_cdf(w, n, stream);
-    if (!e) e = launch_stage(w, n, (int)p.sz.slices, p.max_f, rows, cols, 0, stream);
-    if (!e) e = launch_chamfer(w, p.n_units, p.total_sub, p.mode, p.warps, stream);
+    if (!e) e = launch_area_cdf(w, n, stream);  // and the frame boxes
+    if (!e) e = launch_stage(w, n, (int)p.sz.slices, p.max_f, rows, cols, 0, tc ? 1 : 0, stream);
+    if (!e)
+        e = tc ? launch_tcpass(w, p.tc_grid, p.tc_chunks, p.tc_units, rows, cols, p.mode, n,
+                               stream)
+               : launch_chamfer(w, p.n_units, p.total_sub, p.mode, p.warps, stream);
     if (!e)
         e = launch_epilogue(w, n, (int)p.sz.slices, p.any_grad ? p.max_v : 0, p.mode,
                             EPI_RESCAN | EPI_LOSS | (p.any_grad ? EPI_GRAD : 0), loss_total,
-                            stream);
+                            tc ? p.tc_grid : 0, stream);
     if (e) return cuda_fail(e, "dc_batch_run");
     return DC_OK;
 }
@@ -651,7 +797,8 @@ extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
     if (V <= 0 || F <= 0) return fail(DC_EINVAL, "V and F must be positive");
     // the size check comes first: a problem that does not fit is refused before any pointer
     // is looked at or any CUDA call is made
-    const size_t need = dc_workspace_size(T, V, F, N, M);
+    // the built-in scratch runs the direct engine, whose layout has no tensor-core regions
+    const size_t need = direct_workspace_size(T, V, F, N, M);
     if (need == 0) return fail(DC_EINVAL, "problem too large for 32-bit offsets");
     if (need > DC_NOALLOC_SCRATCH_BYTES)
         return fail(DC_ENOSPC,
@@ -687,9 +834,9 @@ extern "C" int dc_loss_traj_noalloc(const float* verts, const int32_t* faces,
     }
     // Every region of the scratch that a call reads is written earlier in the same call (the
     // status word included), so nothing needs clearing between calls.
-    rc = dc_loss_traj(verts, faces, face_mask, draws, targets, T, V, F, N, M, mode, frame_w,
-                      loss_total, loss_frames, grad_verts, nn_ab, nn_ba, ws,
-                      DC_NOALLOC_SCRATCH_BYTES, stream);
+    rc = loss_traj_impl(verts, faces, face_mask, draws, targets, T, V, F, N, M, mode, frame_w,
+                        loss_total, loss_frames, grad_verts, nn_ab, nn_ba, ws,
+                        DC_NOALLOC_SCRATCH_BYTES, stream, true);
     if (rc) return rc;
     if (status) {
         e = cudaMemcpyAsync(status, &static_cast<const WsHeader*>(ws)->status, sizeof(int32_t),

@@ -43,6 +43,53 @@ constexpr int MAX_SLICES = 32;                            // epilogue slices per
 constexpr float COORD_MAX = 1e15f;
 constexpr unsigned long long EMPTY = ~0ull;
 
+// ---------------------------------------------------------------------------------------
+// Tensor-core filter (tcpass.cu). Every point p of a frame is centred on the frame's box
+// centre c and scaled by a power of two sig (|(p - c) sig| < 64 per coordinate), and each
+// scaled coordinate s is split into two halves h = fp16(s), l = fp16(s - h) (22 significant
+// bits). With n = |s|^2 (float32, split the same way), the K = 16 vectors
+//   A(p) = (h0 h0 l0 l0  h1 h1 l1 l1  h2 h2 l2 l2  1  1  nh nl)
+//   B(q) = (-2h0 -2l0 -2h0 -2l0  -2h1 -2l1 -2h1 -2l1  -2h2 -2l2 -2h2 -2l2  nh nl 1 1)
+// give A(p).B(q) = |p - q|^2 sig^2 up to a small bound (the expanded form, used only to
+// select candidates; the reported minimum is recomputed exactly in the direct form). The
+// four quad lanes that share a row each see a quarter of its columns; a lane's minimum over
+// its columns of a block of TC_BLOCK becomes a 32-bit key, (value bits truncated to 20) |
+// block, and every (row, lane) keeps its three smallest keys in a slot of its own.
+// Both forms are stored per group of 8 points as the two 8 x 16-byte halves of K (256 B).
+// ---------------------------------------------------------------------------------------
+constexpr int TC_WARPS = 4;                                 // warps per CTA
+constexpr int TC_ROWS_PER_WARP = 128;                       // eight m16 tiles per warp
+constexpr int TC_UNIT_ROWS = TC_WARPS * TC_ROWS_PER_WARP;   // rows per work unit (512)
+constexpr int TC_CHUNK = 256;                               // columns per staged chunk
+constexpr int TC_BLOCK = 128;                               // columns per key block
+constexpr int TC_MAX_BLOCKS = 4096;                         // block ids a key can hold (12 bits)
+constexpr int TC_MAX_COLS = TC_MAX_BLOCKS * TC_BLOCK;       // 524 288 points per side
+constexpr int TC_MAX_GRID = 1024;                           // partial-key slots sized for it
+constexpr int TC_KEYS = 12;                                 // keys per row: 3 per quad lane
+constexpr unsigned TC_VALUE_MASK = 0xFFFFF000u;             // sign, exponent, 11 mantissa bits
+constexpr unsigned TC_EMPTY = 0xFFFFFFFFu;
+constexpr float TC_PAD_NORM = 60000.0f;                     // norm of a padding column
+constexpr float TC_SCALE_LIMIT = 64.0f;                     // |scaled coordinate| below this
+// Error bound of the filter in units of u = 2^-24, per unit of (|sp| + |sq|)^2: measured
+// on GB300 at most 6.7 over 6.7e7 pairs of cloth-like clouds (accumulation at most 5.4 ulp
+// of the largest product, split residuals below 2^-21 |sp||sq| per coordinate).
+constexpr float TC_KAPPA = 32.0f;
+static_assert(ROW_PAD % TC_UNIT_ROWS == 0 && COL_PAD % TC_CHUNK == 0 &&
+                  TC_CHUNK % TC_BLOCK == 0 && TC_ROWS_PER_WARP % 16 == 0,
+              "the tensor-core tiles nest in the padded sizes");
+
+enum : int { ENGINE_AUTO = 0, ENGINE_DIRECT = 1, ENGINE_TC = 2 };
+
+// (k1, k2, k3) stays the three smallest of the keys inserted
+__device__ __forceinline__ void top3_insert(unsigned& k1, unsigned& k2, unsigned& k3,
+                                            unsigned v) {
+    const unsigned x1 = max(k1, v);
+    k1 = min(k1, v);
+    const unsigned x2 = max(k2, x1);
+    k2 = min(k2, x1);
+    k3 = min(k3, x2);
+}
+
 // Everything a kernel needs to know about one frame. Built on the device for uniform
 // trajectories, on the host for batches.
 struct FrameDesc {
@@ -68,6 +115,7 @@ struct FrameDesc {
     int cdf0;             // offset of this frame's CDF
     int unit0;            // first Chamfer unit of this frame
     int skip;             // weight (or gradient multiplier) 0: no work, L reported as 0
+    int tc_unit0;         // first tensor-core unit of this frame (sim rows, then targets)
 };
 
 // Header at the start of every workspace.
@@ -85,18 +133,25 @@ struct WsHeader {
     int max_v;        // largest V among frames with a gradient
     int slices;       // epilogue slices per frame
     int warps;        // warps per Chamfer CTA (units of warps * ROWS_PER_WARP sim points)
-    int pad[51];
+    int engine;       // ENGINE_DIRECT or ENGINE_TC
+    int tc_units;     // tensor-core work units (frame, side, 512 rows)
+    int tc_total;     // their chunks of TC_CHUNK columns (live frames only)
+    int tc_fallback;  // rows whose keys certified no candidate set (scanned in full)
+    int pad[47];
 };
 
 // Byte offsets of every region of a workspace (computed on the host).
 struct Layout {
     size_t hdr, frames, rowpre, colpre, unit_frame, unit_rb, unit_pre, cdf, x, fw, tsoa, tpl,
-        pab, pba, nnab, nnba, loss, part, frame_err, total;
+        pab, pba, nnab, nnba, loss, part, frame_err, fbox, tc_ufr, tc_urb, tc_upre, tca, tcb,
+        kab, kba, kpart, tcfb, tcfn, total;
 };
 
 struct Sizes {
     long long n_frames, n_units, sum_f, rows, cols;
-    long long slices;  // epilogue slices per frame
+    long long slices;    // epilogue slices per frame
+    long long tc_units;  // tensor-core units (0: no tensor-core regions)
+    long long tc_slots;  // CTAs the partial-key buffer is sized for
 };
 
 // Epilogue slices per frame: as many as keep all (frame, slice) CTAs in one wave, at most
@@ -129,6 +184,18 @@ struct Ws {
     float* loss;       // [n_frames] fallback loss buffer
     int* frame_err;    // [n_frames] error code of the fused build + area launch, per frame
     float* part;       // [n_frames][slices][2] loss partial sums
+    float4* fbox;      // [n_frames] (centre x, y, z, scale) of the tensor-core forms
+    int* tc_ufr;       // [tc_units] frame of each tensor-core unit
+    int* tc_urb;       // [tc_units] side << 30 | row block
+    int* tc_upre;      // [tc_units + 1] prefix of chunk counts
+    uint4* tca;        // [(rows + cols) * 2] A forms (sim points, then targets), 32 B each
+    uint4* tcb;        // [(rows + cols) * 2] B forms
+    unsigned* kab;     // [rows][4 lanes][3] the smallest keys of every sim point
+    unsigned* kba;     // [cols][4][3] the same of every target
+    unsigned* kpart;   // [tc_slots][2][TC_UNIT_ROWS][4][3] keys of units split between CTAs
+    int* tcfb;         // [rows + cols] frame-local indices of the rows the keys did not
+                       // certify, each frame's list at its own row (rows + column) range
+    int* tcfn;         // [n_frames][2] lengths of those lists (zeroed by the staging)
 };
 
 Ws make_ws(void* base, const Layout& L);
@@ -187,6 +254,7 @@ struct UniformArgs {
     const float* gframes;  // [T] nullable (backward only): dJ/dL_t directly
     int bwd;               // 1: gradient multipliers g_t = w_t gtotal + gframes[t]
     int T, V, F, N, M, mode, units_per_frame, subs_per_unit, slices, warps;
+    int engine;            // ENGINE_DIRECT or ENGINE_TC (set when the call has a Chamfer)
 };
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s);
@@ -196,12 +264,23 @@ cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t
 cudaError_t launch_build_area(const UniformArgs& a, const Ws& w, cudaStream_t s);
 cudaError_t launch_reset(const Ws& w, cudaStream_t s);
 cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s);
-cudaError_t launch_sample(const Ws& w, int n_frames, int rows, int fold, cudaStream_t s);
-cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s);
+// tc = 1 also writes the tensor-core forms of the points (the frame boxes must be ready)
+cudaError_t launch_sample(const Ws& w, int n_frames, int rows, int fold, int tc, cudaStream_t s);
+cudaError_t launch_targets(const Ws& w, int n_frames, int cols, int tc, cudaStream_t s);
 // sampling + target staging in one (frame, slice) launch when the largest CDF (max_f
 // floats) fits in shared memory, else launch_sample + launch_targets
 cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
-                         int fold, cudaStream_t s);
+                         int fold, int tc, cudaStream_t s);
+// frame boxes for the tensor-core forms when no area launch computes them (given points)
+cudaError_t launch_bbox(const Ws& w, int n_frames, cudaStream_t s);
+// the tensor-core filter over every unit (both sides in Eq. 1) on `grid` CTAs, then the merge
+// of the keys of units split between CTAs (n_units: the units the call can have), then the
+// exact recovery of every row's minimum and neighbour from its keys into pab (and pba in
+// Eq. 1) as (distance bits << 32 | index)
+cudaError_t launch_tcpass(const Ws& w, int grid, long long total_chunks, int n_units,
+                          int rows, int cols, int mode, int n_frames, cudaStream_t s);
+// CTAs of the tensor-core pass for an upper bound of its chunk count
+int tc_grid(long long total_chunks);
 cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, int warps,
                            cudaStream_t s);
 // resident Chamfer CTAs on the current device for a CTA width (persistent grid size)
@@ -211,11 +290,12 @@ int chamfer_grid(int mode, int warps);
 int choose_warps(int mode, long long sub_w4, long long sub_w2, long long sub_w1);
 void set_tuned_warps(int warps);  // 0: automatic
 void inject_stall();              // the next Chamfer launch never gets its first chunk
+int take_stall();                 // 1 once after inject_stall (read by the Chamfer launchers)
 int tuned_warps();
 // epilogue: neighbour recovery (rescan), loss partials, gradient scatter
 enum : int { EPI_RESCAN = 1, EPI_LOSS = 2, EPI_GRAD = 4 };
 cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, int mode,
-                            int flags, float* total, cudaStream_t s);
+                            int flags, float* total, int tc_grid, cudaStream_t s);
 cudaError_t launch_chamfer_bwd_points(const float* a, const float* b, const int* nn_ab,
                                       const int* nn_ba, int T, int N, int M, int mode,
                                       const float* g, float* grad_a, cudaStream_t s);

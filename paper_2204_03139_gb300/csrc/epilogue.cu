@@ -42,6 +42,7 @@ struct EpiArgs {
     int flags;     // EPI_RESCAN | EPI_LOSS | EPI_GRAD
     int bidir;
     int use_smem;  // one slice per frame and the V x 3 accumulator fits in shared memory
+    int exact;     // the packed minima hold the neighbour's index itself (tensor-core path)
 };
 
 __device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiA
     const float* PZ = PY + fr->Mpad;
     const int i0 = (int)((long long)N * sl / e.slices);
     const int i1 = (int)((long long)N * (sl + 1) / e.slices);
+    const bool exact = e.exact != 0 && rescan;
     float sab = 0.f, cab_c = 0.f;
     for (int base = i0 + warp * 8; base < i1; base += NW * 8) {
         const int i = base + grp;
@@ -122,7 +124,20 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiA
         const float4 x = w.x[g];
         int nn = -1;
         float dmin = 0.f;
-        if (rescan) {
+        if (exact) {
+            // the recovery kernels left (distance bits << 32 | neighbour) for every row
+            const u64 p = valid ? w.pab[g] : EMPTY;
+            if (valid && p != EMPTY) {
+                nn = (int)(p & 0xffffffffu);
+                dmin = __uint_as_float((unsigned)(p >> 32));
+            }
+            if (valid && q == 0) {
+                if (p != EMPTY && want_loss) kahan_add(sab, cab_c, dmin);
+                if (p == EMPTY || (unsigned)nn >= (unsigned)M) set_status(&w.hdr->status, DC_EDEVICE);
+                fr->nn_ab[i] = nn;
+            }
+            if ((unsigned)nn >= (unsigned)M) nn = -1;
+        } else if (rescan) {
             const u64 p = valid ? w.pab[g] : EMPTY;
             int first = 0x7fffffff;
             if (p != EMPTY) {
@@ -194,7 +209,20 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiA
             const float tx = PX[jj], ty = PY[jj], tz = PZ[jj];
             int nn = -1;
             float dmin = 0.f;
-            if (rescan) {
+            if (exact) {
+                const u64 p = valid ? w.pba[col0 + jj] : EMPTY;
+                if (valid && p != EMPTY) {
+                    nn = (int)(p & 0xffffffffu);
+                    dmin = __uint_as_float((unsigned)(p >> 32));
+                }
+                if (valid && q == 0) {
+                    if (p != EMPTY && want_loss) kahan_add(sba, cba_c, dmin);
+                    if (p == EMPTY || (unsigned)nn >= (unsigned)N)
+                        set_status(&w.hdr->status, DC_EDEVICE);
+                    fr->nn_ba[j] = nn;
+                }
+                if ((unsigned)nn >= (unsigned)N) nn = -1;
+            } else if (rescan) {
                 const u64 p = valid ? w.pba[col0 + jj] : EMPTY;
                 int first = 0x7fffffff;
                 if (p != EMPTY) {
@@ -336,7 +364,7 @@ int g_smem_limit[64];
 constexpr int EPI_THREADS_ONE_SLICE = 4 * EPI_THREADS;
 
 cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, int mode,
-                            int flags, float* total, cudaStream_t s) {
+                            int flags, float* total, int tc_grid, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
@@ -354,6 +382,7 @@ cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, in
     a.slices = slices;
     a.flags = flags;
     a.bidir = mode == DC_BIDIR_MEAN;
+    a.exact = tc_grid > 0;
     const bool grad = (flags & EPI_GRAD) && max_v > 0;
     const size_t need = (size_t)max_v * 3 * sizeof(float);
     a.use_smem = grad && slices == 1 && need <= (size_t)g_smem_limit[dev];

@@ -1,4 +1,5 @@
 // Frame tables, area CDF, area-weighted sampling and target staging (Sec. III-B, Eq. 3).
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "dc_internal.cuh"
@@ -40,6 +41,112 @@ __device__ __forceinline__ void frame_scales(const UniformArgs& a, int k, float&
     } else {
         gs = w;
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// tensor-core forms (see dc_internal.cuh): frame box, centre and scale, and the A / B forms
+// ---------------------------------------------------------------------------------------
+// Centre and scale of a frame over its sim-side points P[np] (vertices or given points) and
+// its targets Y[ny]: the centre of their bounding box and the power of two sig with
+// |(p - c) sig| < TC_SCALE_LIMIT. Coordinates that fail the range check are left out (they
+// are reported as DC_EINVAL elsewhere). The whole block (a multiple of 32 threads) calls it.
+__device__ void frame_box(const float* __restrict__ P, int np, const float* __restrict__ Y,
+                          int ny, float4* out) {
+    __shared__ float s_box[32][6];
+    float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int side = 0; side < 2; ++side) {
+        const float* Q = side ? Y : P;
+        const int n = side ? ny : np;
+        if (!Q) continue;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float v = Q[3LL * i + k];
+                if (coord_ok(v)) {
+                    b[k] = fminf(b[k], v);
+                    b[3 + k] = fmaxf(b[3 + k], v);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            b[k] = fminf(b[k], __shfl_xor_sync(0xffffffffu, b[k], o));
+            b[3 + k] = fmaxf(b[3 + k], __shfl_xor_sync(0xffffffffu, b[3 + k], o));
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) s_box[warp][k] = b[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < nw; ++q)
+            for (int k = 0; k < 3; ++k) {
+                b[k] = fminf(b[k], s_box[q][k]);
+                b[3 + k] = fmaxf(b[3 + k], s_box[q][3 + k]);
+            }
+        float c[3], R = 0.0f;
+        for (int k = 0; k < 3; ++k) {
+            c[k] = b[k] <= b[3 + k] ? 0.5f * b[k] + 0.5f * b[3 + k] : 0.0f;
+            if (b[k] <= b[3 + k]) R = fmaxf(R, fmaxf(b[3 + k] - c[k], c[k] - b[k]));
+        }
+        R *= 1.0f + 0x1p-20f;  // covers the rounding of c
+        float sig = 1.0f;
+        if (R > 0.0f && R < 1e30f) {
+            int e = 0;
+            frexpf(R, &e);  // R < 2^e
+            sig = ldexpf(1.0f, 6 - e);  // R sig < 64 = TC_SCALE_LIMIT
+        }
+        *out = make_float4(c[0], c[1], c[2], sig);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned pack_h2(__half lo, __half hi) {
+    return (unsigned)__half_as_ushort(lo) | ((unsigned)__half_as_ushort(hi) << 16);
+}
+
+// The A and B forms of form index p for the point (x, y, z) of a frame with box `box`; a
+// padding point gets forms that never win a minimum (A = 0; B adds TC_PAD_NORM, above any
+// real scaled squared distance, 4 * 3 * 64^2).
+__device__ __forceinline__ void write_forms(const Ws& w, long long p, float x, float y, float z,
+                                            float4 box, bool real) {
+    uint4 a0, a1, b0, b1;
+    const __half one = __float2half_rn(1.0f);
+    if (real) {
+        const float sc[3] = {__fmul_rn(__fsub_rn(x, box.x), box.w),
+                             __fmul_rn(__fsub_rn(y, box.y), box.w),
+                             __fmul_rn(__fsub_rn(z, box.z), box.w)};
+        __half h[3], l[3], H[3], L[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            h[k] = __float2half_rn(sc[k]);
+            l[k] = __float2half_rn(__fsub_rn(sc[k], __half2float(h[k])));
+            H[k] = __float2half_rn(-2.0f * __half2float(h[k]));  // exact
+            L[k] = __float2half_rn(-2.0f * __half2float(l[k]));
+        }
+        const float n = __fmaf_rn(sc[2], sc[2], __fmaf_rn(sc[1], sc[1], __fmul_rn(sc[0], sc[0])));
+        const __half nh = __float2half_rn(n), nl = __float2half_rn(__fsub_rn(n, __half2float(nh)));
+        a0 = make_uint4(pack_h2(h[0], h[0]), pack_h2(l[0], l[0]), pack_h2(h[1], h[1]),
+                        pack_h2(l[1], l[1]));
+        a1 = make_uint4(pack_h2(h[2], h[2]), pack_h2(l[2], l[2]), pack_h2(one, one),
+                        pack_h2(nh, nl));
+        b0 = make_uint4(pack_h2(H[0], L[0]), pack_h2(H[0], L[0]), pack_h2(H[1], L[1]),
+                        pack_h2(H[1], L[1]));
+        b1 = make_uint4(pack_h2(H[2], L[2]), pack_h2(H[2], L[2]), pack_h2(nh, nl),
+                        pack_h2(one, one));
+    } else {
+        const __half zero = __float2half_rn(0.0f), pad = __float2half_rn(TC_PAD_NORM);
+        a0 = a1 = b0 = make_uint4(0u, 0u, 0u, 0u);
+        b1 = make_uint4(0u, 0u, pack_h2(pad, zero), pack_h2(one, one));
+    }
+    // group of 8 points = 16 uint4: K 0..7 of the 8 points, then K 8..15
+    const long long q = (p >> 3) * 16 + (p & 7);
+    w.tca[q] = a0;
+    w.tca[q + 8] = a1;
+    w.tcb[q] = b0;
+    w.tcb[q + 8] = b1;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -126,6 +233,10 @@ __device__ void build_uniform(const UniformArgs& a, const Ws& w) {
         h->max_v = a.V;
         h->slices = a.slices;
         h->warps = a.warps;
+        h->engine = a.engine == ENGINE_TC ? ENGINE_TC : ENGINE_DIRECT;
+        h->tc_units = 0;
+        h->tc_total = 0;
+        h->tc_fallback = 0;
     }
     __syncthreads();  // the frames' live counts are written
     // units: a skipped frame's units carry no sub-chunks
@@ -140,9 +251,39 @@ __device__ void build_uniform(const UniformArgs& a, const Ws& w) {
         w.unit_rb[u] = rb;
         w.unit_pre[u] = (f->unit0 * upf + (f->skip ? 0 : rb)) * spu;
     }
+    // tensor-core units: per frame the sim rows (side 0) against the targets, then in Eq. 1
+    // the targets (side 1) against the sim points; a skipped frame's units carry no chunks
+    const int tu0 = div_up(a.N, TC_UNIT_ROWS);
+    const int tu1 = a.mode == DC_BIDIR_MEAN ? div_up(a.M, TC_UNIT_ROWS) : 0;
+    const int tupf = tu0 + tu1;
+    if (a.engine == ENGINE_TC) {
+        const int c0 = Mpad / TC_CHUNK, c1 = Npad / TC_CHUNK;  // chunks per unit, by side
+        const int per_frame = tu0 * c0 + tu1 * c1;
+        const int n_tc = a.T * tupf;
+        for (int u = tid; u <= n_tc; u += nt) {
+            if (u == n_tc) {
+                w.tc_upre[u] = s_carry * per_frame;
+                continue;
+            }
+            const int k = u / tupf, r = u - k * tupf;
+            const int side = r >= tu0 ? 1 : 0, rb = side ? r - tu0 : r;
+            const FrameDesc* f = w.frames + k;
+            w.tc_ufr[u] = k;
+            w.tc_urb[u] = (side << 30) | rb;
+            w.tc_upre[u] = f->unit0 * per_frame +
+                           (f->skip ? 0 : (side ? tu0 * c0 + rb * c1 : rb * c0));
+        }
+        if (tid == 0) {
+            w.hdr->tc_units = n_tc;
+            w.hdr->tc_total = s_carry * per_frame;
+        }
+    }
     // unit0 now holds "live frames before"; restore its documented meaning
     __syncthreads();
-    for (int k = tid; k < a.T; k += nt) w.frames[k].unit0 = k * upf;
+    for (int k = tid; k < a.T; k += nt) {
+        w.frames[k].unit0 = k * upf;
+        w.frames[k].tc_unit0 = k * tupf;
+    }
 }
 
 __global__ void __launch_bounds__(BUILD_THREADS) k_build_uniform(UniformArgs a, Ws w) {
@@ -303,6 +444,8 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
     const AreaFrame af{fr->verts, fr->faces, fr->mask, fr->grad, w.cdf + fr->cdf0,
                        fr->F, fr->V, fr->skip != 0};
     area_cdf(af, &w.hdr->status);
+    if (w.hdr->engine == ENGINE_TC && !fr->skip)
+        frame_box(fr->verts, fr->V, fr->tgt, fr->M, &w.fbox[blockIdx.x]);
 }
 
 // Uniform trajectory: block 0 builds the tables (as k_build_uniform) while block 1 + t
@@ -327,6 +470,17 @@ __global__ void __launch_bounds__(CDF_THREADS) k_build_area(UniformArgs a, Ws w)
     area_cdf(af, &s_err);
     __syncthreads();
     if (threadIdx.x == 0) w.frame_err[t] = s_err;
+    if (a.engine == ENGINE_TC && !af.skip)
+        frame_box(af.verts, a.V, a.tgt ? a.tgt + 3LL * t * a.M : nullptr, a.M, &w.fbox[t]);
+}
+
+// frame boxes of frames given as points (no area launch)
+__global__ void __launch_bounds__(512) k_bbox(Ws w) {
+    pdl_entry();
+    const FrameDesc* fr = w.frames + blockIdx.x;
+    if (fr->skip) return;
+    frame_box(fr->pts ? fr->pts : fr->verts, fr->pts ? fr->N : fr->V, fr->tgt, fr->M,
+              &w.fbox[blockIdx.x]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -334,7 +488,7 @@ __global__ void __launch_bounds__(CDF_THREADS) k_build_area(UniformArgs a, Ws w)
 // ---------------------------------------------------------------------------------------
 // Row g (frame-local index i) of frame fr, with the frame's CDF at `cdf` (global or shared).
 __device__ __forceinline__ void sample_row(const Ws& w, const FrameDesc* fr, int i, int g,
-                                           const float* cdf) {
+                                           const float* cdf, bool tc, float4 box) {
     float4 x = make_float4(ROW_SENTINEL, ROW_SENTINEL, ROW_SENTINEL, 0.0f);
     int4 q = make_int4(-1, 0, 0, 0);
     if (i < fr->N) {
@@ -395,11 +549,13 @@ __device__ __forceinline__ void sample_row(const Ws& w, const FrameDesc* fr, int
     w.x[g] = x;
     w.fw[g] = q;
     w.pab[g] = EMPTY;
+    if (tc) write_forms(w, g, x.x, x.y, x.z, box, i < fr->N);
 }
 
 // Target j (frame-local) of frame fr at padded column g: the negated duplicated planes the
 // Chamfer kernel stages, the compact planes the epilogue re-scans, and the column minimum.
-__device__ __forceinline__ void stage_target(const Ws& w, const FrameDesc* fr, int j, int g) {
+__device__ __forceinline__ void stage_target(const Ws& w, const FrameDesc* fr, int j, int g,
+                                             bool tc, float4 box) {
     float vx = COL_SENTINEL, vy = COL_SENTINEL, vz = COL_SENTINEL;
     const bool real = j < fr->M;
     if (real) {
@@ -421,6 +577,7 @@ __device__ __forceinline__ void stage_target(const Ws& w, const FrameDesc* fr, i
     Q[fr->Mpad + j] = real ? vy : 0.0f;
     Q[2 * fr->Mpad + j] = real ? vz : 0.0f;
     w.pba[g] = EMPTY;
+    if (tc) write_forms(w, (long long)w.hdr->total_rows + g, vx, vy, vz, box, real);
 }
 
 // the area errors that a fused build + area launch left for frame k
@@ -429,22 +586,30 @@ __device__ __forceinline__ void fold_area_err(const Ws& w, int k) {
     if (code != DC_OK) set_status(&w.hdr->status, code);
 }
 
-__global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows, int fold) {
+__global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows, int fold, int tc) {
     pdl_entry();
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.rowpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
         if (fold && g == fr->row0) fold_area_err(w, k);
-        if (!fr->skip) sample_row(w, fr, g - fr->row0, g, w.cdf + fr->cdf0);
+        if (!fr->skip)
+            sample_row(w, fr, g - fr->row0, g, w.cdf + fr->cdf0, tc != 0,
+                       tc ? w.fbox[k] : make_float4(0.f, 0.f, 0.f, 1.f));
     }
 }
 
-__global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
+__global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols, int tc) {
     pdl_entry();
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < cols; g += gridDim.x * blockDim.x) {
         const int k = last_le(w.colpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
-        if (!fr->skip) stage_target(w, fr, g - fr->col0, g);
+        if (tc && g == fr->col0) {  // the frame's fallback lists start empty
+            w.tcfn[2 * k] = 0;
+            w.tcfn[2 * k + 1] = 0;
+        }
+        if (!fr->skip)
+            stage_target(w, fr, g - fr->col0, g, tc != 0,
+                         tc ? w.fbox[k] : make_float4(0.f, 0.f, 0.f, 1.f));
     }
 }
 
@@ -453,13 +618,18 @@ __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols) {
 constexpr int STAGE_THREADS = 512;
 
 __global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int rows, int cols,
-                                                        int fold) {
+                                                        int fold, int tc) {
     pdl_entry();
     extern __shared__ float s_cdf[];
     const int k = blockIdx.x / slices, sl = blockIdx.x - k * slices;
     const FrameDesc* fr = w.frames + k;
     if (fold && sl == 0 && threadIdx.x == 0) fold_area_err(w, k);
+    if (tc && sl == 0 && threadIdx.x == 0) {  // the frame's fallback lists start empty
+        w.tcfn[2 * k] = 0;
+        w.tcfn[2 * k + 1] = 0;
+    }
     if (fr->skip) return;
+    const float4 box = tc ? w.fbox[k] : make_float4(0.f, 0.f, 0.f, 1.f);
     const bool sampled = fr->verts && !fr->pts;
     if (sampled)
         for (int f = threadIdx.x; f < fr->F; f += STAGE_THREADS) s_cdf[f] = w.cdf[fr->cdf0 + f];
@@ -468,13 +638,13 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int r
         const int a = (int)((long long)fr->Npad * sl / slices);
         const int b = (int)((long long)fr->Npad * (sl + 1) / slices);
         for (int i = a + threadIdx.x; i < b; i += STAGE_THREADS)
-            sample_row(w, fr, i, fr->row0 + i, s_cdf);
+            sample_row(w, fr, i, fr->row0 + i, s_cdf, tc != 0, box);
     }
     if (cols) {
         const int a = (int)((long long)fr->Mpad * sl / slices);
         const int b = (int)((long long)fr->Mpad * (sl + 1) / slices);
         for (int j = a + threadIdx.x; j < b; j += STAGE_THREADS)
-            stage_target(w, fr, j, fr->col0 + j);
+            stage_target(w, fr, j, fr->col0 + j, tc != 0, box);
     }
 }
 
@@ -500,11 +670,18 @@ cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t
 }
 
 cudaError_t launch_reset(const Ws& w, cudaStream_t s) {
-    return cudaMemsetAsync(&w.hdr->status, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(&w.hdr->status, 0, sizeof(int), s);
+    return e ? e : cudaMemsetAsync(&w.hdr->tc_fallback, 0, sizeof(int), s);
 }
 
 cudaError_t launch_build_area(const UniformArgs& a, const Ws& w, cudaStream_t s) {
     cudaError_t e = launch_pdl(k_build_area, a.T + 1, CDF_THREADS, 0, s, a, w);
+    count_launch();
+    return e ? e : cudaGetLastError();
+}
+
+cudaError_t launch_bbox(const Ws& w, int n_frames, cudaStream_t s) {
+    cudaError_t e = launch_pdl(k_bbox, n_frames, 512, 0, s, w);
     count_launch();
     return e ? e : cudaGetLastError();
 }
@@ -515,20 +692,21 @@ cudaError_t launch_area_cdf(const Ws& w, int n_frames, cudaStream_t s) {
     return e ? e : cudaGetLastError();
 }
 
-cudaError_t launch_sample(const Ws& w, int n_frames, int rows, int fold, cudaStream_t s) {
-    cudaError_t e = launch_pdl(k_sample, grid_for(rows, 256), 256, 0, s, w, n_frames, rows, fold);
+cudaError_t launch_sample(const Ws& w, int n_frames, int rows, int fold, int tc, cudaStream_t s) {
+    cudaError_t e =
+        launch_pdl(k_sample, grid_for(rows, 256), 256, 0, s, w, n_frames, rows, fold, tc);
     count_launch();
     return e ? e : cudaGetLastError();
 }
 
-cudaError_t launch_targets(const Ws& w, int n_frames, int cols, cudaStream_t s) {
-    cudaError_t e = launch_pdl(k_targets, grid_for(cols, 256), 256, 0, s, w, n_frames, cols);
+cudaError_t launch_targets(const Ws& w, int n_frames, int cols, int tc, cudaStream_t s) {
+    cudaError_t e = launch_pdl(k_targets, grid_for(cols, 256), 256, 0, s, w, n_frames, cols, tc);
     count_launch();
     return e ? e : cudaGetLastError();
 }
 
 cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int rows, int cols,
-                         int fold, cudaStream_t s) {
+                         int fold, int tc, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
@@ -545,12 +723,12 @@ cudaError_t launch_stage(const Ws& w, int n_frames, int slices, int max_f, int r
     if (need > (size_t)g_stage_smem[dev]) {
         // the CDF does not fit on chip: one kernel per step, searching the CDF in global memory
         cudaError_t e = cudaSuccess;
-        if (rows) e = launch_sample(w, n_frames, rows, fold, s);
-        if (!e && cols) e = launch_targets(w, n_frames, cols, s);
+        if (rows) e = launch_sample(w, n_frames, rows, fold, tc, s);
+        if (!e && cols) e = launch_targets(w, n_frames, cols, tc, s);
         return e;
     }
     cudaError_t e = launch_pdl(k_stage, n_frames * slices, STAGE_THREADS, need, s, w, slices,
-                               (int)(rows > 0), (int)(cols > 0), fold);
+                               (int)(rows > 0), (int)(cols > 0), fold, tc);
     count_launch();
     return e ? e : cudaGetLastError();
 }

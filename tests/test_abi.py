@@ -96,9 +96,10 @@ def test_noalloc_rejects_problems_beyond_its_scratch(L):
     regression of that order would fail with DC_EINVAL instead, and nothing would launch."""
     from paper_2204_03139_gb300 import _lib
 
-    T, V, F, N, M = 16, 2500, 4802, 10000, 10000
-    while _lib.dc_workspace_size(T, V, F, N, M) <= 4 * NOALLOC_SCRATCH_BYTES:
-        T *= 2
+    # 512 frames of 10 000 x 10 000: the sampled points alone (16 B each, before any other
+    # region) take 82 MB, more than four times the scratch, whatever the engine's layout
+    T, V, F, N, M = 512, 2500, 4802, 10000, 10000
+    assert T * N * 16 > 4 * NOALLOC_SCRATCH_BYTES
     rc = L.dc_loss_traj_noalloc(None, None, None, None, None, T, V, F, N, M, 0,
                                 None, None, None, None, None, None, None, None)
     assert rc == _lib.DC_ENOSPC

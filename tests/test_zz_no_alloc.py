@@ -53,10 +53,13 @@ def test_noalloc_matches_workspace_entry_point_twice(mode):
                                           ref["loss_frames"].cpu().numpy())
             parity.check_loss(got["loss_total"].cpu().numpy(), ref["loss_total"].cpu().numpy())
             parity.check_grad(got["grad_verts"].cpu().numpy(), ref["grad_verts"].cpu().numpy())
-            np.testing.assert_array_equal(got["nn_ab"].cpu().numpy(), ref["nn_ab"].cpu().numpy())
+            # neighbours of the frames that ran (a skipped frame's are not written)
+            live = [t for t in range(tr.T) if w is None or w[t] != 0.0]
+            np.testing.assert_array_equal(got["nn_ab"].cpu().numpy()[live],
+                                          ref["nn_ab"].cpu().numpy()[live])
             if mode == 0:
-                np.testing.assert_array_equal(got["nn_ba"].cpu().numpy(),
-                                              ref["nn_ba"].cpu().numpy())
+                np.testing.assert_array_equal(got["nn_ba"].cpu().numpy()[live],
+                                              ref["nn_ba"].cpu().numpy()[live])
             if w is not None:
                 dead = [t for t in range(tr.T) if w[t] == 0.0]
                 assert np.all(got["loss_frames"].cpu().numpy()[dead] == 0.0)
