@@ -197,6 +197,21 @@ size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames);
 int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size_t ws_bytes,
                   dc_stream_t stream);
 
+/* Bytes of host staging memory dc_batch_plan_async needs for these frames and mode (with
+ * the engine that the current dc_tune_set selects); 0 if the frames are invalid. */
+size_t dc_batch_plan_bytes(const dc_frame* frames, int n_frames, int mode);
+
+/*
+ * dc_batch_plan_async -- dc_batch_plan that does not wait for `stream`: the tables are built
+ * in the caller's host_staging (host memory of at least dc_batch_plan_bytes bytes; pinned, for
+ * the copy to be asynchronous) and copied from there on `stream`. The caller keeps
+ * host_staging unchanged until that copy has completed (e.g. until an event recorded on
+ * `stream` after the call, or after the batch's first run, has completed).
+ */
+int dc_batch_plan_async(const dc_frame* frames, int n_frames, int mode, void* ws,
+                        size_t ws_bytes, void* host_staging, size_t staging_bytes,
+                        dc_stream_t stream);
+
 /*
  * dc_batch_run -- forward (and the gradient of every frame whose grad_verts is set) of a
  * planned batch: sampling, one persistent Chamfer launch over all frames, neighbours,
@@ -230,6 +245,16 @@ typedef struct dc_tune {
 
 int dc_tune_set(const dc_tune* tune); /* NULL restores automatic */
 int dc_tune_get(dc_tune* tune);
+
+/*
+ * dc_loss_total -- the weighted total of given per-frame losses, sum_t w_t L_t (the
+ * objective over a trajectory, Sec. III-C), in the same fixed summation order as the
+ * loss_total of dc_loss_traj: a caller that computed a trajectory's frames in several
+ * batches gets the total the whole trajectory would have given in one call.
+ *   loss_frames [T] device; frame_w [T] device, nullable (all ones); loss_total [1] device out.
+ */
+int dc_loss_total(const float* loss_frames, const float* frame_w, int T, float* loss_total,
+                  dc_stream_t stream);
 
 /*
  * dc_ws_status -- synchronise `stream` and return the first device-side error recorded in

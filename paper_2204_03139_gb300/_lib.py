@@ -75,6 +75,9 @@ def lib() -> ctypes.CDLL:
                                          S, P]),
                 "dc_batch_workspace_size": (S, [P, I]),
                 "dc_batch_plan": (I, [P, I, I, P, S, P]),
+                "dc_batch_plan_bytes": (S, [P, I, I]),
+                "dc_batch_plan_async": (I, [P, I, I, P, S, P, S, P]),
+                "dc_loss_total": (I, [P, P, I, P, P]),
                 "dc_batch_run": (I, [P, P, P]),
                 "dc_ws_status": (I, [P, P]),
                 "dc_last_error": (ctypes.c_char_p, []),
@@ -364,6 +367,19 @@ def dc_loss_traj_bwd(verts, faces, draws, targets, nn_ab, nn_ba, grad_frames=Non
     if check:
         check_ws(ws)
     return gv
+
+
+def dc_loss_total(loss_frames, frame_w=None, out=None):
+    """sum_t w_t L_t of per-frame losses on the device, in the library's fixed order."""
+    dev = _dev(loss_frames)
+    T = loss_frames.numel()
+    _need(loss_frames, "loss_frames", torch.float32, (T,), dev)
+    if frame_w is not None:
+        _need(frame_w, "frame_w", torch.float32, (T,), dev)
+    lt = out if out is not None else torch.empty(1, dtype=torch.float32, device=dev)
+    _need(lt, "loss_total", torch.float32, (1,), dev)
+    _check(lib().dc_loss_total(_ptr(loss_frames), _ptr(frame_w), T, _ptr(lt), _stream(dev)))
+    return lt
 
 
 def launch_count() -> int:

@@ -73,10 +73,14 @@ class BatchedLoss:
     """
 
     def __init__(self, trajs, mode=_lib.BIDIR_MEAN, weights=None, grad=True, graph=False,
-                 nn=False, stream=None, tune=False, shape=None):
+                 nn=False, stream=None, tune=False, shape=None, outputs=None,
+                 async_plan=False):
         """tune=True: plan with the shape the autotuner found fastest for this batch's size
         bucket (timing every shape first if the bucket has no entry); shape: plan with this
-        shape (autotune.SHAPES); otherwise the library's default."""
+        shape (autotune.SHAPES); otherwise the library's default. outputs: per trajectory a
+        (loss_frames [T], grad_verts [T, V, 3] or None) pair of device tensors to write into
+        instead of new ones. async_plan: upload the plan from pinned staging memory without
+        waiting for the stream (the staging stays referenced by this object)."""
         from . import autotune
 
         self.trajs = list(trajs)
@@ -94,11 +98,11 @@ class BatchedLoss:
         # outputs and workspace belong to the batch's stream (the caching allocator reuses
         # memory per stream); the plan keeps the shape it was made with
         with torch.cuda.stream(self.stream), autotune.tuned(shape):
-            self._build(mode, weights, grad, nn)
+            self._build(mode, weights, grad, nn, outputs, async_plan)
         if graph:
             self._capture()
 
-    def _build(self, mode, weights, grad, nn):
+    def _build(self, mode, weights, grad, nn, outputs=None, async_plan=False):
         dev = self.device
         nfr = sum(t.T for t in self.trajs)
         # the dc_frame table, filled column by column (one row per frame)
@@ -107,8 +111,17 @@ class BatchedLoss:
         k = 0
         for i, tr in enumerate(self.trajs):
             T, V, F = tr.T, int(tr.verts.shape[1]), int(tr.faces.shape[0])
-            lf = torch.empty(T, dtype=torch.float32, device=dev)
-            gv = torch.empty((T, V, 3), dtype=torch.float32, device=dev) if grad else None
+            if outputs is not None and outputs[i] is not None:
+                lf, gv = outputs[i]
+                if lf.dtype != torch.float32 or tuple(lf.shape) != (T,) or not lf.is_contiguous():
+                    raise ValueError("outputs: loss_frames must be a contiguous [T] float32 tensor")
+                if grad and (gv is None or tuple(gv.shape) != (T, V, 3) or
+                             gv.dtype != torch.float32 or not gv.is_contiguous()):
+                    raise ValueError("outputs: grad_verts must be a contiguous [T, V, 3] "
+                                     "float32 tensor")
+            else:
+                lf = torch.empty(T, dtype=torch.float32, device=dev)
+                gv = torch.empty((T, V, 3), dtype=torch.float32, device=dev) if grad else None
             nab = torch.empty(int(tr.n_off[-1]), dtype=torch.int32, device=dev) if nn else None
             nba = (torch.empty(int(tr.m_off[-1]), dtype=torch.int32, device=dev)
                    if nn and mode == _lib.BIDIR_MEAN else None)
@@ -151,8 +164,19 @@ class BatchedLoss:
         self.total = torch.empty(1, dtype=torch.float32, device=dev)
         self.workspace_bytes = nb
         self.n_frames = nfr
-        _lib._check(L.dc_batch_plan(self.frames, nfr, mode, ctypes.c_void_p(self.ws.data_ptr()),
-                                    nb, ctypes.c_void_p(self.stream.cuda_stream)))
+        if async_plan:
+            sb = int(L.dc_batch_plan_bytes(self.frames, nfr, mode))
+            if sb == 0:
+                raise _lib.DCError(_lib.DC_EINVAL, "bad batch sizes")
+            self._staging = torch.empty(sb, dtype=torch.uint8, pin_memory=True)
+            _lib._check(L.dc_batch_plan_async(self.frames, nfr, mode,
+                                              ctypes.c_void_p(self.ws.data_ptr()), nb,
+                                              ctypes.c_void_p(self._staging.data_ptr()), sb,
+                                              ctypes.c_void_p(self.stream.cuda_stream)))
+        else:
+            _lib._check(L.dc_batch_plan(self.frames, nfr, mode,
+                                        ctypes.c_void_p(self.ws.data_ptr()), nb,
+                                        ctypes.c_void_p(self.stream.cuda_stream)))
         self.graph = None
 
     def _launch(self):

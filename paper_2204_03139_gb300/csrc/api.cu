@@ -318,6 +318,9 @@ struct Plan {
 std::mutex g_plan_mu;
 std::unordered_map<const void*, Plan> g_plans;
 
+int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t ws_bytes,
+              char* host_staging, size_t staging_bytes, size_t* size_only, cudaStream_t stream);
+
 }  // namespace
 }  // namespace dc
 
@@ -391,6 +394,18 @@ size_t dc_workspace_size(int T, int V, int F, int N, int M) {
     int spu;
     if (!uniform_sizes(T, V, F, N, M, sz, sub, spu)) return 0;
     return make_layout(sz).total;
+}
+
+int dc_loss_total(const float* loss_frames, const float* frame_w, int T, float* loss_total,
+                  dc_stream_t stream) {
+    if (T <= 0) return fail(DC_EINVAL, "T must be positive");
+    int rc = check_ptrs({loss_frames, loss_total}, "dc_loss_total");
+    if (rc) return rc;
+    if (frame_w && !aligned(frame_w, 4)) return fail(DC_EINVAL, "frame_w not 4-byte aligned");
+    cudaError_t e = launch_loss_total(loss_frames, frame_w, T, loss_total,
+                                      static_cast<cudaStream_t>(stream));
+    if (e) return cuda_fail(e, "dc_loss_total");
+    return DC_OK;
 }
 
 int dc_ws_status(const void* ws, dc_stream_t stream) {
@@ -586,6 +601,35 @@ size_t dc_batch_workspace_size(const dc_frame* frames, int n_frames) {
 
 int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size_t ws_bytes,
                   dc_stream_t stream) {
+    return plan_impl(frames, n_frames, mode, ws, ws_bytes, nullptr, 0, nullptr, stream);
+}
+
+size_t dc_batch_plan_bytes(const dc_frame* frames, int n_frames, int mode) {
+    size_t need = 0;
+    if (plan_impl(frames, n_frames, mode, nullptr, 0, nullptr, 0, &need, nullptr) != DC_OK)
+        return 0;
+    return need;
+}
+
+int dc_batch_plan_async(const dc_frame* frames, int n_frames, int mode, void* ws,
+                        size_t ws_bytes, void* host_staging, size_t staging_bytes,
+                        dc_stream_t stream) {
+    if (!host_staging) return fail(DC_EINVAL, "dc_batch_plan_async: host_staging is NULL");
+    return plan_impl(frames, n_frames, mode, ws, ws_bytes, static_cast<char*>(host_staging),
+                     staging_bytes, nullptr, stream);
+}
+
+}  // extern "C"
+
+namespace dc {
+namespace {
+
+// dc_batch_plan and its variants. With host_staging the tables are built there and copied
+// without waiting for the stream; without it the copy is made from the library's own host
+// memory and the stream is synchronised. With size_only (and no workspace) only the bytes of
+// the staging image are returned.
+int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t ws_bytes,
+              char* host_staging, size_t staging_bytes, size_t* size_only, cudaStream_t stream) {
     if (!frames || n_frames <= 0) return fail(DC_EINVAL, "no frames");
     if (mode != DC_BIDIR_MEAN && mode != DC_UNIDIR_SUM) return fail(DC_EINVAL, "bad mode");
     for (int k = 0; k < n_frames; ++k) {
@@ -605,8 +649,17 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     const int engine = choose_engine(sz.tc_units > 0);
     const int warps = engine == ENGINE_DIRECT ? choose_warps(mode, sub[2], sub[1], sub[0]) : 1;
     const Layout L = make_layout(sz);
+    // the staging image: the table regions [hdr, cdf), then the tensor-core unit tables
+    const size_t img_bytes = L.cdf + (engine == ENGINE_TC ? L.tca - L.tc_ufr : 0);
+    if (size_only) {
+        *size_only = img_bytes;
+        return DC_OK;
+    }
     int rc = check_ws(ws, ws_bytes, L.total);
     if (rc) return rc;
+    if (host_staging && staging_bytes < img_bytes)
+        return fail(DC_ENOSPC, "host staging has %zu bytes, %zu needed", staging_bytes,
+                    img_bytes);
     const Ws w = make_ws(ws, L);
 
     // host image of the table regions [hdr, cdf)
@@ -714,11 +767,19 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     h->tc_units = engine == ENGINE_TC ? tunit : 0;
     h->tc_total = engine == ENGINE_TC ? tchunk : 0;
     h->tc_fallback = 0;
-    cudaError_t e = cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, stream);
+    const char* src_img = img.data();
+    const char* src_tc = tcimg.data();
+    if (host_staging) {  // the caller's (pinned) memory: the copies need no host wait
+        memcpy(host_staging, img.data(), img.size());
+        if (!tcimg.empty()) memcpy(host_staging + img.size(), tcimg.data(), tcimg.size());
+        src_img = host_staging;
+        src_tc = host_staging + img.size();
+    }
+    cudaError_t e = cudaMemcpyAsync(ws, src_img, img.size(), cudaMemcpyHostToDevice, stream);
     if (!e && !tcimg.empty())
-        e = cudaMemcpyAsync(static_cast<char*>(ws) + tc_beg, tcimg.data(), tcimg.size(),
+        e = cudaMemcpyAsync(static_cast<char*>(ws) + tc_beg, src_tc, tcimg.size(),
                             cudaMemcpyHostToDevice, stream);
-    if (!e) e = cudaStreamSynchronize(stream);
+    if (!e && !host_staging) e = cudaStreamSynchronize(stream);
     if (e) return cuda_fail(e, "dc_batch_plan copy");
     Plan p;
     p.sz = sz;
@@ -738,6 +799,11 @@ int dc_batch_plan(const dc_frame* frames, int n_frames, int mode, void* ws, size
     g_plans[ws] = p;
     return DC_OK;
 }
+
+}  // namespace
+}  // namespace dc
+
+extern "C" {
 
 int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
     Plan p;

@@ -296,6 +296,9 @@ int tuned_warps();
 enum : int { EPI_RESCAN = 1, EPI_LOSS = 2, EPI_GRAD = 4 };
 cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, int mode,
                             int flags, float* total, int tc_grid, cudaStream_t s);
+// sum_t w_t L_t of given per-frame losses, in the fixed order of the trajectory calls
+cudaError_t launch_loss_total(const float* lf, const float* w, int T, float* total,
+                              cudaStream_t s);
 cudaError_t launch_chamfer_bwd_points(const float* a, const float* b, const int* nn_ab,
                                       const int* nn_ba, int T, int N, int M, int mode,
                                       const float* g, float* grad_a, cudaStream_t s);

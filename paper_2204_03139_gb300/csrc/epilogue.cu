@@ -309,6 +309,18 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_frame_loss(Ws w, int n_frames,
     if (threadIdx.x == 0 && total) total[0] = s;
 }
 
+// sum_t w_t L_t of given per-frame losses in the same fixed order as k_frame_loss
+__global__ void __launch_bounds__(LOSS_THREADS) k_loss_total(const float* lf, const float* w,
+                                                             int T, float* total) {
+    pdl_entry();
+    __shared__ float s_red[LOSS_THREADS / 32];
+    float t = 0.f, tc = 0.f;
+    for (int k = threadIdx.x; k < T; k += LOSS_THREADS)
+        kahan_add(t, tc, __fmul_rn(w ? w[k] : 1.0f, lf[k]));
+    const float s = block_sum_fixed(t, s_red);
+    if (threadIdx.x == 0) total[0] = s;
+}
+
 // ---- gradient with respect to given sim points (dc_chamfer_bwd) ----
 __global__ void __launch_bounds__(256) k_cbwd_rows(const float* a, const float* b,
                                                    const int* nn_ab, int T, int N, int M,
@@ -396,6 +408,13 @@ cudaError_t launch_epilogue(const Ws& w, int n_frames, int slices, int max_v, in
                        total);
         count_launch();
     }
+    return e ? e : cudaGetLastError();
+}
+
+cudaError_t launch_loss_total(const float* lf, const float* w, int T, float* total,
+                              cudaStream_t s) {
+    cudaError_t e = launch_pdl(k_loss_total, 1, LOSS_THREADS, 0, s, lf, w, T, total);
+    count_launch();
     return e ? e : cudaGetLastError();
 }
 

@@ -17,7 +17,12 @@ every optimisation). The server batches continuously:
     one after another instead of sharing the GPU and all finishing late), except that a
     request waiting longer than `max_wait_s` goes first, so that long ones never starve;
   - overlap: batches on different streams run at the same time while new requests are
-    admitted and copied in; finished batches resolve their requests' futures and release their
+    admitted and copied in. A batch's plan is uploaded from pinned staging memory without
+    waiting for its stream, and every item writes its frames' losses and gradients straight
+    into its request's device buffers; when a request's last item finishes, the library forms
+    its total (dc_loss_total, the same fixed order as one dc_loss_traj call) and the results
+    go back to pinned host memory by copies that an event completes, so the scheduler thread
+    never waits for the device. Finished requests resolve their futures and release their
     memory, which admits the next requests.
 
 Every result equals the one the request gets alone (same kernels; only the order of the
@@ -61,10 +66,16 @@ class _Request:
     dev: DeviceTrajectory | None = None
     ready: torch.cuda.Event | None = None
     host: tuple = field(default_factory=tuple)
-    loss: np.ndarray | None = None     # [T] filled item by item
-    gradv: np.ndarray | None = None    # [T, V, 3]
-    left: int = 0                      # items not finished yet
+    loss_dev: torch.Tensor | None = None   # [T] on the device, written item by item
+    grad_dev: torch.Tensor | None = None   # [T, V, 3]
+    w_dev: torch.Tensor | None = None      # [T] frame weights (None: all ones)
+    total_dev: torch.Tensor | None = None  # [1] sum_t w_t L_t, formed by the library
+    out_host: tuple = field(default_factory=tuple)  # pinned (loss, grad, total) copies
+    fin: torch.cuda.Event | None = None    # the host copies of the results are complete
+    left: int = 0                          # items not finished yet
     batches: set = field(default_factory=set)
+    last_batch: int = 0
+    last_batch_items: int = 0              # items in the batch that finished the request
     failed: bool = False
 
 
@@ -161,6 +172,8 @@ class Server:
         self._closing = False
         self.completed: list[tuple[int, float, int, int]] = []  # (rid, latency, pairs, batch)
         self.batch_sizes: list[int] = []
+        self.host_launch_s: list[float] = []  # scheduler host time to plan and launch a batch
+        self._finishing: list = []
         self._thread = threading.Thread(target=self._loop, name="diffcloud-serve", daemon=True)
         self._thread.start()
 
@@ -198,11 +211,14 @@ class Server:
 
     def stats(self) -> dict:
         lat = np.array([c[1] for c in self.completed]) if self.completed else np.zeros(0)
+        hl = np.array(self.host_launch_s) if self.host_launch_s else np.zeros(0)
         return {"requests": len(self.completed),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
                 "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
                 "mean_batch_requests": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0,
-                "batches": len(self.batch_sizes)}
+                "batches": len(self.batch_sizes),
+                "host_ms_per_batch": float(hl.mean() * 1e3) if hl.size else None,
+                "host_ms_per_batch_p99": float(np.percentile(hl, 99) * 1e3) if hl.size else None}
 
     # ---- scheduler thread ----
     def _loop(self):
@@ -212,7 +228,7 @@ class Server:
         torch.cuda.set_stream(self._copy)
         while True:
             with self._cv:
-                idle = (not self._waiting and not self._admitted
+                idle = (not self._waiting and not self._admitted and not self._finishing
                         and all(b is None for b in self._busy))
                 if idle and self._closing:
                     return
@@ -223,6 +239,7 @@ class Server:
                 self._admit()
                 self._launch()
                 progressed = self._complete()
+                progressed = self._finish() or progressed
             except Exception as e:  # fail the affected requests, keep serving
                 self._fail_all(e)
                 progressed = True
@@ -257,8 +274,14 @@ class Server:
             r.dev = DeviceTrajectory(dv[0], dv[1], dv[2], dv[3], np.asarray(tr.n_off, np.int64),
                                      np.asarray(tr.m_off, np.int64),
                                      dv[4] if len(dv) > 4 else None)
-            r.loss = np.empty(tr.T, np.float32)
-            r.gradv = np.empty(tr.verts.shape, np.float32) if r.grad else None
+            with torch.cuda.stream(self._copy):
+                r.loss_dev = torch.empty(tr.T, dtype=torch.float32, device=self.device)
+                r.grad_dev = (torch.empty(tr.verts.shape, dtype=torch.float32, device=self.device)
+                              if r.grad else None)
+                r.total_dev = torch.empty(1, dtype=torch.float32, device=self.device)
+                if r.weights is not None:
+                    r.w_dev = torch.from_numpy(np.ascontiguousarray(r.weights, np.float32)).to(
+                        self.device, non_blocking=False)
             # cut into items of consecutive frames of at most item_pairs pairs
             per = np.diff(r.dev.n_off) * np.diff(r.dev.m_off)
             a = 0
@@ -290,13 +313,22 @@ class Server:
             stream = self._streams[s_idx]
             for r in {id(it.req): it.req for it in take}.values():
                 stream.wait_event(r.ready)
-            weights = []
+            t_host = time.perf_counter()
+            weights, outs = [], []
             for it in take:
                 w = it.req.weights
                 weights.append(w[it.a:it.b] if w is not None else np.ones(it.b - it.a, np.float32))
-            b = BatchedLoss([it.dev for it in take], mode=mode, weights=weights,
-                            grad=any(it.req.grad for it in take), stream=stream)
+                outs.append((it.req.loss_dev[it.a:it.b],
+                             it.req.grad_dev[it.a:it.b] if it.req.grad_dev is not None else None))
+            any_grad = any(it.req.grad for it in take)
+            if any_grad:  # a batch either computes every frame's gradient or none
+                outs = [(lf, gv) if gv is not None else (lf, torch.empty(
+                    (lf.shape[0],) + tuple(it.dev.verts.shape[1:]), dtype=torch.float32,
+                    device=self.device)) for (lf, gv), it in zip(outs, take)]
+            b = BatchedLoss([it.dev for it in take], mode=mode, weights=weights, grad=any_grad,
+                            stream=stream, outputs=outs, async_plan=True)
             b.run()
+            self.host_launch_s.append(time.perf_counter() - t_host)
             done = torch.cuda.Event()
             done.record(stream)
             self._busy[s_idx] = (b, done, take, self._next_batch, pairs)
@@ -311,39 +343,67 @@ class Server:
             b, done, take, bid, _ = busy
             if not done.query():
                 continue
-            finished = []
-            # status and results are read on the batch's own stream, which is done: nothing
-            # here waits for the batch running on the other stream
-            with torch.cuda.stream(b.stream):
-                status = _lib.ws_status(b.ws, b.stream)
-                for i, it in enumerate(take):
-                    r = it.req
-                    if status != _lib.DC_OK:
-                        r.failed = True
-                    else:
-                        r.loss[it.a:it.b] = b.loss_frames[i].cpu().numpy()
-                        if r.grad and b.grad_verts[i] is not None:
-                            r.gradv[it.a:it.b] = b.grad_verts[i].cpu().numpy()
-                    r.batches.add(bid)
-                    r.left -= 1
-                    if r.left == 0:
-                        finished.append(r)
-            for r in finished:
-                if r.failed:
-                    r.future.set_exception(_lib.DCError(status, "device-side error in batch"))
-                else:
-                    w = r.weights if r.weights is not None else np.ones_like(r.loss)
-                    lat = time.perf_counter() - r.arrival
-                    r.future.set_result(Result(r.loss, float(np.sum(w.astype(np.float64) * r.loss)),
-                                               r.gradv, lat, max(r.batches), len(take)))
-                    self.completed.append((r.rid, lat, r.dev.pairs(), bid))
-                r.dev = None
-                r.host = ()
-                with self._cv:
-                    self._used -= r.nbytes
+            # the batch's stream is idle: reading its status waits for nothing
+            status = _lib.ws_status(b.ws, b.stream)
+            for it in take:
+                r = it.req
+                if status != _lib.DC_OK:
+                    r.failed = True
+                r.batches.add(bid)
+                r.last_batch = bid
+                r.last_batch_items = len(take)
+                r.left -= 1
+                if r.left == 0:
+                    self._finalize(r, b.stream, status)
             self._busy[s_idx] = None
             progressed = True
         return progressed
+
+    def _finalize(self, r, stream, status):
+        """The request's last item is done (every earlier one too): on the batch's stream, the
+        library forms the total and the results are copied to pinned host memory; an event
+        marks their arrival, which _finish waits for without blocking."""
+        if r.failed:
+            r.future.set_exception(_lib.DCError(status, "device-side error in batch"))
+            self._release(r)
+            return
+        with torch.cuda.stream(stream):
+            _lib.dc_loss_total(r.loss_dev, r.w_dev, out=r.total_dev)
+            h_loss = torch.empty(r.loss_dev.shape, dtype=torch.float32, pin_memory=True)
+            h_total = torch.empty(1, dtype=torch.float32, pin_memory=True)
+            h_loss.copy_(r.loss_dev, non_blocking=True)
+            h_total.copy_(r.total_dev, non_blocking=True)
+            h_grad = None
+            if r.grad_dev is not None:
+                h_grad = torch.empty(r.grad_dev.shape, dtype=torch.float32, pin_memory=True)
+                h_grad.copy_(r.grad_dev, non_blocking=True)
+            r.fin = torch.cuda.Event()
+            r.fin.record(stream)
+        r.out_host = (h_loss, h_grad, h_total)
+        self._finishing.append(r)
+
+    def _finish(self) -> bool:
+        progressed = False
+        for r in list(self._finishing):
+            if not r.fin.query():
+                continue
+            self._finishing.remove(r)
+            h_loss, h_grad, h_total = r.out_host
+            lat = time.perf_counter() - r.arrival
+            r.future.set_result(Result(h_loss.numpy(), float(h_total[0]),
+                                       h_grad.numpy() if h_grad is not None else None, lat,
+                                       r.last_batch, r.last_batch_items))
+            self.completed.append((r.rid, lat, r.dev.pairs(), r.last_batch))
+            self._release(r)
+            progressed = True
+        return progressed
+
+    def _release(self, r):
+        r.dev = None
+        r.host = ()
+        r.loss_dev = r.grad_dev = r.total_dev = r.w_dev = None
+        with self._cv:
+            self._used -= r.nbytes
 
     def _fail_all(self, e):
         reqs = {}
@@ -355,6 +415,9 @@ class Server:
         for it in self._admitted:
             reqs[id(it.req)] = it.req
         self._admitted.clear()
+        for r in self._finishing:
+            reqs[id(r)] = r
+        self._finishing.clear()
         for r in reqs.values():
             if not r.future.done():
                 r.future.set_exception(e)

@@ -77,14 +77,14 @@ def test_single_frame_25x25(mode):
     compare_traj(tr, g, ref, [0], mode)
 
 
-def test_trajectory_50x50_full_size_sampled_frames():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_trajectory_50x50_full_size_every_frame(mode):
     """The 40-frame 50x50 trajectory at full size (10 000 x 10 000 per frame), in the launch
-    configuration the bench times; the oracle checks frames 0, 19 and 39."""
+    configuration the bench times; every frame against the oracle, and the total."""
     tr = parity.nudged(W.trajectory_50x50())
-    g = run_traj(tr)
-    frames = [0, 19, 39]
-    ref = oracle.loss_traj(tr, frames=frames)
-    compare_traj(tr, g, ref, frames)
+    g = run_traj(tr, mode)
+    ref = oracle.loss_traj(tr, mode=mode)
+    compare_traj(tr, g, ref, list(range(tr.T)), mode)
     assert np.all(np.isfinite(g["loss_frames"])) and np.all(g["loss_frames"] > 0)
 
 
@@ -279,14 +279,70 @@ def test_zero_weight_frames_are_skipped(w):
     assert parity.rel_l2(gb[live], g["grad_verts"][live]) < 1e-6
 
 
-@pytest.mark.slow
-def test_trajectory_100x100_full_size_sampled_frames():
-    """100x100 grid, T = 100, 32 768 x 32 768 per frame; the oracle checks two frames."""
+@pytest.fixture(scope="module")
+def traj100():
+    """The 100-frame 100x100 trajectory (32 768 x 32 768 per frame) and its oracle result."""
     tr = parity.nudged(W.trajectory_100x100())
+    return tr, oracle.loss_traj(tr)
+
+
+@pytest.mark.slow
+def test_trajectory_100x100_full_size_every_frame(traj100):
+    """100x100 grid, T = 100, 32 768 x 32 768 per frame: every frame against the oracle."""
+    tr, ref = traj100
     g = run_traj(tr)
-    frames = [0, 99]
-    ref = oracle.loss_traj(tr, frames=frames)
-    compare_traj(tr, g, ref, frames)
+    compare_traj(tr, g, ref, list(range(tr.T)))
+
+
+@pytest.mark.slow
+def test_trajectory_100x100_autograd_recompute_matches_oracle_and_fd(traj100):
+    """The differentiation configuration at full size: the loss through the autograd Function
+    (forward without the gradient, backward recomputing the samples from the stored draws),
+    its full 100-frame vertex gradient against the oracle, and 200 random vertex coordinates
+    of one frame against FP64 central differences of the oracle at h = 1e-6 m (coordinates
+    whose +-h runs change a face pick or a neighbour are skipped)."""
+    from paper_2204_03139_gb300.autograd import loss_traj
+
+    tr, ref = traj100
+    v, f, d, y = to_dev(tr)
+    vv = v.clone().requires_grad_(True)
+    total, lf = loss_traj(vv, f, d, y)
+    total.backward()
+    torch.cuda.synchronize()
+    parity.check_loss(lf.detach().cpu().numpy(), ref["loss_frames"])
+    parity.check_loss([float(total)], [ref["loss_total"]], what="total")
+    gpu_g = vv.grad.cpu().numpy()
+    parity.check_grad(gpu_g, ref["grad_verts"])
+    fd_check(tr, gpu_g, ref, t=37, n=200, seed=17)
+
+
+def fd_check(tr, gpu_g, ref, t, n, seed):
+    """FP64 central differences of the oracle loss of frame t at h = 1e-6 m on n random
+    vertex coordinates against the GPU gradient; coordinates whose +-h runs change a pick or
+    a neighbour are skipped (at least three quarters must count)."""
+    rng = W.rng_for(seed)
+    base = oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t), tr.frame_targets(t),
+                        grads=False)
+    scale = np.abs(ref["grad_verts"][t]).max()
+    checked = 0
+    for _ in range(n):
+        vi, k = int(rng.integers(tr.V)), int(rng.integers(3))
+        vp, vm = tr.verts[t].copy(), tr.verts[t].copy()
+        vp[vi, k] = np.float32(vp[vi, k] + 1e-6)
+        vm[vi, k] = np.float32(vm[vi, k] - 1e-6)
+        rp = oracle.frame(vp, tr.faces, tr.frame_draws(t), tr.frame_targets(t), grads=False)
+        rm = oracle.frame(vm, tr.faces, tr.frame_draws(t), tr.frame_targets(t), grads=False)
+        if not all(np.array_equal(rp[q], rm[q]) and np.array_equal(rp[q], base[q])
+                   for q in ("face_idx", "nn_ab", "nn_ba")):
+            continue
+        a_ = float(vp[vi, k]) - float(tr.verts[t][vi, k])
+        b_ = float(tr.verts[t][vi, k]) - float(vm[vi, k])
+        fd = (b_ * b_ * (rp["loss"] - base["loss"]) + a_ * a_ * (base["loss"] - rm["loss"])) / (
+            a_ * b_ * (a_ + b_))
+        # the GPU gradient of this coordinate agrees with the FP64 difference quotient
+        assert abs(gpu_g[t, vi, k] - fd) <= 1e-4 * scale + 1e-6 * abs(fd), (vi, k, fd)
+        checked += 1
+    assert checked >= 0.75 * n
 
 
 # ---------------------------------------------------------------------------------------------
@@ -418,30 +474,33 @@ def test_autograd_matches_oracle_and_fd():
     parity.check_loss(lf.detach().cpu().numpy(), ref["loss_frames"])
     gpu_g = vv.grad.cpu().numpy()
     parity.check_grad(gpu_g, ref["grad_verts"])
-    # FD of the oracle loss at h = 1e-6 m; coordinates whose +-h runs change a pick or a
-    # neighbour are skipped
-    rng = W.rng_for(7)
-    t = 1
-    base = oracle.frame(tr.verts[t], tr.faces, tr.frame_draws(t), tr.frame_targets(t))
-    checked = 0
-    for _ in range(200):
-        vi, k = int(rng.integers(tr.V)), int(rng.integers(3))
-        vp, vm = tr.verts[t].copy(), tr.verts[t].copy()
-        vp[vi, k] = np.float32(vp[vi, k] + 1e-6)
-        vm[vi, k] = np.float32(vm[vi, k] - 1e-6)
-        rp = oracle.frame(vp, tr.faces, tr.frame_draws(t), tr.frame_targets(t), grads=False)
-        rm = oracle.frame(vm, tr.faces, tr.frame_draws(t), tr.frame_targets(t), grads=False)
-        if not all(np.array_equal(rp[q], rm[q]) and np.array_equal(rp[q], base[q])
-                   for q in ("face_idx", "nn_ab", "nn_ba")):
-            continue
-        a_, b_ = float(vp[vi, k]) - float(tr.verts[t][vi, k]), float(tr.verts[t][vi, k]) - float(vm[vi, k])
-        fd = (b_ * b_ * (rp["loss"] - base["loss"]) + a_ * a_ * (base["loss"] - rm["loss"])) / (
-            a_ * b_ * (a_ + b_))
-        # the GPU gradient of this coordinate agrees with the FP64 difference quotient
-        scale = np.abs(ref["grad_verts"][t]).max()
-        assert abs(gpu_g[t, vi, k] - fd) <= 1e-4 * scale + 1e-6 * abs(fd)
-        checked += 1
-    assert checked >= 150
+    fd_check(tr, gpu_g, ref, t=1, n=200, seed=7)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_autograd_total_and_frame_gradients_combine(mode):
+    """An objective of both outputs, J = 2 L_total + sum_t c_t L_t with a frame of weight 0:
+    the library forms g_t = 2 w_t + c_t (0 for the weight-0 frame, whose L_t is the constant
+    0), and the vertex gradient equals the oracle's with those multipliers."""
+    from paper_2204_03139_gb300.autograd import loss_traj
+
+    tr = parity.nudged(W.trajectory_50x50(T=4, n=3000, m=2500))
+    v, f, d, y = to_dev(tr)
+    w = np.array([1.0, 0.0, 0.5, 2.0])
+    c = np.array([0.25, 3.0, -1.0, 0.5])
+    vv = v.clone().requires_grad_(True)
+    total, lf = loss_traj(vv, f, d, y, mode=mode, frame_w=w)
+    J = 2.0 * total + (torch.tensor(c, dtype=torch.float32, device=DEV) * lf).sum()
+    J.backward()
+    torch.cuda.synchronize()
+    gs = np.where(w != 0.0, 2.0 * w + c, 0.0)
+    ref = oracle.loss_traj(tr, mode=mode, weights=w, gscale=gs)
+    live = [t for t in range(4) if w[t] != 0.0]
+    parity.check_loss(lf.detach().cpu().numpy()[live], ref["loss_frames"][live])
+    assert float(lf[1]) == 0.0
+    g = vv.grad.cpu().numpy()
+    parity.check_grad(g[live], ref["grad_verts"][live])
+    assert np.all(g[1] == 0.0)
 
 
 # ---------------------------------------------------------------------------------------------

@@ -89,3 +89,30 @@ def test_device_error_fails_only_its_batch(dev):
     srv.close()
     ref = oracle.loss_traj(good)
     parity.check_loss(out.loss_frames, ref["loss_frames"])
+
+
+@pytest.mark.slow
+def test_config5_sizes_alone_equals_in_mix(dev):
+    """Requests of the serving mix's two sizes (50x50 / 40 frames / 10 000 points and
+    100x100 / 100 frames / 32 768 points): each result in a mix equals the one the request gets
+    alone, and a request of each size matches the oracle."""
+    from paper_2204_03139_gb300.serve import Server
+
+    small = [parity.nudged(W.lift_trajectory(W.SEED_BASE + 50 + k, 50, 40, 10_000, 10_000,
+                                             name=f"small{k}")) for k in range(3)]
+    big = parity.nudged(W.trajectory_100x100(seed=W.SEED_BASE + 60))
+    srv = Server(dev, hbm_budget=120 << 30)
+    alone_small = srv.submit(small[0]).result(timeout=600)
+    alone_big = srv.submit(big).result(timeout=600)
+    futs = [srv.submit(r) for r in (small[1], big, small[0], small[2])]
+    mixed = [f.result(timeout=600) for f in futs]
+    srv.close()
+    for a, m in ((alone_big, mixed[1]), (alone_small, mixed[2])):
+        np.testing.assert_allclose(m.loss_frames, a.loss_frames, rtol=1e-6)
+        assert parity.rel_l2(m.grad_verts, a.grad_verts) < 1e-6
+    assert max(r.batch_requests for r in mixed) > 1
+    for tr, res in ((small[0], alone_small), (big, alone_big)):
+        ref = oracle.loss_traj(tr)
+        parity.check_loss(res.loss_frames, ref["loss_frames"])
+        parity.check_loss([res.loss_total], [ref["loss_total"]], what="total")
+        parity.check_grad(res.grad_verts, ref["grad_verts"])
