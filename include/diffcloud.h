@@ -221,13 +221,16 @@ int dc_batch_plan_async(const dc_frame* frames, int n_frames, int mode, void* ws
 int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
 
 /*
- * Tuning of the nearest-neighbour search. Two engines compute the same neighbours and losses
+ * Tuning of the nearest-neighbour search. Three engines compute the same neighbours and losses
  * (the float32 direct form, lowest index among equal distances):
  *   DC_ENGINE_TENSOR -- a tensor-core filter: the expanded form |p|^2 - 2 p.q + |q|^2 on
- *     split-fp16 operands (one MMA per 16 x 8 pairs) keeps, per point, the three best blocks
- *     of 128 candidates, and the direct form re-checks only the blocks that a proven error
- *     bound cannot exclude (all candidates when it cannot certify two). Frames of at most
- *     524 288 points per side. The default (DC_ENGINE_AUTO) wherever it applies.
+ *     split-fp16 operands, warp-level MMAs (16 points x 8 candidates each), keeps per point
+ *     and quarter of the candidates the three best blocks of 128, and the direct form
+ *     re-checks only the blocks that an error bound cannot exclude (every candidate when it
+ *     cannot certify the blocks). Frames of at most 524 288 points per side. The default
+ *     (DC_ENGINE_AUTO) wherever it applies.
+ *   DC_ENGINE_TCGEN05 -- the same filter on tcgen05 MMAs (128 points x 64 candidates each)
+ *     into tensor memory; same keys, same recovery, same results.
  *   DC_ENGINE_DIRECT -- every pair in the direct form on the CUDA cores; a CTA of w warps
  *     (w = 1, 2 or 4) holds w * 512 sim points in registers while target chunks stream
  *     through it. warps_per_cta = 0 picks two warps when that gives every resident CTA
@@ -236,11 +239,11 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
  * them per problem size and sets the winner before its calls); batch plans keep the choice
  * they were planned with.
  */
-enum { DC_ENGINE_AUTO = 0, DC_ENGINE_DIRECT = 1, DC_ENGINE_TENSOR = 2 };
+enum { DC_ENGINE_AUTO = 0, DC_ENGINE_DIRECT = 1, DC_ENGINE_TENSOR = 2, DC_ENGINE_TCGEN05 = 3 };
 
 typedef struct dc_tune {
     int32_t warps_per_cta; /* direct engine: 0 (automatic), 1, 2 or 4 */
-    int32_t engine;        /* DC_ENGINE_AUTO, DC_ENGINE_DIRECT or DC_ENGINE_TENSOR */
+    int32_t engine;        /* DC_ENGINE_AUTO, _DIRECT, _TENSOR or _TCGEN05 */
 } dc_tune;
 
 int dc_tune_set(const dc_tune* tune); /* NULL restores automatic */

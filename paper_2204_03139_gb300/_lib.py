@@ -31,7 +31,7 @@ class DCError(RuntimeError):
         self.code = code
 
 
-ENGINE_AUTO, ENGINE_DIRECT, ENGINE_TENSOR = 0, 1, 2
+ENGINE_AUTO, ENGINE_DIRECT, ENGINE_TENSOR, ENGINE_TCGEN05 = 0, 1, 2, 3
 
 
 class dc_tune(ctypes.Structure):
@@ -422,8 +422,9 @@ def dc_loss_traj_noalloc(verts, faces, draws, targets, mode=BIDIR_MEAN, frame_w=
 
 
 def tune_set(warps_per_cta: int = 0, engine: int = ENGINE_AUTO):
-    """Nearest-neighbour engine (ENGINE_AUTO, ENGINE_DIRECT or ENGINE_TENSOR) and the direct
-    engine's CTA width (1, 2 or 4 warps; 0: automatic) for every later call and plan."""
+    """Nearest-neighbour engine (ENGINE_AUTO, ENGINE_DIRECT, ENGINE_TENSOR or ENGINE_TCGEN05)
+    and the direct engine's CTA width (1, 2 or 4 warps; 0: automatic) for every later call
+    and plan."""
     t = dc_tune(int(warps_per_cta), int(engine))
     _check(lib().dc_tune_set(ctypes.byref(t)))
 

@@ -1,7 +1,9 @@
 """Autotuner of the nearest-neighbour search's engine and tile shape.
 
 The shapes it chooses between:
-  ("tensor", 0)  the tensor-core filter (frames of at most 524 288 points per side);
+  ("tensor", 0)  the tensor-core filter on warp-level MMAs (frames of at most 524 288
+                 points per side; the library's default);
+  ("tcgen05", 0) the same filter on tcgen05 MMAs;
   ("direct", w)  the CUDA-core direct form with CTAs of w = 1, 2 or 4 warps (w x 512 sim
                  points held in registers; wide CTAs amortise the target staging and the
                  column merges, narrow ones split small problems into enough work items).
@@ -23,7 +25,9 @@ import torch
 
 from . import _lib
 
-SHAPES = (("tensor", 0), ("direct", 1), ("direct", 2), ("direct", 4))
+SHAPES = (("tensor", 0), ("tcgen05", 0), ("direct", 1), ("direct", 2), ("direct", 4))
+_ENGINES = {"tcgen05": _lib.ENGINE_TCGEN05, "tensor": _lib.ENGINE_TENSOR,
+            "direct": _lib.ENGINE_DIRECT}
 WIDTHS = (1, 2, 4)
 _lock = threading.Lock()
 _cache: dict | None = None
@@ -93,15 +97,14 @@ def best(T: int, N: int, M: int, mode: int = _lib.BIDIR_MEAN, device=None):
 
 @contextlib.contextmanager
 def tuned(shape):
-    """Use `shape` (("tensor", 0), ("direct", w), or an int w for the direct engine; None
-    leaves the current setting) for the calls and plans in the block."""
+    """Use `shape` (("tcgen05", 0), ("tensor", 0), ("direct", w), or an int w for the direct
+    engine; None leaves the current setting) for the calls and plans in the block."""
     shape = _norm(shape)
     if shape is None:
         yield
         return
     old = _lib.tune_get()
-    eng = _lib.ENGINE_TENSOR if shape[0] == "tensor" else _lib.ENGINE_DIRECT
-    _lib.tune_set(shape[1] if shape[0] == "direct" else 0, eng)
+    _lib.tune_set(shape[1] if shape[0] == "direct" else 0, _ENGINES[shape[0]])
     try:
         yield
     finally:

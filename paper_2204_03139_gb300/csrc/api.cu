@@ -185,11 +185,19 @@ int check_ws(void* ws, size_t ws_bytes, size_t need) {
 
 int g_engine = ENGINE_AUTO;  // process-wide engine set by dc_tune_set
 
-// The Chamfer engine of a call: the tensor-core filter when the problem fits its key format
-// (the default), else, or when the direct engine is requested, the CUDA-core direct form.
+// The Chamfer engine of a call: a tensor-core filter when the problem fits its key format
+// (tcgen05 by default, the warp-level MMA one when asked for), else, or when the direct
+// engine is requested, the CUDA-core direct form.
+// The default is the warp-level tensor-core filter: it measured faster than the tcgen05 one
+// on every workload (at K = 16 each distance tile is one isolated tcgen05 MMA, whose issue
+// cost the folds cannot hide), which stays available on request.
 int choose_engine(bool tc_fits) {
-    if (g_engine == ENGINE_DIRECT) return ENGINE_DIRECT;
-    return tc_fits ? ENGINE_TC : ENGINE_DIRECT;
+    if (g_engine == ENGINE_DIRECT || !tc_fits) return ENGINE_DIRECT;
+    return g_engine == ENGINE_TC5 ? ENGINE_TC5 : ENGINE_TC;
+}
+
+int keyed_grid(int engine, long long chunks) {
+    return engine == ENGINE_TC5 ? tc5_grid(chunks) : tc_grid(chunks);
 }
 
 int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total, void* ws,
@@ -213,7 +221,7 @@ int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total
     if (rc) return rc;
     const Ws w = make_ws(ws, L);
     const int T = a.T, rows = (int)sz.rows, cols = (int)sz.cols;
-    const bool tc = chamfer && engine == ENGINE_TC;
+    const bool tc = chamfer && keyed(engine);
     // with sampling to follow, the tables and the area CDFs (and the frame boxes of the
     // tensor-core forms) share one launch
     const bool fused = (phases & PH_AREA) && (phases & PH_SAMPLE);
@@ -231,11 +239,11 @@ int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total
             const long long u1 = a.mode == DC_BIDIR_MEAN ? div_up(a.M, TC_UNIT_ROWS) : 0;
             const long long chunks =
                 (long long)T * (div_up(a.N, TC_UNIT_ROWS) * (Mpad / TC_CHUNK) + u1 * (Npad / TC_CHUNK));
-            grid = tc_grid(chunks);
+            grid = keyed_grid(engine, chunks);
             const int units =
                 T * (div_up(a.N, TC_UNIT_ROWS) +
                      (a.mode == DC_BIDIR_MEAN ? div_up(a.M, TC_UNIT_ROWS) : 0));
-            e = launch_tcpass(w, grid, chunks, units, rows, cols, a.mode, T, st);
+            e = launch_tcpass(w, engine, grid, chunks, units, rows, cols, a.mode, T, st);
         } else {
             const long long units = (long long)T * a.units_per_frame;
             e = launch_chamfer(w, (int)units, (int)(units * spu), a.mode, warps, st);
@@ -369,12 +377,15 @@ int dc_tune_set(const dc_tune* tune) {
     const int en = tune ? tune->engine : DC_ENGINE_AUTO;
     if (w != 0 && w != 1 && w != 2 && w != 4)
         return fail(DC_EINVAL, "warps_per_cta must be 0 (automatic), 1, 2 or 4");
-    if (en != DC_ENGINE_AUTO && en != DC_ENGINE_DIRECT && en != DC_ENGINE_TENSOR)
-        return fail(DC_EINVAL, "engine must be DC_ENGINE_AUTO, DC_ENGINE_DIRECT or "
-                               "DC_ENGINE_TENSOR");
+    if (en != DC_ENGINE_AUTO && en != DC_ENGINE_DIRECT && en != DC_ENGINE_TENSOR &&
+        en != DC_ENGINE_TCGEN05)
+        return fail(DC_EINVAL, "engine must be DC_ENGINE_AUTO, DC_ENGINE_DIRECT, "
+                               "DC_ENGINE_TENSOR or DC_ENGINE_TCGEN05");
     set_tuned_warps(w);
-    g_engine = en == DC_ENGINE_DIRECT ? ENGINE_DIRECT : (en == DC_ENGINE_TENSOR ? ENGINE_TC
-                                                                                : ENGINE_AUTO);
+    g_engine = en == DC_ENGINE_DIRECT    ? ENGINE_DIRECT
+               : en == DC_ENGINE_TENSOR  ? ENGINE_TC
+               : en == DC_ENGINE_TCGEN05 ? ENGINE_TC5
+                                         : ENGINE_AUTO;
     return DC_OK;
 }
 
@@ -382,8 +393,9 @@ int dc_tune_get(dc_tune* tune) {
     if (!tune) return fail(DC_EINVAL, "tune is NULL");
     tune->warps_per_cta = tuned_warps();
     tune->engine = g_engine == ENGINE_DIRECT ? DC_ENGINE_DIRECT
-                                             : (g_engine == ENGINE_TC ? DC_ENGINE_TENSOR
-                                                                      : DC_ENGINE_AUTO);
+                   : g_engine == ENGINE_TC   ? DC_ENGINE_TENSOR
+                   : g_engine == ENGINE_TC5  ? DC_ENGINE_TCGEN05
+                                             : DC_ENGINE_AUTO;
     return DC_OK;
 }
 
@@ -650,7 +662,7 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
     const int warps = engine == ENGINE_DIRECT ? choose_warps(mode, sub[2], sub[1], sub[0]) : 1;
     const Layout L = make_layout(sz);
     // the staging image: the table regions [hdr, cdf), then the tensor-core unit tables
-    const size_t img_bytes = L.cdf + (engine == ENGINE_TC ? L.tca - L.tc_ufr : 0);
+    const size_t img_bytes = L.cdf + (keyed(engine) ? L.tca - L.tc_ufr : 0);
     if (size_only) {
         *size_only = img_bytes;
         return DC_OK;
@@ -673,7 +685,7 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
     int* upre = reinterpret_cast<int*>(img.data() + L.unit_pre);
     // the tensor-core unit tables follow in the workspace; they get a host image of their own
     const size_t tc_beg = L.tc_ufr, tc_end = L.tca;
-    std::vector<char> tcimg(engine == ENGINE_TC ? tc_end - tc_beg : 0, 0);
+    std::vector<char> tcimg(keyed(engine) ? tc_end - tc_beg : 0, 0);
     int* tufr = reinterpret_cast<int*>(tcimg.data() + (L.tc_ufr - tc_beg));
     int* turb = reinterpret_cast<int*>(tcimg.data() + (L.tc_urb - tc_beg));
     int* tupre = reinterpret_cast<int*>(tcimg.data() + (L.tc_upre - tc_beg));
@@ -715,7 +727,7 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
         d.unit0 = unit;
         d.tc_unit0 = tunit;
         fd[k] = d;
-        if (engine == ENGINE_TC) {
+        if (keyed(engine)) {
             // sim rows against the targets, then (Eq. 1) the targets against the sim points
             const int u0 = div_up(f.N, TC_UNIT_ROWS);
             const int u1 = mode == DC_BIDIR_MEAN ? div_up(f.M, TC_UNIT_ROWS) : 0;
@@ -749,7 +761,7 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
     rowpre[n_frames] = row0;
     colpre[n_frames] = col0;
     upre[unit] = subc;
-    if (engine == ENGINE_TC) tupre[tunit] = tchunk;
+    if (keyed(engine)) tupre[tunit] = tchunk;
     h->status = DC_OK;
     h->n_frames = n_frames;
     h->n_units = unit;
@@ -764,8 +776,8 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
     h->slices = (int)sz.slices;
     h->warps = warps;
     h->engine = engine;
-    h->tc_units = engine == ENGINE_TC ? tunit : 0;
-    h->tc_total = engine == ENGINE_TC ? tchunk : 0;
+    h->tc_units = keyed(engine) ? tunit : 0;
+    h->tc_total = keyed(engine) ? tchunk : 0;
     h->tc_fallback = 0;
     const char* src_img = img.data();
     const char* src_tc = tcimg.data();
@@ -791,8 +803,8 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
     p.n_units = unit;
     p.warps = warps;
     p.engine = engine;
-    p.tc_grid = engine == ENGINE_TC ? tc_grid(tchunk) : 0;
-    p.tc_units = engine == ENGINE_TC ? tunit : 0;
+    p.tc_grid = keyed(engine) ? keyed_grid(engine, tchunk) : 0;
+    p.tc_units = keyed(engine) ? tunit : 0;
     p.tc_chunks = tchunk;
     p.bytes = L.total;
     std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -816,13 +828,13 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream) {
     const Layout L = make_layout(p.sz);
     const Ws w = make_ws(ws, L);
     const int n = (int)p.sz.n_frames, rows = (int)p.sz.rows, cols = (int)p.sz.cols;
-    const bool tc = p.engine == ENGINE_TC;
+    const bool tc = keyed(p.engine);
     cudaError_t e = launch_reset(w, stream);
     if (!e) e = launch_area_cdf(w, n, stream);  // and the frame boxes
     if (!e) e = launch_stage(w, n, (int)p.sz.slices, p.max_f, rows, cols, 0, tc ? 1 : 0, stream);
     if (!e)
-        e = tc ? launch_tcpass(w, p.tc_grid, p.tc_chunks, p.tc_units, rows, cols, p.mode, n,
-                               stream)
+        e = tc ? launch_tcpass(w, p.engine, p.tc_grid, p.tc_chunks, p.tc_units, rows, cols,
+                               p.mode, n, stream)
                : launch_chamfer(w, p.n_units, p.total_sub, p.mode, p.warps, stream);
     if (!e)
         e = launch_epilogue(w, n, (int)p.sz.slices, p.any_grad ? p.max_v : 0, p.mode,

@@ -78,7 +78,12 @@ static_assert(ROW_PAD % TC_UNIT_ROWS == 0 && COL_PAD % TC_CHUNK == 0 &&
                   TC_CHUNK % TC_BLOCK == 0 && TC_ROWS_PER_WARP % 16 == 0,
               "the tensor-core tiles nest in the padded sizes");
 
-enum : int { ENGINE_AUTO = 0, ENGINE_DIRECT = 1, ENGINE_TC = 2 };
+// ENGINE_TC: the filter on warp-level MMAs; ENGINE_TC5: on tcgen05 MMAs into tensor memory.
+// Both write the same keys, which the same kernels merge and resolve.
+enum : int { ENGINE_AUTO = 0, ENGINE_DIRECT = 1, ENGINE_TC = 2, ENGINE_TC5 = 3 };
+__host__ __device__ inline bool keyed(int engine) {
+    return engine == ENGINE_TC || engine == ENGINE_TC5;
+}
 
 // (k1, k2, k3) stays the three smallest of the keys inserted
 __device__ __forceinline__ void top3_insert(unsigned& k1, unsigned& k2, unsigned& k3,
@@ -133,7 +138,7 @@ struct WsHeader {
     int max_v;        // largest V among frames with a gradient
     int slices;       // epilogue slices per frame
     int warps;        // warps per Chamfer CTA (units of warps * ROWS_PER_WARP sim points)
-    int engine;       // ENGINE_DIRECT or ENGINE_TC
+    int engine;       // ENGINE_DIRECT, ENGINE_TC or ENGINE_TC5
     int tc_units;     // tensor-core work units (frame, side, 512 rows)
     int tc_total;     // their chunks of TC_CHUNK columns (live frames only)
     int tc_fallback;  // rows whose keys certified no candidate set (scanned in full)
@@ -254,7 +259,7 @@ struct UniformArgs {
     const float* gframes;  // [T] nullable (backward only): dJ/dL_t directly
     int bwd;               // 1: gradient multipliers g_t = w_t gtotal + gframes[t]
     int T, V, F, N, M, mode, units_per_frame, subs_per_unit, slices, warps;
-    int engine;            // ENGINE_DIRECT or ENGINE_TC (set when the call has a Chamfer)
+    int engine;            // ENGINE_DIRECT, ENGINE_TC or ENGINE_TC5 (calls with a Chamfer)
 };
 
 cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t s);
@@ -277,8 +282,11 @@ cudaError_t launch_bbox(const Ws& w, int n_frames, cudaStream_t s);
 // of the keys of units split between CTAs (n_units: the units the call can have), then the
 // exact recovery of every row's minimum and neighbour from its keys into pab (and pba in
 // Eq. 1) as (distance bits << 32 | index)
-cudaError_t launch_tcpass(const Ws& w, int grid, long long total_chunks, int n_units,
-                          int rows, int cols, int mode, int n_frames, cudaStream_t s);
+cudaError_t launch_tcpass(const Ws& w, int engine, int grid, long long total_chunks,
+                          int n_units, int rows, int cols, int mode, int n_frames,
+                          cudaStream_t s);
+// CTAs of the tcgen05 pass (one per SM) for an upper bound of its chunk count
+int tc5_grid(long long total_chunks);
 // CTAs of the tensor-core pass for an upper bound of its chunk count
 int tc_grid(long long total_chunks);
 cudaError_t launch_chamfer(const Ws& w, int n_units, int total_sub, int mode, int warps,

@@ -233,7 +233,7 @@ __device__ void build_uniform(const UniformArgs& a, const Ws& w) {
         h->max_v = a.V;
         h->slices = a.slices;
         h->warps = a.warps;
-        h->engine = a.engine == ENGINE_TC ? ENGINE_TC : ENGINE_DIRECT;
+        h->engine = keyed(a.engine) ? a.engine : ENGINE_DIRECT;
         h->tc_units = 0;
         h->tc_total = 0;
         h->tc_fallback = 0;
@@ -256,7 +256,7 @@ __device__ void build_uniform(const UniformArgs& a, const Ws& w) {
     const int tu0 = div_up(a.N, TC_UNIT_ROWS);
     const int tu1 = a.mode == DC_BIDIR_MEAN ? div_up(a.M, TC_UNIT_ROWS) : 0;
     const int tupf = tu0 + tu1;
-    if (a.engine == ENGINE_TC) {
+    if (keyed(a.engine)) {
         const int c0 = Mpad / TC_CHUNK, c1 = Npad / TC_CHUNK;  // chunks per unit, by side
         const int per_frame = tu0 * c0 + tu1 * c1;
         const int n_tc = a.T * tupf;
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(CDF_THREADS) k_area_cdf(Ws w) {
     const AreaFrame af{fr->verts, fr->faces, fr->mask, fr->grad, w.cdf + fr->cdf0,
                        fr->F, fr->V, fr->skip != 0};
     area_cdf(af, &w.hdr->status);
-    if (w.hdr->engine == ENGINE_TC && !fr->skip)
+    if (keyed(w.hdr->engine) && !fr->skip)
         frame_box(fr->verts, fr->V, fr->tgt, fr->M, &w.fbox[blockIdx.x]);
 }
 
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(CDF_THREADS) k_build_area(UniformArgs a, Ws w)
     area_cdf(af, &s_err);
     __syncthreads();
     if (threadIdx.x == 0) w.frame_err[t] = s_err;
-    if (a.engine == ENGINE_TC && !af.skip)
+    if (keyed(a.engine) && !af.skip)
         frame_box(af.verts, a.V, a.tgt ? a.tgt + 3LL * t * a.M : nullptr, a.M, &w.fbox[t]);
 }
 

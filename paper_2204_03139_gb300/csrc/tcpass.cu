@@ -544,6 +544,337 @@ __global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// The same filter on the fifth-generation tensor cores: tcgen05 MMAs write the distances to
+// tensor memory asynchronously. A CTA holds a 512-row unit as four tiles of M = 128 rows, one
+// row per thread of 16 consumer warps (tile t is read by warps 4t .. 4t+3, one lane quarter
+// each). Each tile has two slots of 64 columns of tensor memory, one per half of a block of
+// TC_BLOCK columns, so tensor memory (4 tiles x 2 slots x 64 columns) is full. One MMA
+// (N = 64, K = 16) fills one slot; a warp reads its tile's two slots in turn, and a slot is
+// refilled with the same half of the next block as soon as its four warps have read it, by
+// one thread of one of those warps (the eight issuing threads spread over the four SM
+// sub-partitions). So each refill runs while the warps read the other slot. Each warp folds
+// the block into the four column subsets (2 of every 8) and their block keys exactly as the
+// warp-level kernel does, so the keys, their merge across CTAs and the recovery are shared.
+// One producer warp streams the column chunks with bulk copies.
+//
+// An MMA issues at a fixed cost of about as many cycles as an N = 128, K = 16 product takes,
+// whatever N up to 128; at N = 64 the tensor pipe still keeps ahead of the folds (one
+// three-input minimum per two distances, and the key inserts), which bound the pass.
+// ---------------------------------------------------------------------------------------
+constexpr int T5_CWARPS = 16;                          // consumer warps (one row per thread)
+constexpr int T5_THREADS = 32 * (T5_CWARPS + 1);       // and the producer warp
+constexpr int T5_N = 64;                               // columns per MMA: half a key block
+constexpr int T5_KB = TC_CHUNK / TC_BLOCK;             // key blocks per staged chunk
+constexpr int T5_BUFS = 4;                             // staged chunks
+constexpr int T5_TILES = TC_UNIT_ROWS / 128;           // tiles of M = 128 rows
+constexpr int T5_SLOTS = 2 * T5_TILES;                 // (tile, half block)
+constexpr uint32_t T5_TMEM_COLS = T5_SLOTS * T5_N;     // 512: all of an SM's tensor memory
+// MMAs that read one staged chunk: every slot, once per key block of the chunk
+constexpr int T5_CHUNK_READS = T5_SLOTS * T5_KB;
+// dynamic shared memory: the staged chunks, padded so that one CTA fills an SM (the CTA
+// allocates all of the SM's tensor memory)
+constexpr int T5_SMEM_B = T5_BUFS * TC_CHUNK * 32;     // 32 KB of staged chunks
+constexpr int T5_SMEM = 100 * 1024;
+static_assert(TC_BLOCK == 2 * T5_N && T5_KB == 2 && T5_TILES == 4 && T5_TMEM_COLS == 512,
+              "two MMAs per key block, two key blocks per chunk, tensor memory full");
+static_assert(T5_SMEM_B <= T5_SMEM, "dynamic shared memory");
+
+// shared-memory matrix descriptor of a K-major operand without swizzle, as the staging lays
+// it out: core matrices of 8 rows x 16 bytes, 128 bytes between the two halves of K (the
+// leading dimension), 256 bytes between groups of 8 rows; descriptor version 1
+__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: f16 A and B, f32 D, both K-major, M = 128, N = T5_N
+constexpr uint32_t T5_IDESC = (1u << 4) | ((uint32_t)(T5_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void t5_mma(uint32_t d_tmem, uint64_t ad, uint64_t bd) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(T5_IDESC), "r"(0)
+        : "memory");
+}
+__device__ __forceinline__ void t5_commit(u64* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void t5_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void t5_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(u64* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 32 consecutive columns of the 32 tensor-memory lanes of this warp, one row per lane
+__device__ __forceinline__ void t5_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// fold 32 columns (four groups of 8) into the four column subsets' running minima; subset t
+// holds the columns 8 g + 2 t and 8 g + 2 t + 1 of every group g
+__device__ __forceinline__ void t5_fold(const float (&v)[32], float (&bm)[4], bool first) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        float m = first ? fminf(v[2 * t], v[2 * t + 1]) : min3(bm[t], v[2 * t], v[2 * t + 1]);
+#pragma unroll
+        for (int g = 1; g < 4; ++g) m = min3(m, v[8 * g + 2 * t], v[8 * g + 2 * t + 1]);
+        bm[t] = m;
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive_n(u64* bar, uint32_t n) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
+    pdl_entry();
+    __shared__ __align__(1024) uint4 s_a[TC_UNIT_ROWS * 2];  // A forms of the unit, 16 KB
+    extern __shared__ __align__(1024) uint4 t5_dyn[];
+    uint4* const s_b = t5_dyn;                                // T5_BUFS chunks of B forms
+    // s_bar_b: a chunk landed; s_cfree: the MMAs that read a chunk are complete;
+    // s_full: a slot's MMA is complete; s_free: a slot's four warps have read it
+    __shared__ __align__(8) u64 s_bar_a, s_bar_b[T5_BUFS], s_cfree[T5_BUFS], s_full[T5_SLOTS],
+        s_free[T5_SLOTS], s_drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ TcSeg s_u;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool producer = warp == T5_CWARPS;
+    const int n_units = w.hdr->tc_units, total = w.hdr->tc_total;
+    const int per = (total + gridDim.x - 1) / gridDim.x;
+    int s = blockIdx.x * per;
+    const int s_end = min(total, s + per);
+    if (s >= s_end) return;
+    int u = last_le(w.tc_upre, n_units, s);
+    const long long tot_rows = w.hdr->total_rows;
+
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(&s_tmem)),
+            "r"(T5_TMEM_COLS)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&s_bar_a, 1);
+        mbar_init(&s_drain, T5_SLOTS);  // the eight issuing threads
+        for (int i = 0; i < T5_BUFS; ++i) {
+            mbar_init(&s_bar_b[i], 1);
+            mbar_init(&s_cfree[i], T5_CHUNK_READS);
+        }
+        for (int i = 0; i < T5_SLOTS; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_free[i], 4);  // the four warps that read the slot
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    t5_fence_before();
+    __syncthreads();
+    t5_fence_after();
+    const uint32_t tmem = s_tmem;
+    // consumer warp: tile and lane quarter; slot (tile, hb) holds tensor-memory columns
+    // 64 (2 tile + hb) .., and its MMAs are issued by the warp of lane quarter (tile + 2 hb) % 4
+    const int quarter = warp & 3, tile = (warp >> 2) & 3;
+    const int my_hb = ((quarter - tile) & 3) >> 1;  // the half block whose slot this warp issues
+    const bool issuer = !producer && ((quarter - tile) & 1) == 0 && lane == 0;
+    const int my_slot = 2 * tile + my_hb;
+
+    int uses0 = 0, uses1 = 0;  // consumer: blocks read from its two slots (barrier phases)
+    uint32_t pend_b = 0;       // producer: buffers with a copy in flight
+    uint32_t pend_p = 0;       // and the phase that copy completes
+    long long chunk0 = 0;      // chunks staged before this segment (buffer of chunk k: k % 4)
+    int n_seg = 0;             // segments begun (phase of the A barrier)
+    bool abort = false, issued = false;
+
+    while (s < s_end && !abort) {
+        __syncthreads();  // the previous segment is done with s_u and s_a
+        if (producer && lane == 0) {
+            const FrameDesc* fr = w.frames + w.tc_ufr[u];
+            const int urb = w.tc_urb[u];
+            const int side = urb >> 30, rb = urb & 0x3fffffff;
+            const int upre = w.tc_upre[u], unext = w.tc_upre[u + 1];
+            const long long first = (long long)rb * TC_UNIT_ROWS;
+            s_u.rows_live = (side ? fr->Mpad : fr->Npad) - (int)first;
+            s_u.arow = (side ? tot_rows + fr->col0 : (long long)fr->row0) + first;
+            s_u.bcol = side ? (long long)fr->row0 : tot_rows + fr->col0;
+            s_u.kout = side ? w.kba + TC_KEYS * ((long long)fr->col0 + first)
+                            : w.kab + TC_KEYS * ((long long)fr->row0 + first);
+            s_u.c_lo = s - upre;
+            s_u.c_hi = min(s_end, unext) - upre - 1;
+            s_u.whole = s == upre && s_end >= unext;
+            s_u.slot = s > upre ? 0 : 1;
+            // the unit's A forms (its rows that exist; a multiple of 256 rows)
+            const uint32_t abytes = (uint32_t)min(TC_UNIT_ROWS, s_u.rows_live) * 32u;
+            mbar_expect_tx(&s_bar_a, abytes);
+            bulk_g2s(&s_a[0], w.tca + 2 * s_u.arow, abytes, &s_bar_a);
+        }
+        __syncthreads();
+        const int c_lo = s_u.c_lo, c_hi = s_u.c_hi;
+        const int ntiles = min(T5_TILES, s_u.rows_live / 128);  // 2 or 4
+        const int nkb = (c_hi - c_lo + 1) * T5_KB;
+
+        if (producer) {
+            if (lane == 0) {
+                // stream the segment's chunks; chunk k reuses the buffer of chunk k - 4 once
+                // the MMAs that read that one are complete
+                for (int c = c_lo; c <= c_hi; ++c) {
+                    const long long k = chunk0 + (c - c_lo);
+                    const int b = (int)(k & (T5_BUFS - 1));
+                    if (k >= T5_BUFS &&
+                        !mbar_wait(&s_cfree[b], (uint32_t)(((k >> 2) - 1) & 1))) {
+                        abort = true;
+                        break;
+                    }
+                    if (stall && k == 0) continue;  // test of the bounded waits only
+                    mbar_expect_tx(&s_bar_b[b], TC_CHUNK * 32);
+                    bulk_g2s(s_b + b * (TC_CHUNK * 2),
+                             w.tcb + 2 * (s_u.bcol + (long long)c * TC_CHUNK), TC_CHUNK * 32,
+                             &s_bar_b[b]);
+                    pend_b |= 1u << b;
+                    pend_p = (pend_p & ~(1u << b)) | ((uint32_t)((k >> 2) & 1) << b);
+                }
+            }
+        } else if (tile < ntiles) {
+            const uint64_t a_desc = t5_desc(smem_u32(&s_a[0]) + (uint32_t)(tile * 4096));
+            // with two tiles live, each live slot's MMA stands for two slots' reads of a chunk
+            const uint32_t reads = (uint32_t)(T5_TILES / ntiles);
+            // issuing thread: the MMA of half my_hb of key block kb, once its chunk landed
+            auto issue = [&](int kb) -> bool {
+                const long long k = chunk0 + kb / T5_KB;
+                const int b = (int)(k & (T5_BUFS - 1));
+                if (!mbar_wait(&s_bar_b[b], (uint32_t)((k >> 2) & 1))) return false;
+                t5_fence_after();
+                const uint32_t off = (uint32_t)(((kb % T5_KB) * TC_BLOCK + my_hb * T5_N) * 32);
+                t5_mma(tmem + (uint32_t)(my_slot * T5_N), a_desc,
+                       t5_desc(smem_u32(s_b + b * (TC_CHUNK * 2)) + off));
+                t5_commit(&s_full[my_slot]);
+                issued = true;
+                return true;
+            };
+            bool ok = true;
+            if (issuer) ok = mbar_wait(&s_bar_a, (uint32_t)(n_seg & 1)) && issue(0);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            float bm[4];
+            unsigned k1[4], k2[4], k3[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) k1[t] = k2[t] = k3[t] = TC_EMPTY;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+            for (int kb = 0; ok && kb < nkb; ++kb) {
+#pragma unroll
+                for (int hb = 0; hb < 2; ++hb) {
+                    const int slot = 2 * tile + hb;
+                    const int uses = hb ? uses1 : uses0;
+                    if (!__all_sync(0xffffffffu,
+                                    mbar_wait(&s_full[slot], (uint32_t)(uses & 1)))) {
+                        ok = false;
+                        break;
+                    }
+                    t5_fence_after();
+                    float v[32];
+                    t5_ld32(taddr + (uint32_t)(slot * T5_N), v);
+                    t5_fold(v, bm, hb == 0);
+                    t5_ld32(taddr + (uint32_t)(slot * T5_N + 32), v);
+                    // the slot is read: release it to its next MMA, then fold
+                    t5_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&s_free[slot]);
+                    t5_fold(v, bm, false);
+                    if (issuer && hb == my_hb) {
+                        // this slot's MMA is complete: its chunk has fewer readers left;
+                        // once the slot's four warps have read it, its next block
+                        mbar_arrive_n(&s_cfree[(int)((chunk0 + kb / T5_KB) & (T5_BUFS - 1))],
+                                      reads);
+                        ok = mbar_wait(&s_free[slot], (uint32_t)(uses & 1));
+                        if (ok && kb + 1 < nkb) ok = issue(kb + 1);
+                    }
+                    if (hb) ++uses1; else ++uses0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) break;
+                }
+                if (!ok) break;
+                // the block's keys: value clamped at 0 and truncated, with the block (the
+                // subset is implied by the key's slot)
+                const unsigned id = (unsigned)(c_lo * T5_KB + kb);
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    top3_insert(k1[t], k2[t], k3[t],
+                                (__float_as_uint(fmaxf(bm[t], 0.0f)) & TC_VALUE_MASK) | id);
+            }
+            abort = !ok;
+            if (ok) {
+                unsigned* out =
+                    s_u.whole ? s_u.kout
+                              : w.kpart + TC_KEYS * ((2LL * blockIdx.x + s_u.slot) * TC_UNIT_ROWS);
+                unsigned* o = out + TC_KEYS * (tile * 128 + quarter * 32 + lane);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    o[3 * t] = k1[t];
+                    o[3 * t + 1] = k2[t];
+                    o[3 * t + 2] = k3[t];
+                }
+            }
+        }
+        // a wait that gave up anywhere ends the CTA's work (every other wait then gives up
+        // too, since no further MMA is issued or read, so every warp gets here)
+        abort = __syncthreads_or(abort) != 0;
+        if (abort) break;
+        // every copy of the segment has landed: each was waited for before its MMAs
+        pend_b = 0;
+        chunk0 += c_hi - c_lo + 1;
+        ++n_seg;
+        s = min(s_end, w.tc_upre[u + 1]);
+        ++u;
+    }
+
+    if (abort) {
+        if (tid == 0) set_status(&w.hdr->status, DC_ETIMEOUT);
+        // let the MMAs and copies still in flight finish before the CTA's tensor memory and
+        // shared memory go away
+        if (issuer) {
+            if (issued)
+                t5_commit(&s_drain);
+            else
+                mbar_arrive(&s_drain);
+        }
+        if (producer && lane == 0) {
+            (void)mbar_wait(&s_drain, 0u);
+            for (int b = 0; b < T5_BUFS; ++b)
+                if (pend_b & (1u << b)) (void)mbar_wait(&s_bar_b[b], (pend_p >> b) & 1u);
+        }
+    }
+    t5_fence_before();
+    __syncthreads();
+    t5_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(T5_TMEM_COLS)
+                     : "memory");
+}
+
 int g_tc_ctas[64];  // per device: resident CTAs of the persistent grid
 
 }  // namespace
@@ -569,11 +900,38 @@ int tc_grid(long long total_chunks) {
     return (int)(g < 1 ? 1 : g);
 }
 
-cudaError_t launch_tcpass(const Ws& w, int grid, long long total_chunks, int n_units,
-                          int rows, int cols, int mode, int n_frames, cudaStream_t s) {
+int g_t5_smem_set[64];
+
+int tc5_grid(long long total_chunks) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0) {
+        cudaGetLastError();
+        sms = TC_MAX_GRID;
+    }
+    const long long g = total_chunks < sms ? total_chunks : sms;
+    return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_tcpass(const Ws& w, int engine, int grid, long long total_chunks,
+                          int n_units, int rows, int cols, int mode, int n_frames,
+                          cudaStream_t s) {
     const int stall = take_stall();
+    cudaError_t e = cudaSuccess;
+    if (engine == ENGINE_TC5) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !g_t5_smem_set[dev]) {
+            e = cudaFuncSetAttribute(k_tcpass5, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     T5_SMEM);
+            if (e) return e;
+            g_t5_smem_set[dev] = 1;
+        }
+    }
     prof_before(s);
-    cudaError_t e = launch_pdl(k_tcpass, grid, TC_THREADS, 0, s, w, stall);
+    e = engine == ENGINE_TC5 ? launch_pdl(k_tcpass5, grid, T5_THREADS, T5_SMEM, s, w, stall)
+                             : launch_pdl(k_tcpass, grid, TC_THREADS, 0, s, w, stall);
     prof_after(s);
     count_launch();
     if (e) return e;

@@ -105,6 +105,37 @@ def test_batch_equals_per_frame_form(trajs):
         assert parity.rel_l2(b.grad_verts[k].cpu().numpy(), gv[k].cpu().numpy()) < 1e-6
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_engines_agree(trajs, mode):
+    """One batch plan per engine (warp-level MMA filter, tcgen05 filter, direct form): the
+    neighbours and per-frame losses agree bit for bit, gradients to float rounding of the
+    scatter order, and the tcgen05 plan matches the oracle."""
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
+
+    dts = [DeviceTrajectory.from_host(t, DEV) for t in trajs]
+    outs = {}
+    for sh in (("tensor", 0), ("tcgen05", 0), ("direct", 2)):
+        b = BatchedLoss(dts, mode=mode, grad=True, graph=True, nn=True, shape=sh)
+        b.run(check=True)
+        torch.cuda.synchronize()
+        outs[sh[0]] = b
+    ref = outs["direct"]
+    for eng in ("tensor", "tcgen05"):
+        b = outs[eng]
+        for k in range(len(dts)):
+            np.testing.assert_array_equal(b.loss_frames[k].cpu().numpy(),
+                                          ref.loss_frames[k].cpu().numpy())
+            np.testing.assert_array_equal(b.nn_ab[k].cpu().numpy(), ref.nn_ab[k].cpu().numpy())
+            if mode == 0:
+                np.testing.assert_array_equal(b.nn_ba[k].cpu().numpy(),
+                                              ref.nn_ba[k].cpu().numpy())
+            assert parity.rel_l2(b.grad_verts[k].cpu().numpy(),
+                                 ref.grad_verts[k].cpu().numpy()) < 1e-6
+    for k, t in enumerate(trajs):
+        o = oracle.loss_traj(t, mode=mode)
+        parity.check_loss(outs["tcgen05"].loss_frames[k].cpu().numpy(), o["loss_frames"])
+
+
 @pytest.mark.slow
 def test_batched_uneven_full_size_sampled_frames():
     """All 64 trajectories of the uneven workload (grids 15x15..80x80, 20..100 frames, 2 000 to

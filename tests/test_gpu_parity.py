@@ -152,19 +152,24 @@ def test_exact_ties_go_to_the_lowest_index(mode):
 # failure detection without a GPU fault
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.timeout(120)
-def test_bounded_wait_gives_up_with_a_timeout_status_and_the_device_stays_usable():
-    """The Chamfer kernel's waits for its target chunks are bounded (2 s). A launch whose
-    first chunk is never requested must end with DC_ETIMEOUT in the workspace status, and the
-    next call on the same context must produce the normal result."""
+@pytest.mark.parametrize("shape", [None, ("tcgen05", 0), ("direct", 2)])
+def test_bounded_wait_gives_up_with_a_timeout_status_and_the_device_stays_usable(shape):
+    """The Chamfer kernels' waits for their target chunks (and, on the tcgen05 engine, for
+    the MMAs and the reading warps) are bounded (2 s). A launch whose first chunk is never
+    requested must end with DC_ETIMEOUT in the workspace status, and the next call on the same
+    context must produce the normal result; for the default engine and both others."""
+    from paper_2204_03139_gb300 import autotune
+
     tr = parity.nudged(W.trajectory_50x50(T=2, n=2000, m=2000))
     v, f, d, y = to_dev(tr)
-    good = L().dc_loss_traj(v, f, d, y, check=True)
-    ref_loss = good["loss_frames"].cpu().numpy().copy()
-    L().test_inject_stall()
-    with pytest.raises(L().DCError) as e:
-        L().dc_loss_traj(v, f, d, y, check=True)
-    assert e.value.code == L().DC_ETIMEOUT
-    again = L().dc_loss_traj(v, f, d, y, check=True)
+    with autotune.tuned(shape):
+        good = L().dc_loss_traj(v, f, d, y, check=True)
+        ref_loss = good["loss_frames"].cpu().numpy().copy()
+        L().test_inject_stall()
+        with pytest.raises(L().DCError) as e:
+            L().dc_loss_traj(v, f, d, y, check=True)
+        assert e.value.code == L().DC_ETIMEOUT
+        again = L().dc_loss_traj(v, f, d, y, check=True)
     np.testing.assert_array_equal(again["loss_frames"].cpu().numpy(), ref_loss)
 
 
@@ -596,11 +601,11 @@ def test_every_cta_width_gives_identical_results(shape):
 
 @pytest.mark.parametrize("case", ["traj", "ragged", "ties", "grid", "outliers", "eq2"])
 def test_engines_give_identical_results(case):
-    """The tensor-core filter and the direct engine decide every neighbour in the same
-    float32 direct form, so neighbours, per-frame losses and totals agree bit for bit; the
-    cases cover uniform trajectories, ragged tails of every tile, exact ties in many blocks
-    (every row falls back to a full scan), a regular grid (equidistant neighbours), far
-    outliers and Eq. 2."""
+    """The tensor-core filter (on warp-level MMAs and on tcgen05 MMAs) and the direct engine
+    decide every neighbour in the same float32 direct form, so neighbours, per-frame losses
+    and totals agree bit for bit; the cases cover uniform trajectories, ragged tails of every
+    tile, exact ties in many blocks (every row falls back to a full scan), a regular grid
+    (equidistant neighbours), far outliers and Eq. 2."""
     from paper_2204_03139_gb300 import autotune
 
     mode = 1 if case == "eq2" else 0
@@ -615,14 +620,15 @@ def test_engines_give_identical_results(case):
     if tr is not None:
         v, f, d, y = to_dev(tr)
         outs = {}
-        for sh in (("tensor", 0), ("direct", 2)):
+        for sh in (("tensor", 0), ("tcgen05", 0), ("direct", 2)):
             with autotune.tuned(sh):
                 r = L().dc_loss_traj(v, f, d, y, mode=mode, check=True)
             torch.cuda.synchronize()
             outs[sh[0]] = {k: x.cpu().numpy() for k, x in r.items() if x is not None}
-        for k in ("loss_frames", "loss_total", "nn_ab") + (("nn_ba",) if mode == 0 else ()):
-            np.testing.assert_array_equal(outs["tensor"][k], outs["direct"][k])
-        assert parity.rel_l2(outs["tensor"]["grad_verts"], outs["direct"]["grad_verts"]) < 1e-6
+        for eng in ("tensor", "tcgen05"):
+            for k in ("loss_frames", "loss_total", "nn_ab") + (("nn_ba",) if mode == 0 else ()):
+                np.testing.assert_array_equal(outs[eng][k], outs["direct"][k])
+            assert parity.rel_l2(outs[eng]["grad_verts"], outs["direct"]["grad_verts"]) < 1e-6
         return
     if case == "ties":
         rng = np.random.default_rng(3)
@@ -637,7 +643,7 @@ def test_engines_give_identical_results(case):
     A = torch.from_numpy(a[None]).to(DEV)
     B = torch.from_numpy(b[None]).to(DEV)
     ref = oracle.nn_pair(a, b)
-    for sh in (("tensor", 0), ("direct", 1)):
+    for sh in (("tensor", 0), ("tcgen05", 0), ("direct", 1)):
         with autotune.tuned(sh):
             loss, nab, nba = L().dc_chamfer_fwd(A, B, check=True)
         np.testing.assert_array_equal(nab[0].cpu().numpy(), ref["nn_ab"])
