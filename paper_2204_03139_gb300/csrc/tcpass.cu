@@ -550,20 +550,21 @@ __global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows) {
 // row per thread of 16 consumer warps (tile t is read by warps 4t .. 4t+3, one lane quarter
 // each). Each tile has two slots of 64 columns of tensor memory, one per half of a block of
 // TC_BLOCK columns, so tensor memory (4 tiles x 2 slots x 64 columns) is full. One MMA
-// (N = 64, K = 16) fills one slot; a warp reads its tile's two slots in turn, and a slot is
-// refilled with the same half of the next block as soon as its four warps have read it, by
-// one thread of one of those warps (the eight issuing threads spread over the four SM
-// sub-partitions). So each refill runs while the warps read the other slot. Each warp folds
-// the block into the four column subsets (2 of every 8) and their block keys exactly as the
-// warp-level kernel does, so the keys, their merge across CTAs and the recovery are shared.
-// One producer warp streams the column chunks with bulk copies.
+// (N = 64, K = 16) fills one slot; a consumer warp reads its tile's two slots in turn, so a
+// slot's refill runs while the warp reads the other one. Each warp folds the block into the
+// four column subsets (2 of every 8) and their block keys exactly as the warp-level kernel
+// does, so the keys, their merge across CTAs and the recovery are shared.
 //
-// An MMA issues at a fixed cost of about as many cycles as an N = 128, K = 16 product takes,
-// whatever N up to 128; at N = 64 the tensor pipe still keeps ahead of the folds (one
-// three-input minimum per two distances, and the key inserts), which bound the pass.
+// The MMAs are issued by four more warps, one per SM sub-partition, each for two slots: its
+// thread polls both slots (and the first also streams the column chunks with bulk copies)
+// and issues whichever slot its readers have released, so no consumer warp ever waits on an
+// issue and no slot waits behind another. An isolated tcgen05 MMA occupies its issuing thread
+// for a few hundred cycles, at K = 16 as long as the product itself takes, which is why the
+// issue has threads of its own.
 // ---------------------------------------------------------------------------------------
 constexpr int T5_CWARPS = 16;                          // consumer warps (one row per thread)
-constexpr int T5_THREADS = 32 * (T5_CWARPS + 1);       // and the producer warp
+constexpr int T5_MWARPS = 4;                           // MMA-issuing warps
+constexpr int T5_THREADS = 32 * (T5_CWARPS + T5_MWARPS);
 constexpr int T5_N = 64;                               // columns per MMA: half a key block
 constexpr int T5_KB = TC_CHUNK / TC_BLOCK;             // key blocks per staged chunk
 constexpr int T5_BUFS = 4;                             // staged chunks
@@ -579,6 +580,8 @@ constexpr int T5_SMEM = 100 * 1024;
 static_assert(TC_BLOCK == 2 * T5_N && T5_KB == 2 && T5_TILES == 4 && T5_TMEM_COLS == 512,
               "two MMAs per key block, two key blocks per chunk, tensor memory full");
 static_assert(T5_SMEM_B <= T5_SMEM, "dynamic shared memory");
+static_assert(T5_THREADS % 128 == 0, "whole warps per sub-partition");
+constexpr unsigned T5_POLL_NS = 40;  // back-off of an issuing thread that found nothing to do
 
 // shared-memory matrix descriptor of a K-major operand without swizzle, as the staging lays
 // it out: core matrices of 8 rows x 16 bytes, 128 bytes between the two halves of K (the
@@ -648,6 +651,21 @@ __device__ __forceinline__ void mbar_arrive_n(u64* bar, uint32_t n) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n)
                  : "memory");
 }
+// non-blocking test of phase `parity`
+__device__ __forceinline__ bool mbar_test(u64* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// slot (tile, hb) of the MMA warp m, i = 0, 1: the first half block of tile m, the second of
+// tile m + 2 (mod 4); the consumer warp of lane quarter m of that tile reports its chunk reads
+__device__ __forceinline__ int t5_slot_of(int m, int i) { return i == 0 ? 2 * m : 2 * ((m + 2) & 3) + 1; }
 
 __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
     pdl_entry();
@@ -662,7 +680,10 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
     __shared__ TcSeg s_u;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool producer = warp == T5_CWARPS;
+    const bool mwarp = warp >= T5_CWARPS;
+    const int m = warp - T5_CWARPS;            // MMA warp index (sub-partition), if mwarp
+    const bool mt = mwarp && lane == 0;        // an issuing thread
+    const bool stager = mt && m == 0;          // the thread that also streams the chunks
     const int n_units = w.hdr->tc_units, total = w.hdr->tc_total;
     const int per = (total + gridDim.x - 1) / gridDim.x;
     int s = blockIdx.x * per;
@@ -681,7 +702,7 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
     }
     if (tid == 0) {
         mbar_init(&s_bar_a, 1);
-        mbar_init(&s_drain, T5_SLOTS);  // the eight issuing threads
+        mbar_init(&s_drain, T5_MWARPS);  // the four issuing threads
         for (int i = 0; i < T5_BUFS; ++i) {
             mbar_init(&s_bar_b[i], 1);
             mbar_init(&s_cfree[i], T5_CHUNK_READS);
@@ -697,22 +718,23 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
     t5_fence_after();
     const uint32_t tmem = s_tmem;
     // consumer warp: tile and lane quarter; slot (tile, hb) holds tensor-memory columns
-    // 64 (2 tile + hb) .., and its MMAs are issued by the warp of lane quarter (tile + 2 hb) % 4
+    // 64 (2 tile + hb) ..; the warp of lane quarter (tile + 2 hb) % 4 reports the chunk reads
+    // of that slot's MMAs
     const int quarter = warp & 3, tile = (warp >> 2) & 3;
-    const int my_hb = ((quarter - tile) & 3) >> 1;  // the half block whose slot this warp issues
-    const bool issuer = !producer && ((quarter - tile) & 1) == 0 && lane == 0;
-    const int my_slot = 2 * tile + my_hb;
+    const int rep_hb = ((quarter - tile) & 3) >> 1;
+    const bool reporter = !mwarp && ((quarter - tile) & 1) == 0 && lane == 0;
 
-    int uses0 = 0, uses1 = 0;  // consumer: blocks read from its two slots (barrier phases)
-    uint32_t pend_b = 0;       // producer: buffers with a copy in flight
-    uint32_t pend_p = 0;       // and the phase that copy completes
-    long long chunk0 = 0;      // chunks staged before this segment (buffer of chunk k: k % 4)
-    int n_seg = 0;             // segments begun (phase of the A barrier)
+    int uses0 = 0, uses1 = 0;    // consumer: blocks read from its two slots (barrier phases)
+    int nis0 = 0, nis1 = 0;      // issuing thread: MMAs issued into its two slots
+    uint32_t pend_b = 0;         // stager: buffers with a copy in flight
+    uint32_t pend_p = 0;         // and the phase that copy completes
+    long long chunk0 = 0;        // chunks staged before this segment (buffer of chunk k: k % 4)
+    int n_seg = 0;               // segments begun (phase of the A barrier)
     bool abort = false, issued = false;
 
     while (s < s_end && !abort) {
         __syncthreads();  // the previous segment is done with s_u and s_a
-        if (producer && lane == 0) {
+        if (stager) {
             const FrameDesc* fr = w.frames + w.tc_ufr[u];
             const int urb = w.tc_urb[u];
             const int side = urb >> 30, rb = urb & 0x3fffffff;
@@ -737,47 +759,80 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
         const int ntiles = min(T5_TILES, s_u.rows_live / 128);  // 2 or 4
         const int nkb = (c_hi - c_lo + 1) * T5_KB;
 
-        if (producer) {
-            if (lane == 0) {
-                // stream the segment's chunks; chunk k reuses the buffer of chunk k - 4 once
-                // the MMAs that read that one are complete
-                for (int c = c_lo; c <= c_hi; ++c) {
-                    const long long k = chunk0 + (c - c_lo);
+        if (mt) {
+            // per own slot: the next key block to issue (nkb when done, or when its tile has
+            // no rows in this unit)
+            int next[2];
+            const int sl[2] = {t5_slot_of(m, 0), t5_slot_of(m, 1)};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) next[i] = (sl[i] >> 1) < ntiles ? 0 : nkb;
+            int cnext = stager ? c_lo : c_hi + 1;  // next chunk to stage
+            bool a_ready = false;
+            u64 t_last = globaltimer();
+            int spins = 0;
+            while (next[0] < nkb || next[1] < nkb || cnext <= c_hi) {
+                bool progress = false;
+                if (cnext <= c_hi) {
+                    // chunk k reuses the buffer of chunk k - 4 once the MMAs that read that
+                    // one are complete
+                    const long long k = chunk0 + (cnext - c_lo);
                     const int b = (int)(k & (T5_BUFS - 1));
-                    if (k >= T5_BUFS &&
-                        !mbar_wait(&s_cfree[b], (uint32_t)(((k >> 2) - 1) & 1))) {
+                    if (k < T5_BUFS || mbar_test(&s_cfree[b], (uint32_t)(((k >> 2) - 1) & 1))) {
+                        if (!(stall && k == 0)) {  // test of the bounded waits only
+                            mbar_expect_tx(&s_bar_b[b], TC_CHUNK * 32);
+                            bulk_g2s(s_b + b * (TC_CHUNK * 2),
+                                     w.tcb + 2 * (s_u.bcol + (long long)cnext * TC_CHUNK),
+                                     TC_CHUNK * 32, &s_bar_b[b]);
+                            pend_b |= 1u << b;
+                            pend_p = (pend_p & ~(1u << b)) | ((uint32_t)((k >> 2) & 1) << b);
+                        }
+                        ++cnext;
+                        progress = true;
+                    }
+                }
+                if (!a_ready) a_ready = mbar_test(&s_bar_a, (uint32_t)(n_seg & 1));
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (!a_ready || next[i] >= nkb) continue;
+                    const int slot = sl[i];
+                    const int nis = i ? nis1 : nis0;
+                    // the slot's previous block has been read by its four warps
+                    if (nis > 0 && !mbar_test(&s_free[slot], (uint32_t)((nis - 1) & 1))) continue;
+                    const int kb = next[i];
+                    const long long k = chunk0 + kb / T5_KB;
+                    const int b = (int)(k & (T5_BUFS - 1));
+                    if (!mbar_test(&s_bar_b[b], (uint32_t)((k >> 2) & 1))) continue;
+                    t5_fence_after();
+                    const uint32_t off =
+                        (uint32_t)(((kb % T5_KB) * TC_BLOCK + (slot & 1) * T5_N) * 32);
+                    t5_mma(tmem + (uint32_t)(slot * T5_N),
+                           t5_desc(smem_u32(&s_a[0]) + (uint32_t)((slot >> 1) * 4096)),
+                           t5_desc(smem_u32(s_b + b * (TC_CHUNK * 2)) + off));
+                    t5_commit(&s_full[slot]);
+                    issued = true;
+                    if (i) ++nis1; else ++nis0;
+                    ++next[i];
+                    progress = true;
+                }
+                if (progress) {
+                    spins = 0;
+                    t_last = globaltimer();
+                    continue;
+                }
+                // nothing to do yet: leave the issue slots to the consumer warps for a while
+                __nanosleep(T5_POLL_NS);
+                if (++spins >= 64) {
+                    spins = 0;
+                    if (globaltimer() - t_last > WAIT_LIMIT_NS) {
                         abort = true;
                         break;
                     }
-                    if (stall && k == 0) continue;  // test of the bounded waits only
-                    mbar_expect_tx(&s_bar_b[b], TC_CHUNK * 32);
-                    bulk_g2s(s_b + b * (TC_CHUNK * 2),
-                             w.tcb + 2 * (s_u.bcol + (long long)c * TC_CHUNK), TC_CHUNK * 32,
-                             &s_bar_b[b]);
-                    pend_b |= 1u << b;
-                    pend_p = (pend_p & ~(1u << b)) | ((uint32_t)((k >> 2) & 1) << b);
                 }
             }
-        } else if (tile < ntiles) {
-            const uint64_t a_desc = t5_desc(smem_u32(&s_a[0]) + (uint32_t)(tile * 4096));
+        } else if (!mwarp && tile < ntiles) {
             // with two tiles live, each live slot's MMA stands for two slots' reads of a chunk
             const uint32_t reads = (uint32_t)(T5_TILES / ntiles);
-            // issuing thread: the MMA of half my_hb of key block kb, once its chunk landed
-            auto issue = [&](int kb) -> bool {
-                const long long k = chunk0 + kb / T5_KB;
-                const int b = (int)(k & (T5_BUFS - 1));
-                if (!mbar_wait(&s_bar_b[b], (uint32_t)((k >> 2) & 1))) return false;
-                t5_fence_after();
-                const uint32_t off = (uint32_t)(((kb % T5_KB) * TC_BLOCK + my_hb * T5_N) * 32);
-                t5_mma(tmem + (uint32_t)(my_slot * T5_N), a_desc,
-                       t5_desc(smem_u32(s_b + b * (TC_CHUNK * 2)) + off));
-                t5_commit(&s_full[my_slot]);
-                issued = true;
-                return true;
-            };
             bool ok = true;
-            if (issuer) ok = mbar_wait(&s_bar_a, (uint32_t)(n_seg & 1)) && issue(0);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
             float bm[4];
             unsigned k1[4], k2[4], k3[4];
 #pragma unroll
@@ -802,18 +857,12 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
                     t5_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&s_free[slot]);
-                    t5_fold(v, bm, false);
-                    if (issuer && hb == my_hb) {
-                        // this slot's MMA is complete: its chunk has fewer readers left;
-                        // once the slot's four warps have read it, its next block
+                    // this slot's MMA is complete: its chunk has fewer readers left
+                    if (reporter && hb == rep_hb)
                         mbar_arrive_n(&s_cfree[(int)((chunk0 + kb / T5_KB) & (T5_BUFS - 1))],
                                       reads);
-                        ok = mbar_wait(&s_free[slot], (uint32_t)(uses & 1));
-                        if (ok && kb + 1 < nkb) ok = issue(kb + 1);
-                    }
+                    t5_fold(v, bm, false);
                     if (hb) ++uses1; else ++uses0;
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok) break;
                 }
                 if (!ok) break;
                 // the block's keys: value clamped at 0 and truncated, with the block (the
@@ -854,13 +903,13 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
         if (tid == 0) set_status(&w.hdr->status, DC_ETIMEOUT);
         // let the MMAs and copies still in flight finish before the CTA's tensor memory and
         // shared memory go away
-        if (issuer) {
+        if (mt) {
             if (issued)
                 t5_commit(&s_drain);
             else
                 mbar_arrive(&s_drain);
         }
-        if (producer && lane == 0) {
+        if (stager) {
             (void)mbar_wait(&s_drain, 0u);
             for (int b = 0; b < T5_BUFS; ++b)
                 if (pend_b & (1u << b)) (void)mbar_wait(&s_bar_b[b], (pend_p >> b) & 1u);
