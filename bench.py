@@ -44,6 +44,15 @@ CHAMFER_TRAFFIC_BYTES = {("trajectory_50x50", "k_chamfer<true>", "eq1"): 22.79e6
                          ("trajectory_50x50", "k_chamfer<false>", "eq2"): 19.57e6}
 
 
+def measured_peaks():
+    """The generated peak measurements of this machine's GPUs, if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -68,6 +77,12 @@ def parse():
                    help="batched_uneven: only its first K trajectories (a small case for ncu)")
     p.add_argument("--frames", type=int, default=None,
                    help="use only the first FRAMES frames of the trajectory (profiling runs)")
+    p.add_argument("--shape", default=None,
+                   help="ENGINE:WARPS (tensor:0, tcgen05:0, direct:2): the nearest-neighbour "
+                        "engine; batched_uneven plans with it instead of timing every shape")
+    p.add_argument("--kernels-only", action="store_true",
+                   help="batched_uneven: only the planned launch sequence (no plain per-frame "
+                        "comparison, end-to-end leg, side line or CPU baseline; profiling runs)")
     return p.parse_args()
 
 
@@ -456,8 +471,10 @@ def run_gpu(args, rank, world, dist):
     achieved = FLOP_PER_PAIR * pairs / chamfer_avg_s / 1e12 if chamfer_n else None
     engine = _lib.tune_get()[1]
     tc_fits = max(N, M) <= 524288
-    kernel = ("k_tcpass" if engine != _lib.ENGINE_DIRECT and tc_fits else
-              ("k_chamfer<true>" if mode == _lib.BIDIR_MEAN else "k_chamfer<false>"))
+    if engine != _lib.ENGINE_DIRECT and tc_fits:
+        kernel = "k_tcpass5" if engine == _lib.ENGINE_TCGEN05 else "k_tcpass"
+    else:
+        kernel = "k_chamfer<true>" if mode == _lib.BIDIR_MEAN else "k_chamfer<false>"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": (achieved / peak_tflops) if (achieved and peak_tflops) else None,
             "traffic": (CHAMFER_TRAFFIC_BYTES.get((args.workload, kernel, args.mode))
@@ -552,7 +569,11 @@ def run_batched(args, rank, world, dist):
     dts = [DeviceTrajectory.from_host(t, dev) for t in trajs]
     mode = _lib.UNIDIR_SUM if args.mode == "eq2" else _lib.BIDIR_MEAN
     # the autotuner times every shape on this batch and plans with the fastest
-    tuning = autotune.tune_batch(dts, mode=mode, grad=True, reps=2, save=False)
+    if args.shape:
+        eng, wd = args.shape.split(":")
+        tuning = {"best": (eng, int(wd)), "ms": {}}
+    else:
+        tuning = autotune.tune_batch(dts, mode=mode, grad=True, reps=2, save=False)
     shape = tuning["best"]
     b = BatchedLoss(dts, mode=mode, grad=True, graph=True, shape=shape)
     b.run(check=True)
@@ -592,6 +613,13 @@ def run_batched(args, rank, world, dist):
 
     per = [a.elapsed_time(c) for a, c in ev]
     ms = max_over_ranks(statistics.mean(per), dist)
+    if args.kernels_only:
+        if rank == 0:
+            print(json.dumps({"workload": "batched_uneven", "ms_per_step": ms,
+                              "pairs_per_s": world * pairs / (ms / 1e3),
+                              "shape": list(shape), "kernel_ms": chamfer_ms / max(1, chamfer_n),
+                              "gpu_launches": launches}), flush=True)
+        return
     # the plain per-frame form on the same inputs, at the same shape
     with autotune.tuned(shape):
         per_frame_loss(dts, mode=mode)
@@ -631,9 +659,9 @@ def run_batched(args, rank, world, dist):
             if sm_mhz else None)
     ck = chamfer_ms / max(1, chamfer_n) / 1e3
     ach = FLOP_PER_PAIR * pairs / ck / 1e12 if chamfer_n else None
-    tc = shape[0] == "tensor"
-    kernel = "k_tcpass" if tc else ("k_chamfer<true>" if mode == _lib.BIDIR_MEAN
-                                    else "k_chamfer<false>")
+    tc = shape[0] in ("tensor", "tcgen05")
+    kernel = ({"tensor": "k_tcpass", "tcgen05": "k_tcpass5"}[shape[0]] if tc else
+              ("k_chamfer<true>" if mode == _lib.BIDIR_MEAN else "k_chamfer<false>"))
     traffic = CHAMFER_TRAFFIC_BYTES.get(("batched_uneven", kernel, args.mode))
     roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak if (ach and peak) else None,
@@ -653,9 +681,18 @@ def run_batched(args, rank, world, dist):
                         "expanded form, exact direct-form re-check of the candidates), so the "
                         "8-flop FP32 accounting can exceed the CUDA-core peak; the tensor "
                         "view is below")
-        roof["tensor"] = {"achieved": mma_tflops, "unit": "TFLOP/s (f16 MMA, 32 flop per pair "
-                          "per direction)", "peak_mma_sync_measured": MMA_SYNC_TFLOPS,
-                          "frac_of_mma_sync": (mma_tflops / MMA_SYNC_TFLOPS) if mma_tflops else None}
+        if shape[0] == "tcgen05":
+            # tcgen05 f16 runs at the bf16 rate: the measured cuBLAS bf16 burst peak
+            tpk = measured_peaks().get("bf16_tflops")
+            roof["tensor"] = {"achieved": mma_tflops, "unit": "TFLOP/s (f16 MMA, 32 flop per "
+                              "pair per direction)", "peak": tpk,
+                              "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+                              "frac": (mma_tflops / tpk) if (mma_tflops and tpk) else None}
+        else:
+            roof["tensor"] = {"achieved": mma_tflops, "unit": "TFLOP/s (f16 MMA, 32 flop per "
+                              "pair per direction)", "peak_mma_sync_measured": MMA_SYNC_TFLOPS,
+                              "frac_of_mma_sync": (mma_tflops / MMA_SYNC_TFLOPS)
+                              if mma_tflops else None}
     line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s", "value": world * pairs / (ms / 1e3),
             "unit": "pairs/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -824,6 +861,12 @@ def main():
         run_batched(args, rank, world, dist)
     elif args.workload == "serving":
         run_serving(args, rank, world, dist)
+    elif args.shape:
+        from paper_2204_03139_gb300 import autotune
+
+        eng, wd = args.shape.split(":")
+        with autotune.tuned((eng, int(wd))):
+            run_gpu(args, rank, world, dist)
     else:
         run_gpu(args, rank, world, dist)
     if dist is not None:

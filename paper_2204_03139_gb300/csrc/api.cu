@@ -779,6 +779,7 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
     h->tc_units = keyed(engine) ? tunit : 0;
     h->tc_total = keyed(engine) ? tchunk : 0;
     h->tc_fallback = 0;
+    h->tc_next = 0;
     const char* src_img = img.data();
     const char* src_tc = tcimg.data();
     if (host_staging) {  // the caller's (pinned) memory: the copies need no host wait

@@ -169,7 +169,7 @@ struct MinBlocks {
 template <bool BIDIR, int W>
 __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
     k_chamfer(Ws w, int stall) {
-    pdl_entry();
+    pdl_wait();
     constexpr int THREADS = 32 * W;
     constexpr int WARPS = W;
     constexpr int ROWS_PER_UNIT = ROWS_PER_WARP * W;
@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(32 * W, (MinBlocks<BIDIR, W>::value))
         }
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 int g_chamfer_ctas[64][2][3];  // per device, mode and width: resident CTAs of the grid

@@ -237,6 +237,7 @@ __device__ void build_uniform(const UniformArgs& a, const Ws& w) {
         h->tc_units = 0;
         h->tc_total = 0;
         h->tc_fallback = 0;
+        h->tc_next = 0;
     }
     __syncthreads();  // the frames' live counts are written
     // units: a skipped frame's units carry no sub-chunks
@@ -671,7 +672,9 @@ cudaError_t launch_build_uniform(const UniformArgs& a, const Ws& w, cudaStream_t
 
 cudaError_t launch_reset(const Ws& w, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&w.hdr->status, 0, sizeof(int), s);
-    return e ? e : cudaMemsetAsync(&w.hdr->tc_fallback, 0, sizeof(int), s);
+    static_assert(offsetof(WsHeader, tc_next) == offsetof(WsHeader, tc_fallback) + sizeof(int),
+                  "one memset clears both");
+    return e ? e : cudaMemsetAsync(&w.hdr->tc_fallback, 0, 2 * sizeof(int), s);
 }
 
 cudaError_t launch_build_area(const UniformArgs& a, const Ws& w, cudaStream_t s) {

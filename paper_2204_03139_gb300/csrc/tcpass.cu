@@ -51,21 +51,32 @@ struct TcSeg {
 constexpr int TC_THREADS = 32 * TC_WARPS;
 constexpr int TC_MIN_BLOCKS = 3;  // 12 warps per SM
 
-__global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int stall) {
-    pdl_entry();
+// Work split. Stream-K (dyn = 0): CTA b takes the contiguous range [b per, (b + 1) per) of
+// the (unit, chunk) list, so every CTA gets the same number of chunks and a unit may be
+// split between CTAs (merged by k_tcmerge). With many more units than CTAs (dyn = 1) the
+// CTAs instead take whole units in list order from a counter, so that the units in flight at
+// any time are neighbours, of a few frames whose target forms stay in L2; a contiguous
+// range per CTA would spread the CTAs over the whole list and stream every unit's targets
+// from HBM again. The tail costs at most one unit per CTA.
+__global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int stall, int dyn) {
+    pdl_wait();
     constexpr uint32_t CH_BYTES = TC_CHUNK * 32;  // B forms of one chunk
     __shared__ __align__(128) unsigned s_b[2][CH_BYTES / 4];
     __shared__ __align__(8) u64 s_bar[2];
     __shared__ TcSeg s_u;
+    __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int n_units = w.hdr->tc_units, total = w.hdr->tc_total;
-    const int per = (total + gridDim.x - 1) / gridDim.x;
-    int s = blockIdx.x * per;
-    const int s_end = min(total, s + per);
-    if (s >= s_end) return;
-    int u = last_le(w.tc_upre, n_units, s);
+    int s = 0, s_end = 0, u = 0;
+    if (!dyn) {
+        const int per = (total + gridDim.x - 1) / gridDim.x;
+        s = blockIdx.x * per;
+        s_end = min(total, s + per);
+        if (s >= s_end) return;
+        u = last_le(w.tc_upre, n_units, s);
+    }
     const long long tot_rows = w.hdr->total_rows;
 
     if (tid == 0) {
@@ -79,8 +90,19 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
     bool abort = false;
     const unsigned* A32 = reinterpret_cast<const unsigned*>(w.tca);
 
-    while (s < s_end) {
+    for (;;) {
         __syncthreads();  // the previous segment is done with s_u and the buffers' contents
+        if (dyn) {
+            if (tid == 0) s_next = atomicAdd(&w.hdr->tc_next, 1);
+            __syncthreads();
+            u = s_next;
+            if (u >= n_units) break;
+            s = w.tc_upre[u];
+            s_end = w.tc_upre[u + 1];
+            if (s >= s_end) continue;  // a skipped frame's unit: no chunks
+        } else if (s >= s_end) {
+            break;
+        }
         if (tid == 0) {
             const FrameDesc* fr = w.frames + w.tc_ufr[u];
             const int urb = w.tc_urb[u];
@@ -195,8 +217,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
                 o[2] = k3[r];
             }
         }
-        s = min(s_end, w.tc_upre[u + 1]);
-        ++u;
+        if (!dyn) {
+            s = min(s_end, w.tc_upre[u + 1]);
+            ++u;
+        }
     }
 
     if (abort) {
@@ -208,6 +232,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
         }
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 // Units split between CTAs: one CTA per unit merges the lists that its CTAs left in their
@@ -667,8 +692,8 @@ __device__ __forceinline__ bool mbar_test(u64* bar, uint32_t parity) {
 // tile m + 2 (mod 4); the consumer warp of lane quarter m of that tile reports its chunk reads
 __device__ __forceinline__ int t5_slot_of(int m, int i) { return i == 0 ? 2 * m : 2 * ((m + 2) & 3) + 1; }
 
-__global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
-    pdl_entry();
+__global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int dyn) {
+    pdl_wait();
     __shared__ __align__(1024) uint4 s_a[TC_UNIT_ROWS * 2];  // A forms of the unit, 16 KB
     extern __shared__ __align__(1024) uint4 t5_dyn[];
     uint4* const s_b = t5_dyn;                                // T5_BUFS chunks of B forms
@@ -685,11 +710,16 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
     const bool mt = mwarp && lane == 0;        // an issuing thread
     const bool stager = mt && m == 0;          // the thread that also streams the chunks
     const int n_units = w.hdr->tc_units, total = w.hdr->tc_total;
-    const int per = (total + gridDim.x - 1) / gridDim.x;
-    int s = blockIdx.x * per;
-    const int s_end = min(total, s + per);
-    if (s >= s_end) return;
-    int u = last_le(w.tc_upre, n_units, s);
+    // the work split of the warp-level kernel: stream-K, or whole units on demand (dyn)
+    int s = 0, s_end = 0, u = 0;
+    if (!dyn) {
+        const int per = (total + gridDim.x - 1) / gridDim.x;
+        s = blockIdx.x * per;
+        s_end = min(total, s + per);
+        if (s >= s_end) return;
+        u = last_le(w.tc_upre, n_units, s);
+    }
+    __shared__ int s_next;
     const long long tot_rows = w.hdr->total_rows;
 
     if (warp == 0) {
@@ -732,8 +762,19 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
     int n_seg = 0;               // segments begun (phase of the A barrier)
     bool abort = false, issued = false;
 
-    while (s < s_end && !abort) {
+    while (!abort) {
         __syncthreads();  // the previous segment is done with s_u and s_a
+        if (dyn) {
+            if (stager) s_next = atomicAdd(&w.hdr->tc_next, 1);
+            __syncthreads();
+            u = s_next;
+            if (u >= n_units) break;
+            s = w.tc_upre[u];
+            s_end = w.tc_upre[u + 1];
+            if (s >= s_end) continue;  // a skipped frame's unit: no chunks
+        } else if (s >= s_end) {
+            break;
+        }
         if (stager) {
             const FrameDesc* fr = w.frames + w.tc_ufr[u];
             const int urb = w.tc_urb[u];
@@ -895,8 +936,10 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
         pend_b = 0;
         chunk0 += c_hi - c_lo + 1;
         ++n_seg;
-        s = min(s_end, w.tc_upre[u + 1]);
-        ++u;
+        if (!dyn) {
+            s = min(s_end, w.tc_upre[u + 1]);
+            ++u;
+        }
     }
 
     if (abort) {
@@ -922,6 +965,7 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(T5_TMEM_COLS)
                      : "memory");
+    pdl_trigger();
 }
 
 int g_tc_ctas[64];  // per device: resident CTAs of the persistent grid
@@ -978,16 +1022,21 @@ cudaError_t launch_tcpass(const Ws& w, int engine, int grid, long long total_chu
             g_t5_smem_set[dev] = 1;
         }
     }
+    // whole units on demand once there are many more units than CTAs (the tail is then a
+    // small part of every CTA's work), else stream-K
+    const int dyn = (long long)n_units >= TC_DYN_UNITS_PER_CTA * (long long)grid ? 1 : 0;
     prof_before(s);
-    e = engine == ENGINE_TC5 ? launch_pdl(k_tcpass5, grid, T5_THREADS, T5_SMEM, s, w, stall)
-                             : launch_pdl(k_tcpass, grid, TC_THREADS, 0, s, w, stall);
+    e = engine == ENGINE_TC5
+            ? launch_pdl(k_tcpass5, grid, T5_THREADS, T5_SMEM, s, w, stall, dyn)
+            : launch_pdl(k_tcpass, grid, TC_THREADS, 0, s, w, stall, dyn);
     prof_after(s);
     count_launch();
     if (e) return e;
-    // with more than one CTA a unit can be split between CTAs; the merge launch (one CTA per
-    // possible unit) finds the split ones on the device, where the live chunk count is known
+    // with stream-K and more than one CTA a unit can be split between CTAs; the merge launch
+    // (one CTA per possible unit) finds the split ones on the device, where the live chunk
+    // count is known
     (void)total_chunks;
-    if (grid > 1 && n_units > 0) {
+    if (!dyn && grid > 1 && n_units > 0) {
         e = launch_pdl(k_tcmerge, n_units, TC_THREADS, 0, s, w, grid);
         count_launch();
         if (e) return e;
