@@ -800,13 +800,17 @@ def run_serving(args, rank, world, dist):
         res = [f.result(timeout=600) for f in futs]
         t_end = time.perf_counter() - t0
         srv.close()
+        st = srv.stats()
         lat = np.array([r.latency_s for r in res])
         pairs = sum(tr.pairs() for _, tr in reqs)
         return {"rate_hz": rate, "requests": len(reqs), "window_s": window,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "throughput_pairs_per_s": pairs / t_end,
-                "mean_batch_requests": float(np.mean([r.batch_requests for r in res]))}
+                "mean_batch_requests": float(np.mean([r.batch_requests for r in res])),
+                "batches": st["batches"],
+                "scheduler_host_ms_per_batch": st["host_ms_per_batch"],
+                "scheduler_host_ms_per_batch_p99": st["host_ms_per_batch_p99"]}
 
     # warm-up: build pinned copies, first launches
     w = Server(dev, hbm_budget=120 << 30, item_pairs=args.item_pairs,

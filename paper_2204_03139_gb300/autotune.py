@@ -2,7 +2,7 @@
 
 The shapes it chooses between:
   ("tensor", 0)  the tensor-core filter on warp-level MMAs (frames of at most 524 288
-                 points per side; the library's default);
+                 points per side; the library's default for calls of 1e9 pairs and more);
   ("tcgen05", 0) the same filter on tcgen05 MMAs;
   ("direct", w)  the CUDA-core direct form with CTAs of w = 1, 2 or 4 warps (w x 512 sim
                  points held in registers; wide CTAs amortise the target staging and the

@@ -188,12 +188,24 @@ int g_engine = ENGINE_AUTO;  // process-wide engine set by dc_tune_set
 // The Chamfer engine of a call: a tensor-core filter when the problem fits its key format
 // (tcgen05 by default, the warp-level MMA one when asked for), else, or when the direct
 // engine is requested, the CUDA-core direct form.
-// The default is the warp-level tensor-core filter: it measured faster than the tcgen05 one
-// on every workload (at K = 16 each distance tile is one isolated tcgen05 MMA, whose issue
-// cost the folds cannot hide), which stays available on request.
-int choose_engine(bool tc_fits) {
+// The default is the warp-level tensor-core filter for calls large enough to pay back its
+// fixed costs (candidate recovery, the fallback scans, the merge of split units): at least
+// 1e9 pairs and 5e7 per frame on average. Measured on one GB300 against the direct engine:
+// 1 frame of 32 768 points 329 vs 330 us, 10 frames of 10 000 282 vs 302 us, 40 frames of
+// 10 000 0.909 vs 1.028 ms, but 100 frames of 4096 497 vs 483 us and 1 frame of 16 384
+// 139 vs 119 us. The tcgen05 filter measured slower than the warp-level one on every
+// workload (at K = 16 each distance tile is one isolated tcgen05 MMA, whose issue and
+// synchronisation cost the folds cannot hide); it stays available on request.
+constexpr double TC_AUTO_MIN_PAIRS = 1e9;
+constexpr double TC_AUTO_MIN_FRAME_PAIRS = 5e7;
+
+int choose_engine(bool tc_fits, double pairs, long long frames) {
     if (g_engine == ENGINE_DIRECT || !tc_fits) return ENGINE_DIRECT;
-    return g_engine == ENGINE_TC5 ? ENGINE_TC5 : ENGINE_TC;
+    if (g_engine == ENGINE_TC5) return ENGINE_TC5;
+    if (g_engine == ENGINE_TC) return ENGINE_TC;
+    const bool big = pairs >= TC_AUTO_MIN_PAIRS &&
+                     pairs >= TC_AUTO_MIN_FRAME_PAIRS * (double)(frames > 0 ? frames : 1);
+    return big ? ENGINE_TC : ENGINE_DIRECT;
 }
 
 int keyed_grid(int engine, long long chunks) {
@@ -208,7 +220,10 @@ int run_uniform(UniformArgs a, unsigned phases, int epi_flags, float* loss_total
     if (!uniform_sizes(a.T, a.V, a.F, a.N, a.M, sz, sub, spu, !direct_only))
         return fail(DC_EINVAL, "problem too large for 32-bit offsets");
     const bool chamfer = (phases & PH_CHAMFER) != 0;
-    const int engine = chamfer && !direct_only ? choose_engine(sz.tc_units > 0) : ENGINE_DIRECT;
+    const int engine =
+        chamfer && !direct_only
+            ? choose_engine(sz.tc_units > 0, (double)a.T * (double)a.N * (double)a.M, a.T)
+            : ENGINE_DIRECT;
     const int warps =
         (chamfer && engine == ENGINE_DIRECT) ? choose_warps(a.mode, sub[2], sub[1], sub[0]) : 1;
     a.engine = engine;
@@ -658,7 +673,9 @@ int plan_impl(const dc_frame* frames, int n_frames, int mode, void* ws, size_t w
     long long sub[3];
     if (!batch_sizes(frames, n_frames, sz, sub))
         return fail(DC_EINVAL, "batch too large for 32-bit offsets");
-    const int engine = choose_engine(sz.tc_units > 0);
+    double pairs = 0.0;
+    for (int k = 0; k < n_frames; ++k) pairs += (double)frames[k].N * (double)frames[k].M;
+    const int engine = choose_engine(sz.tc_units > 0, pairs, n_frames);
     const int warps = engine == ENGINE_DIRECT ? choose_warps(mode, sub[2], sub[1], sub[0]) : 1;
     const Layout L = make_layout(sz);
     // the staging image: the table regions [hdr, cdf), then the tensor-core unit tables

@@ -503,17 +503,19 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
 constexpr int FB_THREADS = 256;            // eight warps
 constexpr int FB_ROWS_PER_WARP = 8;        // queued rows a warp evaluates at once
 constexpr int FB_TILE = 512;               // columns per shared-memory tile
-constexpr int FB_SPLIT = 4;                // CTAs per list, each over a quarter of the columns
+constexpr int FB_SPLIT = 4;                // CTAs per list at least
+constexpr int FB_SPLIT_MAX = 64;           // and at most
 
-// The rows that their keys did not certify, FB_SPLIT CTAs per (frame, side) list, each over
-// a contiguous quarter of the frame's columns: they stream through shared memory in tiles,
-// each loaded once for up to 64 queued rows (eight per warp, the lanes splitting the
-// columns); the quarters' minima merge with atomicMin on (distance bits << 32 | index), so
-// every row ends with its minimum and the lowest index attaining it.
-__global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows) {
+// The rows that their keys did not certify, `split` CTAs per (frame, side) list, each over
+// a contiguous part of the frame's columns: they stream through shared memory in tiles, each
+// loaded once for up to 64 queued rows (eight per warp, the lanes splitting the columns); the
+// parts' minima merge with atomicMin on (distance bits << 32 | index), so every row ends with
+// its minimum and the lowest index attaining it. Few frames get more parts each, so that the
+// launch still fills the GPU (one 32 768-point frame: 8 CTAs took 279 us).
+__global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows, int split) {
     pdl_entry();
     __shared__ float s_c[3][FB_TILE];
-    const int part = blockIdx.x % FB_SPLIT, ks = blockIdx.x / FB_SPLIT;
+    const int part = blockIdx.x % split, ks = blockIdx.x / split;
     const int k = ks >> 1, side = ks & 1;
     if (k >= w.hdr->n_frames) return;
     const FrameDesc* fr = w.frames + k;
@@ -534,8 +536,8 @@ __global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows) {
             qx[t] = x.x, qy[t] = x.y, qz[t] = x.z;
             best[t] = EMPTY;
         }
-        const int ja = (int)((long long)C.n * part / FB_SPLIT);
-        const int jb = (int)((long long)C.n * (part + 1) / FB_SPLIT);
+        const int ja = (int)((long long)C.n * part / split);
+        const int jb = (int)((long long)C.n * (part + 1) / split);
         for (int j0 = ja; j0 < jb; j0 += FB_TILE) {
             __syncthreads();  // the previous tile is consumed
             for (int j = threadIdx.x; j < FB_TILE; j += FB_THREADS) {
@@ -1050,7 +1052,9 @@ cudaError_t launch_tcpass(const Ws& w, int engine, int grid, long long total_chu
     e = launch_pdl(k_tcrecover, rgrid, REC_THREADS, 0, s, w, rows, total);
     count_launch();
     if (e) return e;
-    e = launch_pdl(k_tcfallback, 2 * n_frames * FB_SPLIT, FB_THREADS, 0, s, w, rows);
+    const int split = std::max(FB_SPLIT, std::min(FB_SPLIT_MAX, div_up(4 * std::max(sms, 1),
+                                                                     2 * n_frames)));
+    e = launch_pdl(k_tcfallback, 2 * n_frames * split, FB_THREADS, 0, s, w, rows, split);
     count_launch();
     return e ? e : cudaGetLastError();
 }

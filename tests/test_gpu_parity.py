@@ -152,12 +152,12 @@ def test_exact_ties_go_to_the_lowest_index(mode):
 # failure detection without a GPU fault
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.timeout(120)
-@pytest.mark.parametrize("shape", [None, ("tcgen05", 0), ("direct", 2)])
+@pytest.mark.parametrize("shape", [("tensor", 0), ("tcgen05", 0), ("direct", 2)])
 def test_bounded_wait_gives_up_with_a_timeout_status_and_the_device_stays_usable(shape):
     """The Chamfer kernels' waits for their target chunks (and, on the tcgen05 engine, for
     the MMAs and the reading warps) are bounded (2 s). A launch whose first chunk is never
     requested must end with DC_ETIMEOUT in the workspace status, and the next call on the same
-    context must produce the normal result; for the default engine and both others."""
+    context must produce the normal result; for each of the three engines."""
     from paper_2204_03139_gb300 import autotune
 
     tr = parity.nudged(W.trajectory_50x50(T=2, n=2000, m=2000))
