@@ -38,9 +38,16 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
 MMA_SYNC_TFLOPS = 600.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the nearest-neighbour kernel,
 # keyed by (workload, kernel, mode), from one-pass ncu captures of one launch:
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:<kernel>
-#       -c 1 python bench.py --workload <workload> --steps 1 --warmup 1 --no-cpu-baseline
-CHAMFER_TRAFFIC_BYTES = {("trajectory_50x50", "k_chamfer<true>", "eq1"): 22.79e6,
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k 'regex:k_tcpass$' -c 1 python bench.py --steps 2 --warmup 3 --kernels-only --shape tensor:0
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k 'regex:k_tcpass$' -s 3 -c 1 python bench.py --workload trajectory_50x50 --steps 3 \
+#       --warmup 3 --no-cpu-baseline [--mode eq2]
+CHAMFER_TRAFFIC_BYTES = {("batched_uneven", "k_tcpass", "eq1"): 7.44e9 + 5.46e9,
+                         ("trajectory_50x50", "k_tcpass", "eq1"): 54.02e6 + 9.09e6,
+                         ("trajectory_50x50", "k_tcpass", "eq2"): 26.26e6 + 0.06e6,
+                         # the direct engine (--shape direct:2), -k regex:k_chamfer
+                         ("trajectory_50x50", "k_chamfer<true>", "eq1"): 22.79e6,
                          ("trajectory_50x50", "k_chamfer<false>", "eq2"): 19.57e6}
 
 
@@ -469,9 +476,9 @@ def run_gpu(args, rank, world, dist):
     peak_tflops = 2 * FP32_LANES_PER_SM * sms * sm_mhz * 1e6 / 1e12 if sm_mhz else None
     chamfer_avg_s = chamfer_ms / max(1, chamfer_n) / 1e3
     achieved = FLOP_PER_PAIR * pairs / chamfer_avg_s / 1e12 if chamfer_n else None
-    engine = _lib.tune_get()[1]
-    tc_fits = max(N, M) <= 524288
-    if engine != _lib.ENGINE_DIRECT and tc_fits:
+    # the engine the library ran (the workspace header's engine word, offset 52)
+    engine = int(out["ws"][52:56].cpu().view(torch.int32)[0])
+    if engine in (_lib.ENGINE_TENSOR, _lib.ENGINE_TCGEN05):
         kernel = "k_tcpass5" if engine == _lib.ENGINE_TCGEN05 else "k_tcpass"
     else:
         kernel = "k_chamfer<true>" if mode == _lib.BIDIR_MEAN else "k_chamfer<false>"
