@@ -69,6 +69,7 @@ class _Request:
     loss_dev: torch.Tensor | None = None   # [T] on the device, written item by item
     grad_dev: torch.Tensor | None = None   # [T, V, 3]
     w_dev: torch.Tensor | None = None      # [T] frame weights (None: all ones)
+    w_host: torch.Tensor | None = None     # their pinned host copy, alive until the copy ran
     total_dev: torch.Tensor | None = None  # [1] sum_t w_t L_t, formed by the library
     out_host: tuple = field(default_factory=tuple)  # pinned (loss, grad, total) copies
     fin: torch.cuda.Event | None = None    # the host copies of the results are complete
@@ -280,8 +281,11 @@ class Server:
                               if r.grad else None)
                 r.total_dev = torch.empty(1, dtype=torch.float32, device=self.device)
                 if r.weights is not None:
-                    r.w_dev = torch.from_numpy(np.ascontiguousarray(r.weights, np.float32)).to(
-                        self.device, non_blocking=False)
+                    # pinned, so the copy does not wait for the stream; the request keeps the
+                    # host buffer until its results are back
+                    r.w_host = torch.from_numpy(
+                        np.ascontiguousarray(r.weights, np.float32)).pin_memory()
+                    r.w_dev = r.w_host.to(self.device, non_blocking=True)
             # cut into items of consecutive frames of at most item_pairs pairs
             per = np.diff(r.dev.n_off) * np.diff(r.dev.m_off)
             a = 0
@@ -401,7 +405,7 @@ class Server:
     def _release(self, r):
         r.dev = None
         r.host = ()
-        r.loss_dev = r.grad_dev = r.total_dev = r.w_dev = None
+        r.loss_dev = r.grad_dev = r.total_dev = r.w_dev = r.w_host = None
         with self._cv:
             self._used -= r.nbytes
 
