@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
     __shared__ __align__(8) u64 s_bar[2];
     __shared__ TcSeg s_u;
     __shared__ int s_next;
+    __shared__ int s_done[2];    // warps done with the buffer's current chunk
+    __shared__ int s_issued[2];  // copies ever issued into the buffer
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -82,10 +84,12 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
+        s_done[0] = s_done[1] = 0;
+        s_issued[0] = s_issued[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     uint32_t par = 0;      // bit b: the phase parity to wait for on buffer b
-    uint32_t pending = 0;  // bit b: a copy into buffer b is in flight (thread 0)
+    int waited0 = 0, waited1 = 0;  // copies into buffers 0 and 1 this thread waited for
     int seq = 0;           // chunks consumed so far; buffer = seq & 1
     bool abort = false;
     const unsigned* A32 = reinterpret_cast<const unsigned*>(w.tca);
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
                 mbar_expect_tx(&s_bar[b], CH_BYTES);
                 bulk_g2s(&s_b[b][0], w.tcb + 2 * (s_u.bcol + (long long)c * TC_CHUNK), CH_BYTES,
                          &s_bar[b]);
-                pending |= 1u << b;
+                ++s_issued[b];
             }
         }
         __syncthreads();
@@ -155,7 +159,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
             const int b = seq & 1;
             // every lane of a warp must agree before the warp-wide MMAs
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&s_bar[b], (par >> b) & 1u));
-            if (ok) par ^= 1u << b;
+            if (ok) {
+                par ^= 1u << b;
+                if (b) ++waited1; else ++waited0;
+            }
             if (ok && wactive) {
                 const unsigned* S = s_b[b];
 #pragma unroll 1
@@ -188,20 +195,33 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
                                     (__float_as_uint(fmaxf(bm[r], 0.0f)) & TC_VALUE_MASK) | id);
                 }
             }
-            abort = __syncthreads_or(!ok) != 0;
-            if (abort) break;
-            if (tid == 0) {
-                pending &= ~(1u << b);
-                // buffer b is free again: stage chunk c + 2 into it
-                if (c + 2 <= c_hi) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx(&s_bar[b], CH_BYTES);
-                    bulk_g2s(&s_b[b][0], w.tcb + 2 * (s_u.bcol + (long long)(c + 2) * TC_CHUNK),
-                             CH_BYTES, &s_bar[b]);
-                    pending |= 1u << b;
+            if (!ok) {  // the chunk never landed: give up the segment
+                abort = true;
+                break;
+            }
+            // This warp is done with buffer b. The last of the CTA's warps to get here stages
+            // chunk c + 2 into it, so the warps meet at no barrier between chunks and may
+            // drift up to a chunk apart (the key inserts of different warps overlap).
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();  // the warp's reads of the buffer before the count
+                if (atomicAdd(&s_done[b], 1) == TC_WARPS - 1) {
+                    __threadfence_block();  // and every other warp's reads before the copy
+                    s_done[b] = 0;
+                    if (c + 2 <= c_hi) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        mbar_expect_tx(&s_bar[b], CH_BYTES);
+                        bulk_g2s(&s_b[b][0],
+                                 w.tcb + 2 * (s_u.bcol + (long long)(c + 2) * TC_CHUNK),
+                                 CH_BYTES, &s_bar[b]);
+                        atomicAdd(&s_issued[b], 1);
+                    }
                 }
             }
         }
+        // a wait that gave up in any warp ends the CTA's work (the other warps' waits for
+        // the chunks that are then never staged give up too, so every warp gets here)
+        abort = __syncthreads_or(abort) != 0;
         if (abort) break;
         if (wactive) {
             // every lane keeps its own column subset's three smallest keys: [row][lane t][3]
@@ -226,9 +246,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
     if (abort) {
         if (tid == 0) {
             set_status(&w.hdr->status, DC_ETIMEOUT);
-            // let copies still in flight land before the CTA's shared memory goes away
-            for (int b = 0; b < 2; ++b)
-                if (pending & (1u << b)) (void)mbar_wait(&s_bar[b], (par >> b) & 1u);
+            // let copies still in flight land before the CTA's shared memory goes away (a
+            // buffer holds at most one copy that thread 0 has not waited for)
+            if (s_issued[0] > waited0) (void)mbar_wait(&s_bar[0], par & 1u);
+            if (s_issued[1] > waited1) (void)mbar_wait(&s_bar[1], (par >> 1) & 1u);
         }
         __syncthreads();
     }

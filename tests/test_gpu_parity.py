@@ -315,7 +315,7 @@ def test_trajectory_100x100_autograd_recompute_matches_oracle_and_fd(traj100):
     total.backward()
     torch.cuda.synchronize()
     parity.check_loss(lf.detach().cpu().numpy(), ref["loss_frames"])
-    parity.check_loss([float(total)], [ref["loss_total"]], what="total")
+    parity.check_loss([float(total.detach())], [ref["loss_total"]], what="total")
     gpu_g = vv.grad.cpu().numpy()
     parity.check_grad(gpu_g, ref["grad_verts"])
     fd_check(tr, gpu_g, ref, t=37, n=200, seed=17)
