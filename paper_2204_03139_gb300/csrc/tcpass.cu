@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
             }
             if (ok && wactive) {
                 const unsigned* S = s_b[b];
-#pragma unroll 1
+#pragma unroll
                 for (int half = 0; half < TC_CHUNK / TC_BLOCK; ++half) {
                     float bm[16];
 #pragma unroll
