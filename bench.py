@@ -43,9 +43,9 @@ MMA_SYNC_TFLOPS = 600.0
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k 'regex:k_tcpass$' -s 3 -c 1 python bench.py --workload trajectory_50x50 --steps 3 \
 #       --warmup 3 --no-cpu-baseline [--mode eq2]
-CHAMFER_TRAFFIC_BYTES = {("batched_uneven", "k_tcpass", "eq1"): 7.44e9 + 5.46e9,
-                         ("trajectory_50x50", "k_tcpass", "eq1"): 54.02e6 + 9.09e6,
-                         ("trajectory_50x50", "k_tcpass", "eq2"): 26.26e6 + 0.06e6,
+CHAMFER_TRAFFIC_BYTES = {("batched_uneven", "k_tcpass", "eq1"): 7.73e9 + 5.46e9,
+                         ("trajectory_50x50", "k_tcpass", "eq1"): 53.94e6 + 8.33e6,
+                         ("trajectory_50x50", "k_tcpass", "eq2"): 26.27e6 + 0.03e6,
                          # the direct engine (--shape direct:2), -k regex:k_chamfer
                          ("trajectory_50x50", "k_chamfer<true>", "eq1"): 22.79e6,
                          ("trajectory_50x50", "k_chamfer<false>", "eq2"): 19.57e6}
