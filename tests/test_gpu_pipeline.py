@@ -42,6 +42,59 @@ def test_pipeline_matches_plain_calls():
             assert np.linalg.norm(o[0].numpy() - g) <= 1e-6 * np.linalg.norm(g)
 
 
+@pytest.mark.parametrize("shape", [("tensor", 0), ("direct", 2)])
+def test_batch_pipeline_matches_single_batches(shape):
+    """Three batches of one structure (ragged frames, uneven trajectories) with different
+    values, through two slots: every result equals the one a fresh batch plan gives for the
+    same inputs, so slot reuse while batches are in flight corrupts nothing."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import copy
+
+    from paper_2204_03139_gb300 import _lib
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
+    from paper_2204_03139_gb300.pipeline import BatchPipeline
+
+    dev = torch.device("cuda:0")
+    base = W.batched_uneven(n_traj=3, grid=(12, 24), T=(2, 4), m=(500, 2500))
+    batches = []
+    for k in range(3):  # the same structure, other values: fresh draws, moved targets
+        rng = W.rng_for(500 + k)
+        bt = []
+        for t in base:
+            t = copy.copy(t)
+            t.draws = np.clip(rng.random(t.draws.shape), 0, np.nextafter(1, 0)).astype(np.float32)
+            t.targets = (t.targets + np.float32(0.01 * k)).astype(np.float32)
+            t.verts = (t.verts * np.float32(1.0 + 0.02 * k)).astype(np.float32)
+            bt.append(t)
+        batches.append(bt)
+    pipe = BatchPipeline([(t.V, t.F, t.n_off, t.m_off) for t in base], device=dev, depth=2,
+                         shape=shape)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    outs, events = [], []
+    for bt in batches:
+        host = [(pin(t.verts), pin(t.faces), pin(t.draws), pin(t.targets)) for t in bt]
+        o = ([torch.empty(t.verts.shape, dtype=torch.float32).pin_memory() for t in bt],
+             torch.empty(1, dtype=torch.float32).pin_memory(),
+             [torch.empty(t.T, dtype=torch.float32).pin_memory() for t in bt])
+        events.append(pipe.submit(host, grads_out=o[0], total_out=o[1], frames_out=o[2]))
+        outs.append((host, o))
+    for e in events:
+        e.synchronize()
+    assert pipe.status() == _lib.DC_OK
+    for bt, (host, o) in zip(batches, outs):
+        ref = BatchedLoss([DeviceTrajectory.from_host(t, dev) for t in bt], grad=True,
+                          shape=shape)
+        total = ref.run(check=True)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(o[1].numpy(), total.cpu().numpy(), rtol=1e-6)
+        for k in range(len(bt)):
+            np.testing.assert_allclose(o[2][k].numpy(), ref.loss_frames[k].cpu().numpy(),
+                                       rtol=1e-6)
+            g = ref.grad_verts[k].cpu().numpy()
+            assert np.linalg.norm(o[0][k].numpy() - g) <= 1e-6 * np.linalg.norm(g)
+
+
 def test_fp32_fma_rate_is_near_the_fp32_peak():
     """The measured FMA rate (the cross-check of the roofline's FP32 peak) lies between 30% and
     110% of 2 x 128 lanes x SMs x 2.1 GHz, for scalar and packed FMAs."""
