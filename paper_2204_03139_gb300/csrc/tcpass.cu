@@ -375,34 +375,36 @@ __device__ __forceinline__ float3 frame_row(const Ws& w, const FrameDesc* fr, in
     return make_float3(p.x, p.y, p.z);
 }
 
-constexpr int REC_THREADS = 256;  // 64 rows per CTA step, four lanes per row
+constexpr int REC_THREADS = 256;     // one row per thread: 256 rows per CTA step
+constexpr int REC_MAX_CAND = 2 * 4;  // candidates per row: two blocks per column quarter
 
 // The rows' exact minima from their keys: rows [0, rows) are sim points, rows
-// [rows, total) targets (Eq. 1 only). Each CTA takes a contiguous range of rows, 64 at a time
-// (frames are padded to multiples of 256 rows, so a step's 64 rows lie in one frame, found
-// by walking the frame table forward). The four lanes of a row read the keys of their
-// quarter of the columns, agree on the threshold and scan, eight columns each, the candidate
-// blocks that any of them admits; the groups of a warp take their candidates in the same
-// order (the s-th of each group in step s), so that the warp runs the largest count, not the
-// sum. A row that the keys do not certify (a lane's third key under the threshold) is
-// queued in its frame's list for k_tcfallback. Writes (distance bits << 32 | index) to
-// pab / pba.
+// [rows, total) targets (Eq. 1 only). Each CTA takes a contiguous range of rows, 256 at a
+// time (frames are padded to multiples of 256 rows, so a step's rows lie in one frame, found
+// by walking the frame table forward). Each thread takes one row: it reads the row's 12 keys,
+// computes the threshold once, and lists the candidate blocks (per quarter of the columns,
+// the first two keys under the threshold); a warp prefix sum lays the warp's candidates out in
+// shared memory, and the warp re-checks them four at a time, eight lanes per candidate (its
+// 32 columns, four per lane) in the direct form, merging into the row's minimum with a shared
+// atomicMin. A row that the keys do not certify (a quarter's third key under the threshold)
+// is queued in its frame's list for k_tcfallback. Writes (distance bits << 32 | index) to
+// pab / pba. (Four lanes per row, each with one quarter's keys, took 81 warp instructions
+// per row: the threshold was computed four times and a warp step covered only 8 rows.)
 __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int total) {
     pdl_entry();
     constexpr int NW = REC_THREADS / 32;
-    __shared__ float s_q[NW][8][4];       // per warp: the query point of each row group
-    __shared__ unsigned s_list[NW][64];   // per warp: candidate entries (cand << 3 | group)
-    __shared__ u64 s_best[NW][8];         // per warp: the rows' packed minima
-    const int steps = div_up(total, REC_THREADS / 4);
+    __shared__ float s_q[NW][32][3];                 // per warp: each row's query point
+    __shared__ unsigned s_list[NW][32 * REC_MAX_CAND];  // candidates: (cand << 5) | row
+    __shared__ u64 s_best[NW][32];                   // per warp: the rows' packed minima
+    const int steps = div_up(total, REC_THREADS);
     const int per = div_up(steps, gridDim.x);
     const int st0 = blockIdx.x * per, st1 = min(steps, st0 + per);
     const int n_frames = w.hdr->n_frames;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = lane & 3, gl = lane & ~3;
-    const int grp = lane >> 2, sub = lane >> 3, l8 = lane & 7;
-    const unsigned lt = (1u << lane) - 1u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane >> 3, l8 = lane & 7;
     int k = -1, side = -1;
     for (int st = st0; st < st1; ++st) {
-        const int base = st * (REC_THREADS / 4);
+        const int base = st * REC_THREADS;
         const int sd = base >= rows ? 1 : 0;
         const int g0 = sd ? base - rows : base;  // first row of the step within its side
         if (sd != side) {
@@ -413,69 +415,83 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
         while (k + 1 < n_frames && pre[k + 1] <= g0) ++k;
         const FrameDesc* fr = w.frames + k;
         if (fr->skip) continue;  // uniform over the CTA
-        const int g = g0 + (threadIdx.x >> 2);
+        const int g = g0 + threadIdx.x;
         const int i = g - (side ? fr->col0 : fr->row0);
         const bool valid = i < (side ? fr->M : fr->N);
         const Cols C = frame_cols(w, fr, side);
-        const float4 box = w.fbox[k];
 
-        unsigned kk[3] = {TC_EMPTY, TC_EMPTY, TC_EMPTY};
-        float qx = 0.f, qy = 0.f, qz = 0.f, r = 0.f;
+        // candidate j = 2 t + i of the row is quarter t's key i, if bit j of cmask is set
+        unsigned kk[TC_KEYS];
+        unsigned cmask = 0;
+        bool full = false;
+        float qx = 0.f, qy = 0.f, qz = 0.f;
         if (valid) {
-            const unsigned* p =
-                (side ? w.kba + (long long)TC_KEYS * g : w.kab + (long long)TC_KEYS * g) + 3 * q;
-            kk[0] = p[0];
-            kk[1] = p[1];
-            kk[2] = p[2];
+            const uint4* p =
+                reinterpret_cast<const uint4*>((side ? w.kba : w.kab) + (long long)TC_KEYS * g);
+            const uint4 v0 = p[0], v1 = p[1], v2 = p[2];
+            // quarter t's keys are kk[3 t], kk[3 t + 1], kk[3 t + 2], smallest first
+            kk[0] = v0.x, kk[1] = v0.y, kk[2] = v0.z, kk[3] = v0.w;
+            kk[4] = v1.x, kk[5] = v1.y, kk[6] = v1.z, kk[7] = v1.w;
+            kk[8] = v2.x, kk[9] = v2.y, kk[10] = v2.z, kk[11] = v2.w;
+            const unsigned kmin = min(min(kk[0], kk[3]), min(kk[6], kk[9]));
             const float3 x = frame_row(w, fr, side, i);
             qx = x.x, qy = x.y, qz = x.z;
-            const float sx = __fmul_rn(__fsub_rn(qx, box.x), box.w);
-            const float sy = __fmul_rn(__fsub_rn(qy, box.y), box.w);
-            const float sz = __fmul_rn(__fsub_rn(qz, box.z), box.w);
-            r = sqrtf(__fmaf_rn(sz, sz, __fmaf_rn(sy, sy, __fmul_rn(sx, sx)))) *
-                (1.0f + 0x1p-20f);
+            if (kmin == TC_EMPTY) {
+                full = true;  // no key at all: scan the whole frame
+            } else {
+                const float4 box = w.fbox[k];
+                const float sx = __fmul_rn(__fsub_rn(qx, box.x), box.w);
+                const float sy = __fmul_rn(__fsub_rn(qy, box.y), box.w);
+                const float sz = __fmul_rn(__fsub_rn(qz, box.z), box.w);
+                const float r = sqrtf(__fmaf_rn(sz, sz, __fmaf_rn(sy, sy, __fmul_rn(sx, sx)))) *
+                                (1.0f + 0x1p-20f);
+                const float tau = tc_tau(kmin, r);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const unsigned key = kk[3 * t + j];
+                        if (key != TC_EMPTY && key_value(key) <= tau) cmask |= 1u << (2 * t + j);
+                    }
+                    // the quarter may hide a candidate beyond its keys
+                    if (kk[3 * t + 2] != TC_EMPTY && key_value(kk[3 * t + 2]) <= tau) full = true;
+                }
+            }
         }
-        unsigned kmin = kk[0];
-        kmin = min(kmin, (unsigned)__shfl_xor_sync(0xffffffffu, kmin, 1));
-        kmin = min(kmin, (unsigned)__shfl_xor_sync(0xffffffffu, kmin, 2));
-        unsigned c0 = TC_EMPTY, c1 = TC_EMPTY;
-        bool open = valid;  // this lane's quarter may hide a candidate beyond its keys
-        if (valid && kmin != TC_EMPTY) {
-            const float tau = tc_tau(kmin, r);
-            // candidates as (block << 2 | the pass's lane whose columns they name)
-            if (kk[0] != TC_EMPTY && key_value(kk[0]) <= tau)
-                c0 = ((kk[0] & ~TC_VALUE_MASK) << 2) | (unsigned)q;
-            if (kk[1] != TC_EMPTY && key_value(kk[1]) <= tau)
-                c1 = ((kk[1] & ~TC_VALUE_MASK) << 2) | (unsigned)q;
-            open = kk[2] != TC_EMPTY && key_value(kk[2]) <= tau;
+        if (!valid || full) cmask = 0;
+        const int nc = __popc(cmask);
+        // the warp's candidates, laid out by an exclusive prefix sum of the rows' counts
+        int off = nc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += y;
         }
-        const bool full = ((__ballot_sync(0xffffffffu, open) >> gl) & 0xFu) != 0u;
-        // the warp's (row, candidate block) entries, in any order: each is scanned by eight
-        // lanes and merged into its row's minimum
-        const bool use = valid && !full;
-        const unsigned b0 = __ballot_sync(0xffffffffu, use && c0 != TC_EMPTY);
-        const unsigned b1 = __ballot_sync(0xffffffffu, use && c1 != TC_EMPTY);
-        const int n0 = __popc(b0), tot = n0 + __popc(b1);
-        if (q == 0) {
-            s_q[warp][grp][0] = qx;
-            s_q[warp][grp][1] = qy;
-            s_q[warp][grp][2] = qz;
-            s_best[warp][grp] = EMPTY;
-        }
-        if (use && c0 != TC_EMPTY) s_list[warp][__popc(b0 & lt)] = (c0 << 3) | (unsigned)grp;
-        if (use && c1 != TC_EMPTY)
-            s_list[warp][n0 + __popc(b1 & lt)] = (c1 << 3) | (unsigned)grp;
+        const int tot = __shfl_sync(0xffffffffu, off, 31);
+        off -= nc;
+        s_q[warp][lane][0] = qx;
+        s_q[warp][lane][1] = qy;
+        s_q[warp][lane][2] = qz;
+        s_best[warp][lane] = EMPTY;
+        // candidates as (block << 2 | the pass's lane whose columns they name) << 5 | row
+#pragma unroll
+        for (int j = 0; j < REC_MAX_CAND; ++j)
+            if (cmask & (1u << j))
+                s_list[warp][off + __popc(cmask & ((1u << j) - 1u))] =
+                    ((((kk[(j >> 1) * 3 + (j & 1)] & ~TC_VALUE_MASK) << 2) | (unsigned)(j >> 1))
+                     << 5) | (unsigned)lane;
         __syncwarp();
+        // each candidate is scanned by eight lanes and merged into its row's minimum
         for (int e0 = 0; e0 < tot; e0 += 4) {
             const int e = e0 + sub;
             float bd = INFINITY;
-            int bj = 0x7fffffff, eg = -1;
+            int bj = 0x7fffffff, er = -1;
             if (e < tot) {
                 const unsigned ent = s_list[warp][e];
-                eg = (int)(ent & 7u);
-                const unsigned c = ent >> 3;
+                er = (int)(ent & 31u);
+                const unsigned c = ent >> 5;
                 const int blk = (int)(c >> 2), tq = (int)(c & 3u);
-                const float ex = s_q[warp][eg][0], ey = s_q[warp][eg][1], ez = s_q[warp][eg][2];
+                const float ex = s_q[warp][er][0], ey = s_q[warp][er][1], ez = s_q[warp][er][2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     // the block's columns that the pass's lane tq saw: 2 of every group of 8;
@@ -502,10 +518,10 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 1));
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 2));
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 4));
-            if (l8 == 0 && eg >= 0) atomicMin(&s_best[warp][eg], key);
+            if (l8 == 0 && er >= 0) atomicMin(&s_best[warp][er], key);
         }
         __syncwarp();
-        if (valid && q == 0) {
+        if (valid) {
             u64* out = side ? w.pba : w.pab;
             if (full) {
                 out[g] = EMPTY;
@@ -514,7 +530,7 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
                 w.tcfb[(side ? rows + fr->col0 : fr->row0) + slot] = i;
                 atomicAdd(&w.hdr->tc_fallback, 1);
             } else {
-                out[g] = s_best[warp][grp];
+                out[g] = s_best[warp][lane];
             }
         }
         __syncwarp();  // the next step reuses the warp's shared lists
@@ -1068,7 +1084,7 @@ cudaError_t launch_tcpass(const Ws& w, int engine, int grid, long long total_chu
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int steps = div_up(total, REC_THREADS / 4);
+    const int steps = div_up(total, REC_THREADS);
     const int rgrid = std::min(steps, 8 * (sms > 0 ? sms : 1));
     e = launch_pdl(k_tcrecover, rgrid, REC_THREADS, 0, s, w, rows, total);
     count_launch();
