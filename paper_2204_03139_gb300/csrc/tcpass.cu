@@ -610,42 +610,41 @@ __global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows, int s
 
 // ---------------------------------------------------------------------------------------
 // The same filter on the fifth-generation tensor cores: tcgen05 MMAs write the distances to
-// tensor memory asynchronously. A CTA holds a 512-row unit as four tiles of M = 128 rows, one
-// row per thread of 16 consumer warps (tile t is read by warps 4t .. 4t+3, one lane quarter
-// each). Each tile has two slots of 64 columns of tensor memory, one per half of a block of
-// TC_BLOCK columns, so tensor memory (4 tiles x 2 slots x 64 columns) is full. One MMA
-// (N = 64, K = 16) fills one slot; a consumer warp reads its tile's two slots in turn, so a
-// slot's refill runs while the warp reads the other one. Each warp folds the block into the
-// four column subsets (2 of every 8) and their block keys exactly as the warp-level kernel
-// does, so the keys, their merge across CTAs and the recovery are shared.
+// tensor memory asynchronously. A CTA takes a 512-row unit in two halves of 256 rows, each
+// two tiles of M = 128 rows. Each tile has two slots of 128 columns of tensor memory (2 tiles
+// x 2 slots x 128 columns fill it), and one MMA (N = 128, K = 16) fills a slot with the
+// distances of one key block of TC_BLOCK columns: slot 0 takes the even blocks, slot 1 the
+// odd ones. 8 consumer warps hold one row per thread (tile t is read by warps 4t .. 4t+3, one
+// lane quarter each) and read their tile's two slots in turn, so a slot's refill with the
+// block after next runs while the warp reads the other one. Each warp folds a block into the
+// four column subsets (2 of every 8) and their keys exactly as the warp-level kernel does, so
+// the keys, their merge across CTAs and the recovery are shared. One MMA warp per slot
+// issues its MMAs (a bounded wait for the slot's release and for the chunk, then the MMA and
+// its commit), and a producer warp streams the column chunks through four shared-memory
+// buffers with bulk copies.
 //
-// The MMAs are issued by four more warps, one per SM sub-partition, each for two slots: its
-// thread polls both slots (and the first also streams the column chunks with bulk copies)
-// and issues whichever slot its readers have released, so no consumer warp ever waits on an
-// issue and no slot waits behind another. An isolated tcgen05 MMA occupies its issuing thread
-// for a few hundred cycles, at K = 16 as long as the product itself takes, which is why the
-// issue has threads of its own.
+// An MMA issues at a fixed cost of about as many cycles as an N = 128, K = 16 product takes,
+// whatever N up to 128, and every slot read costs its warp a wait, a vote, fences and an
+// arrival; 128-column slots halve that cost per distance against 64-column ones.
 // ---------------------------------------------------------------------------------------
-constexpr int T5_CWARPS = 16;                          // consumer warps (one row per thread)
-constexpr int T5_MWARPS = 4;                           // MMA-issuing warps
-constexpr int T5_THREADS = 32 * (T5_CWARPS + T5_MWARPS);
-constexpr int T5_N = 64;                               // columns per MMA: half a key block
+constexpr int T5_CWARPS = 8;                           // consumer warps (one row per thread)
+constexpr int T5_MWARPS = 4;                           // MMA-issuing warps, one per slot
+constexpr int T5_THREADS = 32 * (T5_CWARPS + T5_MWARPS + 1);  // and the producer warp
+constexpr int T5_N = TC_BLOCK;                         // columns per MMA: one key block
 constexpr int T5_KB = TC_CHUNK / TC_BLOCK;             // key blocks per staged chunk
 constexpr int T5_BUFS = 4;                             // staged chunks
-constexpr int T5_TILES = TC_UNIT_ROWS / 128;           // tiles of M = 128 rows
-constexpr int T5_SLOTS = 2 * T5_TILES;                 // (tile, half block)
+constexpr int T5_HALF = 256;                           // rows per half unit (two tiles)
+constexpr int T5_SLOTS = 4;                            // (tile, block parity)
 constexpr uint32_t T5_TMEM_COLS = T5_SLOTS * T5_N;     // 512: all of an SM's tensor memory
-// MMAs that read one staged chunk: every slot, once per key block of the chunk
-constexpr int T5_CHUNK_READS = T5_SLOTS * T5_KB;
+// MMAs that read one staged chunk in a half: each slot once (two tiles x two blocks)
+constexpr int T5_CHUNK_READS = T5_SLOTS;
 // dynamic shared memory: the staged chunks, padded so that one CTA fills an SM (the CTA
 // allocates all of the SM's tensor memory)
 constexpr int T5_SMEM_B = T5_BUFS * TC_CHUNK * 32;     // 32 KB of staged chunks
 constexpr int T5_SMEM = 100 * 1024;
-static_assert(TC_BLOCK == 2 * T5_N && T5_KB == 2 && T5_TILES == 4 && T5_TMEM_COLS == 512,
-              "two MMAs per key block, two key blocks per chunk, tensor memory full");
+static_assert(T5_KB == 2 && TC_UNIT_ROWS == 2 * T5_HALF && T5_TMEM_COLS == 512,
+              "two key blocks per chunk, two halves per unit, tensor memory full");
 static_assert(T5_SMEM_B <= T5_SMEM, "dynamic shared memory");
-static_assert(T5_THREADS % 128 == 0, "whole warps per sub-partition");
-constexpr unsigned T5_POLL_NS = 40;  // back-off of an issuing thread that found nothing to do
 
 // shared-memory matrix descriptor of a K-major operand without swizzle, as the staging lays
 // it out: core matrices of 8 rows x 16 bytes, 128 bytes between the two halves of K (the
@@ -711,26 +710,6 @@ __device__ __forceinline__ void t5_fold(const float (&v)[32], float (&bm)[4], bo
     }
 }
 
-__device__ __forceinline__ void mbar_arrive_n(u64* bar, uint32_t n) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n)
-                 : "memory");
-}
-// non-blocking test of phase `parity`
-__device__ __forceinline__ bool mbar_test(u64* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
-        "selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// slot (tile, hb) of the MMA warp m, i = 0, 1: the first half block of tile m, the second of
-// tile m + 2 (mod 4); the consumer warp of lane quarter m of that tile reports its chunk reads
-__device__ __forceinline__ int t5_slot_of(int m, int i) { return i == 0 ? 2 * m : 2 * ((m + 2) & 3) + 1; }
-
 __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int dyn) {
     pdl_wait();
     __shared__ __align__(1024) uint4 s_a[TC_UNIT_ROWS * 2];  // A forms of the unit, 16 KB
@@ -742,12 +721,12 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int 
         s_free[T5_SLOTS], s_drain;
     __shared__ uint32_t s_tmem;
     __shared__ TcSeg s_u;
+    __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool mwarp = warp >= T5_CWARPS;
-    const int m = warp - T5_CWARPS;            // MMA warp index (sub-partition), if mwarp
-    const bool mt = mwarp && lane == 0;        // an issuing thread
-    const bool stager = mt && m == 0;          // the thread that also streams the chunks
+    const bool consumer = warp < T5_CWARPS;
+    const bool mwarp = warp >= T5_CWARPS && warp < T5_CWARPS + T5_MWARPS;
+    const bool producer = warp == T5_CWARPS + T5_MWARPS;
     const int n_units = w.hdr->tc_units, total = w.hdr->tc_total;
     // the work split of the warp-level kernel: stream-K, or whole units on demand (dyn)
     int s = 0, s_end = 0, u = 0;
@@ -758,7 +737,6 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int 
         if (s >= s_end) return;
         u = last_le(w.tc_upre, n_units, s);
     }
-    __shared__ int s_next;
     const long long tot_rows = w.hdr->total_rows;
 
     if (warp == 0) {
@@ -778,7 +756,7 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int 
         }
         for (int i = 0; i < T5_SLOTS; ++i) {
             mbar_init(&s_full[i], 1);
-            mbar_init(&s_free[i], 4);  // the four warps that read the slot
+            mbar_init(&s_free[i], 4);  // the tile's four warps
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -786,25 +764,25 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int 
     __syncthreads();
     t5_fence_after();
     const uint32_t tmem = s_tmem;
-    // consumer warp: tile and lane quarter; slot (tile, hb) holds tensor-memory columns
-    // 64 (2 tile + hb) ..; the warp of lane quarter (tile + 2 hb) % 4 reports the chunk reads
-    // of that slot's MMAs
-    const int quarter = warp & 3, tile = (warp >> 2) & 3;
-    const int rep_hb = ((quarter - tile) & 3) >> 1;
-    const bool reporter = !mwarp && ((quarter - tile) & 1) == 0 && lane == 0;
+    // consumer warp: tile and lane quarter; slot (tile, parity) holds tensor-memory columns
+    // 128 (2 tile + parity) ..; MMA warp m issues the MMAs of slot m
+    const int quarter = warp & 3, tile = (warp >> 2) & 1;
+    const int my_slot = warp - T5_CWARPS;
+    const bool issuer = mwarp && lane == 0;
+    const bool stager = producer && lane == 0;
 
-    int uses0 = 0, uses1 = 0;    // consumer: blocks read from its two slots (barrier phases)
-    int nis0 = 0, nis1 = 0;      // issuing thread: MMAs issued into its two slots
-    uint32_t pend_b = 0;         // stager: buffers with a copy in flight
-    uint32_t pend_p = 0;         // and the phase that copy completes
-    long long chunk0 = 0;        // chunks staged before this segment (buffer of chunk k: k % 4)
-    int n_seg = 0;               // segments begun (phase of the A barrier)
+    int use0 = 0, use1 = 0;  // consumer: blocks read from its tile's slots 0 and 1
+    int nis = 0;             // issuing thread: MMAs issued into its slot
+    uint32_t pend_b = 0;     // stager: buffers with a copy in flight
+    uint32_t pend_p = 0;     // and the phase that copy completes
+    long long chunk0 = 0;    // chunks staged before this pass (buffer of chunk k: k % 4)
+    int n_seg = 0;           // segments begun (phase of the A barrier)
     bool abort = false, issued = false;
 
     while (!abort) {
         __syncthreads();  // the previous segment is done with s_u and s_a
         if (dyn) {
-            if (stager) s_next = atomicAdd(&w.hdr->tc_next, 1);
+            if (tid == 0) s_next = atomicAdd(&w.hdr->tc_next, 1);
             __syncthreads();
             u = s_next;
             if (u >= n_units) break;
@@ -836,144 +814,124 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int 
         }
         __syncthreads();
         const int c_lo = s_u.c_lo, c_hi = s_u.c_hi;
-        const int ntiles = min(T5_TILES, s_u.rows_live / 128);  // 2 or 4
+        const int nhalves = s_u.rows_live >= TC_UNIT_ROWS ? 2 : 1;
         const int nkb = (c_hi - c_lo + 1) * T5_KB;
 
-        if (mt) {
-            // per own slot: the next key block to issue (nkb when done, or when its tile has
-            // no rows in this unit)
-            int next[2];
-            const int sl[2] = {t5_slot_of(m, 0), t5_slot_of(m, 1)};
-#pragma unroll
-            for (int i = 0; i < 2; ++i) next[i] = (sl[i] >> 1) < ntiles ? 0 : nkb;
-            int cnext = stager ? c_lo : c_hi + 1;  // next chunk to stage
-            bool a_ready = false;
-            u64 t_last = globaltimer();
-            int spins = 0;
-            while (next[0] < nkb || next[1] < nkb || cnext <= c_hi) {
-                bool progress = false;
-                if (cnext <= c_hi) {
-                    // chunk k reuses the buffer of chunk k - 4 once the MMAs that read that
-                    // one are complete
-                    const long long k = chunk0 + (cnext - c_lo);
+        for (int h = 0; h < nhalves && !abort; ++h) {
+            if (stager) {
+                // stream the pass's chunks; chunk k reuses the buffer of chunk k - 4 once the
+                // MMAs that read that one are complete
+                for (int c = c_lo; c <= c_hi; ++c) {
+                    const long long k = chunk0 + (c - c_lo);
                     const int b = (int)(k & (T5_BUFS - 1));
-                    if (k < T5_BUFS || mbar_test(&s_cfree[b], (uint32_t)(((k >> 2) - 1) & 1))) {
-                        if (!(stall && k == 0)) {  // test of the bounded waits only
-                            mbar_expect_tx(&s_bar_b[b], TC_CHUNK * 32);
-                            bulk_g2s(s_b + b * (TC_CHUNK * 2),
-                                     w.tcb + 2 * (s_u.bcol + (long long)cnext * TC_CHUNK),
-                                     TC_CHUNK * 32, &s_bar_b[b]);
-                            pend_b |= 1u << b;
-                            pend_p = (pend_p & ~(1u << b)) | ((uint32_t)((k >> 2) & 1) << b);
-                        }
-                        ++cnext;
-                        progress = true;
-                    }
-                }
-                if (!a_ready) a_ready = mbar_test(&s_bar_a, (uint32_t)(n_seg & 1));
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    if (!a_ready || next[i] >= nkb) continue;
-                    const int slot = sl[i];
-                    const int nis = i ? nis1 : nis0;
-                    // the slot's previous block has been read by its four warps
-                    if (nis > 0 && !mbar_test(&s_free[slot], (uint32_t)((nis - 1) & 1))) continue;
-                    const int kb = next[i];
-                    const long long k = chunk0 + kb / T5_KB;
-                    const int b = (int)(k & (T5_BUFS - 1));
-                    if (!mbar_test(&s_bar_b[b], (uint32_t)((k >> 2) & 1))) continue;
-                    t5_fence_after();
-                    const uint32_t off =
-                        (uint32_t)(((kb % T5_KB) * TC_BLOCK + (slot & 1) * T5_N) * 32);
-                    t5_mma(tmem + (uint32_t)(slot * T5_N),
-                           t5_desc(smem_u32(&s_a[0]) + (uint32_t)((slot >> 1) * 4096)),
-                           t5_desc(smem_u32(s_b + b * (TC_CHUNK * 2)) + off));
-                    t5_commit(&s_full[slot]);
-                    issued = true;
-                    if (i) ++nis1; else ++nis0;
-                    ++next[i];
-                    progress = true;
-                }
-                if (progress) {
-                    spins = 0;
-                    t_last = globaltimer();
-                    continue;
-                }
-                // nothing to do yet: leave the issue slots to the consumer warps for a while
-                __nanosleep(T5_POLL_NS);
-                if (++spins >= 64) {
-                    spins = 0;
-                    if (globaltimer() - t_last > WAIT_LIMIT_NS) {
+                    if (k >= T5_BUFS && !mbar_wait(&s_cfree[b], (uint32_t)(((k >> 2) - 1) & 1))) {
                         abort = true;
                         break;
                     }
+                    if (stall && k == 0) continue;  // test of the bounded waits only
+                    mbar_expect_tx(&s_bar_b[b], TC_CHUNK * 32);
+                    bulk_g2s(s_b + b * (TC_CHUNK * 2),
+                             w.tcb + 2 * (s_u.bcol + (long long)c * TC_CHUNK), TC_CHUNK * 32,
+                             &s_bar_b[b]);
+                    pend_b |= 1u << b;
+                    pend_p = (pend_p & ~(1u << b)) | ((uint32_t)((k >> 2) & 1) << b);
                 }
-            }
-        } else if (!mwarp && tile < ntiles) {
-            // with two tiles live, each live slot's MMA stands for two slots' reads of a chunk
-            const uint32_t reads = (uint32_t)(T5_TILES / ntiles);
-            bool ok = true;
-            float bm[4];
-            unsigned k1[4], k2[4], k3[4];
+            } else if (issuer) {
+                // slot my_slot: tile my_slot / 2, key blocks of parity my_slot % 2
+                const int mt = my_slot >> 1, par = my_slot & 1;
+                const uint64_t a_desc =
+                    t5_desc(smem_u32(&s_a[0]) + (uint32_t)((2 * h + mt) * 4096));
+                bool ok = h > 0 || mbar_wait(&s_bar_a, (uint32_t)(n_seg & 1));
+                int first = 1;
+                for (int kb = par; ok && kb < nkb; kb += 2) {
+                    if (!first) {
+                        // the slot's previous block has been read: its chunk has one reader
+                        // fewer, and the slot takes this block
+                        ok = mbar_wait(&s_free[my_slot], (uint32_t)((nis - 1) & 1));
+                        if (!ok) break;
+                        mbar_arrive(&s_cfree[(int)((chunk0 + (kb - 2) / T5_KB) & (T5_BUFS - 1))]);
+                    }
+                    first = 0;
+                    const long long k = chunk0 + kb / T5_KB;
+                    const int b = (int)(k & (T5_BUFS - 1));
+                    ok = mbar_wait(&s_bar_b[b], (uint32_t)((k >> 2) & 1));
+                    if (!ok) break;
+                    t5_fence_after();
+                    t5_mma(tmem + (uint32_t)(my_slot * T5_N), a_desc,
+                           t5_desc(smem_u32(s_b + b * (TC_CHUNK * 2)) +
+                                   (uint32_t)((kb % T5_KB) * TC_BLOCK * 32)));
+                    t5_commit(&s_full[my_slot]);
+                    issued = true;
+                    ++nis;
+                }
+                // the last block of the pass: once read, its chunk has one reader fewer
+                if (ok) {
+                    const int last = par + ((nkb - 1 - par) / 2) * 2;
+                    ok = mbar_wait(&s_free[my_slot], (uint32_t)((nis - 1) & 1));
+                    if (ok) mbar_arrive(&s_cfree[(int)((chunk0 + last / T5_KB) & (T5_BUFS - 1))]);
+                }
+                abort = !ok;
+            } else if (consumer) {
+                bool ok = true;
+                float bm[4];
+                unsigned k1[4], k2[4], k3[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) k1[t] = k2[t] = k3[t] = TC_EMPTY;
-            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
-            for (int kb = 0; ok && kb < nkb; ++kb) {
-#pragma unroll
-                for (int hb = 0; hb < 2; ++hb) {
-                    const int slot = 2 * tile + hb;
-                    const int uses = hb ? uses1 : uses0;
-                    if (!__all_sync(0xffffffffu,
-                                    mbar_wait(&s_full[slot], (uint32_t)(uses & 1)))) {
+                for (int t = 0; t < 4; ++t) k1[t] = k2[t] = k3[t] = TC_EMPTY;
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int sl = 2 * tile + (kb & 1);
+                    const int use = (kb & 1) ? use1 : use0;
+                    if (!__all_sync(0xffffffffu, mbar_wait(&s_full[sl], (uint32_t)(use & 1)))) {
                         ok = false;
                         break;
                     }
                     t5_fence_after();
+                    const uint32_t ta = taddr + (uint32_t)(sl * T5_N);
                     float v[32];
-                    t5_ld32(taddr + (uint32_t)(slot * T5_N), v);
-                    t5_fold(v, bm, hb == 0);
-                    t5_ld32(taddr + (uint32_t)(slot * T5_N + 32), v);
+#pragma unroll 1
+                    for (int i = 0; i < T5_N / 32 - 1; ++i) {
+                        t5_ld32(ta + 32 * i, v);
+                        t5_fold(v, bm, i == 0);
+                    }
+                    t5_ld32(ta + T5_N - 32, v);
                     // the slot is read: release it to its next MMA, then fold
                     t5_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&s_free[slot]);
-                    // this slot's MMA is complete: its chunk has fewer readers left
-                    if (reporter && hb == rep_hb)
-                        mbar_arrive_n(&s_cfree[(int)((chunk0 + kb / T5_KB) & (T5_BUFS - 1))],
-                                      reads);
+                    if (lane == 0) mbar_arrive(&s_free[sl]);
+                    if (kb & 1) ++use1; else ++use0;
                     t5_fold(v, bm, false);
-                    if (hb) ++uses1; else ++uses0;
-                }
-                if (!ok) break;
-                // the block's keys: value clamped at 0 and truncated, with the block (the
-                // subset is implied by the key's slot)
-                const unsigned id = (unsigned)(c_lo * T5_KB + kb);
+                    // the block's keys: value clamped at 0 and truncated, with the block (the
+                    // subset is implied by the key's slot)
+                    const unsigned id = (unsigned)(c_lo * T5_KB + kb);
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    top3_insert(k1[t], k2[t], k3[t],
-                                (__float_as_uint(fmaxf(bm[t], 0.0f)) & TC_VALUE_MASK) | id);
-            }
-            abort = !ok;
-            if (ok) {
-                unsigned* out =
-                    s_u.whole ? s_u.kout
-                              : w.kpart + TC_KEYS * ((2LL * blockIdx.x + s_u.slot) * TC_UNIT_ROWS);
-                unsigned* o = out + TC_KEYS * (tile * 128 + quarter * 32 + lane);
+                    for (int t = 0; t < 4; ++t)
+                        top3_insert(k1[t], k2[t], k3[t],
+                                    (__float_as_uint(fmaxf(bm[t], 0.0f)) & TC_VALUE_MASK) | id);
+                }
+                abort = !ok;
+                if (ok) {
+                    unsigned* out = s_u.whole
+                                        ? s_u.kout
+                                        : w.kpart + TC_KEYS * ((2LL * blockIdx.x + s_u.slot) *
+                                                               TC_UNIT_ROWS);
+                    unsigned* o = out + TC_KEYS * (h * T5_HALF + tile * 128 + quarter * 32 + lane);
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    o[3 * t] = k1[t];
-                    o[3 * t + 1] = k2[t];
-                    o[3 * t + 2] = k3[t];
+                    for (int t = 0; t < 4; ++t) {
+                        o[3 * t] = k1[t];
+                        o[3 * t + 1] = k2[t];
+                        o[3 * t + 2] = k3[t];
+                    }
                 }
             }
+            // a wait that gave up anywhere ends the CTA's work (every other wait then gives
+            // up too, since no further MMA is issued or read, so every warp gets here)
+            abort = __syncthreads_or(abort) != 0;
+            if (abort) break;
+            // every copy of the pass has landed: each was waited for before its MMAs
+            pend_b = 0;
+            chunk0 += c_hi - c_lo + 1;
         }
-        // a wait that gave up anywhere ends the CTA's work (every other wait then gives up
-        // too, since no further MMA is issued or read, so every warp gets here)
-        abort = __syncthreads_or(abort) != 0;
         if (abort) break;
-        // every copy of the segment has landed: each was waited for before its MMAs
-        pend_b = 0;
-        chunk0 += c_hi - c_lo + 1;
         ++n_seg;
         if (!dyn) {
             s = min(s_end, w.tc_upre[u + 1]);
@@ -985,7 +943,7 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int 
         if (tid == 0) set_status(&w.hdr->status, DC_ETIMEOUT);
         // let the MMAs and copies still in flight finish before the CTA's tensor memory and
         // shared memory go away
-        if (mt) {
+        if (issuer) {
             if (issued)
                 t5_commit(&s_drain);
             else
