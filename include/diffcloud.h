@@ -230,7 +230,7 @@ int dc_batch_run(void* ws, float* loss_total, dc_stream_t stream);
  *     cannot certify the blocks). Frames of at most 524 288 points per side.
  *     DC_ENGINE_AUTO takes it for calls (and batch plans) of at least 1e9 pairs and 5e7
  *     pairs per frame on average, where it pays back its fixed costs; else the direct engine.
- *   DC_ENGINE_TCGEN05 -- the same filter on tcgen05 MMAs (128 points x 64 candidates each)
+ *   DC_ENGINE_TCGEN05 -- the same filter on tcgen05 MMAs (128 points x 128 candidates each)
  *     into tensor memory; same keys, same recovery, same results.
  *   DC_ENGINE_DIRECT -- every pair in the direct form on the CUDA cores; a CTA of w warps
  *     (w = 1, 2 or 4) holds w * 512 sim points in registers while target chunks stream
