@@ -143,7 +143,8 @@ class BatchPipeline:
         draws [sum N,3], targets [sum M,3]) host tensors (pinned for asynchronous copies);
         results go to the given pinned host tensors: grads_out (per trajectory [T,V,3]),
         total_out [1], frames_out (per trajectory [T]), each optional. Returns an event that
-        completes when the results are on the host."""
+        completes when the results are on the host; the caller must not touch the input or
+        output host tensors before (the copies read and write them asynchronously)."""
         s = self._slots[self._k % self.depth]
         self._k += 1
         with torch.cuda.stream(self._s_in):
