@@ -384,8 +384,8 @@ constexpr int REC_MAX_CAND = 2 * 4;  // candidates per row: two blocks per colum
 // by walking the frame table forward). Each thread takes one row: it reads the row's 12 keys,
 // computes the threshold once, and lists the candidate blocks (per quarter of the columns,
 // the first two keys under the threshold); a warp prefix sum lays the warp's candidates out in
-// shared memory, and the warp re-checks them four at a time, eight lanes per candidate (its
-// 32 columns, four per lane) in the direct form, merging into the row's minimum with a shared
+// shared memory, and the warp re-checks them eight at a time, four lanes per candidate (its
+// 32 columns, eight per lane) in the direct form, merging into the row's minimum with a shared
 // atomicMin. A row that the keys do not certify (a quarter's third key under the threshold)
 // is queued in its frame's list for k_tcfallback. Writes (distance bits << 32 | index) to
 // pab / pba. (Four lanes per row, each with one quarter's keys, took 81 warp instructions
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
     const int st0 = blockIdx.x * per, st1 = min(steps, st0 + per);
     const int n_frames = w.hdr->n_frames;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sub = lane >> 3, l8 = lane & 7;
+    const int sub = lane >> 2, l4 = lane & 3;
     int k = -1, side = -1;
     for (int st = st0; st < st1; ++st) {
         const int base = st * REC_THREADS;
@@ -481,8 +481,8 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
                     ((((kk[(j >> 1) * 3 + (j & 1)] & ~TC_VALUE_MASK) << 2) | (unsigned)(j >> 1))
                      << 5) | (unsigned)lane;
         __syncwarp();
-        // each candidate is scanned by eight lanes and merged into its row's minimum
-        for (int e0 = 0; e0 < tot; e0 += 4) {
+        // each candidate is scanned by four lanes and merged into its row's minimum
+        for (int e0 = 0; e0 < tot; e0 += 8) {
             const int e = e0 + sub;
             float bd = INFINITY;
             int bj = 0x7fffffff, er = -1;
@@ -493,10 +493,10 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
                 const int blk = (int)(c >> 2), tq = (int)(c & 3u);
                 const float ex = s_q[warp][er][0], ey = s_q[warp][er][1], ez = s_q[warp][er][2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < 4; ++h) {
                     // the block's columns that the pass's lane tq saw: 2 of every group of 8;
-                    // this lane takes groups l8 and l8 + 8, in increasing column order
-                    const int j0 = blk * TC_BLOCK + 8 * (l8 + 8 * h) + 2 * tq;
+                    // this lane takes groups l4, l4 + 4, l4 + 8 and l4 + 12
+                    const int j0 = blk * TC_BLOCK + 8 * (l4 + 4 * h) + 2 * tq;
                     if (j0 >= C.n) continue;
                     float ax, ay, az, bx, by, bz;
                     if (C.P) {
@@ -514,11 +514,11 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
                     if (j0 + 1 < C.n && d1 < bd) bd = d1, bj = j0 + 1;
                 }
             }
+            // (distance bits << 32 | index): the smallest is the lowest index among equals
             u64 key = bj == 0x7fffffff ? EMPTY : pack_d(bd, bj);
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 1));
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 2));
-            key = min64(key, __shfl_xor_sync(0xffffffffu, key, 4));
-            if (l8 == 0 && er >= 0) atomicMin(&s_best[warp][er], key);
+            if (l4 == 0 && er >= 0) atomicMin(&s_best[warp][er], key);
         }
         __syncwarp();
         if (valid) {
