@@ -748,10 +748,16 @@ def run_batched(args, rank, world, dist):
                               "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
                               "frac": (mma_tflops / tpk) if (mma_tflops and tpk) else None}
         else:
+            # against the warp-level MMA rate this kernel can reach, and against the tensor
+            # cores' measured peak (f16 at the bf16 rate), which only tcgen05 MMAs approach
+            tpk = measured_peaks().get("bf16_tflops")
             roof["tensor"] = {"achieved": mma_tflops, "unit": "TFLOP/s (f16 MMA, 32 flop per "
                               "pair per direction)", "peak_mma_sync_measured": MMA_SYNC_TFLOPS,
                               "frac_of_mma_sync": (mma_tflops / MMA_SYNC_TFLOPS)
-                              if mma_tflops else None}
+                              if mma_tflops else None,
+                              "peak_tensor_measured": tpk,
+                              "frac_of_tensor_peak": (mma_tflops / tpk)
+                              if (mma_tflops and tpk) else None}
     line = {"metric": "chamfer_fwd_bwd_point_pairs_per_s", "value": world * pairs / (ms / 1e3),
             "unit": "pairs/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
