@@ -4,20 +4,22 @@
 // column point of its frame (the targets, respectively the sim points) through the
 // expanded form |p - q|^2 = |p|^2 - 2 p.q + |q|^2, evaluated on the tensor cores with the
 // split-fp16 forms that the staging kernel wrote (dc_internal.cuh): one m16n8k16 MMA gives
-// 16 rows x 8 columns of approximate scaled squared distances. Each of the four lanes that
-// share a row sees a quarter of every block's columns (2 of every 8); per row and lane the
-// filter keeps the three smallest block keys (approximate minimum over the lane's columns of
-// a block of TC_BLOCK, truncated, with the block); it never decides a neighbour. The
-// epilogue
-// re-evaluates the candidate blocks those keys admit in the exact float32 direct form of
-// the oracle, so neighbours and losses are those of the direct form.
+// 16 rows x 8 columns of approximate scaled squared distances (k_tcpass; k_tcpass5 does the
+// same with tcgen05 MMAs of 128 x 128). Each of the four lanes that share a row sees a
+// quarter of every block's columns (2 of every 8); per row and lane the filter keeps the
+// three smallest block keys (approximate minimum over the lane's columns of a block of
+// TC_BLOCK, truncated, with the block); it never decides a neighbour. k_tcrecover
+// re-evaluates the candidate blocks those keys admit, and k_tcfallback every column of the
+// rows they do not certify, in the exact float32 direct form of the oracle, so neighbours
+// and losses are those of the direct form.
 //
 // Work: units of TC_UNIT_ROWS rows of one side of one frame, times their chunks of
-// TC_CHUNK columns, flattened and split evenly over a persistent grid (every CTA gets the
-// same number of chunks). A unit covered by one CTA writes its rows' keys to their final
-// place; a unit split between CTAs writes each CTA's list to that CTA's slot in kpart
-// (slot 0 for the part a CTA started inside the unit, 1 for the part that ends the CTA's
-// range), and the epilogue merges them.
+// TC_CHUNK columns. With few units per CTA the flattened list is split evenly over a
+// persistent grid (every CTA gets the same number of chunks): a unit covered by one CTA
+// writes its rows' keys to their final place; a unit split between CTAs writes each CTA's
+// list to that CTA's slot in kpart (slot 0 for the part a CTA started inside the unit, 1 for
+// the part that ends the CTA's range), and k_tcmerge merges them. With many units per CTA
+// the CTAs take whole units in order from a counter instead.
 #include <cuda_fp16.h>
 
 #include <algorithm>
