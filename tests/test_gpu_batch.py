@@ -136,6 +136,30 @@ def test_batch_engines_agree(trajs, mode):
         parity.check_loss(outs["tcgen05"].loss_frames[k].cpu().numpy(), o["loss_frames"])
 
 
+@pytest.mark.timeout(180)
+@pytest.mark.parametrize("shape", [("tensor", 0), ("tcgen05", 0)])
+def test_bounded_waits_with_units_handed_out_on_demand(shape):
+    """1000 frames of 2048 points (8000 tensor-core units, many more than CTAs): the passes
+    hand out whole units from a counter. A launch whose first chunk is never requested in
+    any CTA must end with DC_ETIMEOUT, and the next run of the same plan must give the
+    normal result."""
+    from paper_2204_03139_gb300 import _lib
+    from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    trs = [W.lift_trajectory(W.SEED_BASE + 900 + k, 12, 100, 2048, 2048, name=f"d{k}")
+           for k in range(10)]
+    b = BatchedLoss([DeviceTrajectory.from_host(t, DEV) for t in trs], grad=True, shape=shape)
+    good = b.run(check=True).cpu().numpy().copy()
+    _lib.test_inject_stall()
+    b.run()
+    torch.cuda.synchronize()
+    assert _lib.ws_status(b.ws, b.stream) == _lib.DC_ETIMEOUT
+    again = b.run(check=True).cpu().numpy()
+    np.testing.assert_array_equal(again, good)
+
+
 @pytest.mark.slow
 def test_batched_uneven_full_size_sampled_frames():
     """All 64 trajectories of the uneven workload (grids 15x15..80x80, 20..100 frames, 2 000 to
