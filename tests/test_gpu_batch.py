@@ -141,8 +141,8 @@ def test_batch_engines_agree(trajs, mode):
 def test_bounded_waits_with_units_handed_out_on_demand(shape):
     """1000 frames of 2048 points (8000 tensor-core units, many more than CTAs): the passes
     hand out whole units from a counter. A launch whose first chunk is never requested in
-    any CTA must end with DC_ETIMEOUT, and the next run of the same plan must give the
-    normal result."""
+    any CTA must end with DC_ETIMEOUT, the next run of the same plan must give the normal
+    result, and its per-frame losses equal the direct engine's."""
     from paper_2204_03139_gb300 import _lib
     from paper_2204_03139_gb300.batch import BatchedLoss, DeviceTrajectory
 
@@ -158,6 +158,14 @@ def test_bounded_waits_with_units_handed_out_on_demand(shape):
     assert _lib.ws_status(b.ws, b.stream) == _lib.DC_ETIMEOUT
     again = b.run(check=True).cpu().numpy()
     np.testing.assert_array_equal(again, good)
+    # and in this mode the filter's per-frame losses equal the direct engine's bit for bit
+    ref = BatchedLoss([DeviceTrajectory.from_host(t, DEV) for t in trs], grad=True,
+                      shape=("direct", 2))
+    ref.run(check=True)
+    torch.cuda.synchronize()
+    for k in range(len(trs)):
+        np.testing.assert_array_equal(b.loss_frames[k].cpu().numpy(),
+                                      ref.loss_frames[k].cpu().numpy())
 
 
 @pytest.mark.slow
