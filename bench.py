@@ -690,7 +690,7 @@ def run_batched(args, rank, world, dist):
             float(o[1][0])
 
     run_pipe(2)
-    n_pipe = 4
+    n_pipe = 8
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     run_pipe(n_pipe)
