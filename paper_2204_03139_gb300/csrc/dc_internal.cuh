@@ -55,10 +55,17 @@ constexpr unsigned long long EMPTY = ~0ull;
 // four quad lanes that share a row each see a quarter of its columns; a lane's minimum over
 // its columns of a block of TC_BLOCK becomes a 32-bit key, (value bits truncated to 20) |
 // block, and every (row, lane) keeps its three smallest keys in a slot of its own.
-// Both forms are stored per group of 8 points as the two 8 x 16-byte halves of K (256 B).
+// Both forms are stored per group of 8 points as the two 8 x 16-byte halves of K (256 B),
+// in the order tc_form_pos gives within each block of TC_BLOCK points.
 // ---------------------------------------------------------------------------------------
-constexpr int TC_WARPS = 4;                                 // warps per CTA
-constexpr int TC_ROWS_PER_WARP = 128;                       // eight m16 tiles per warp
+#ifndef DC_TC_WARPS
+#define DC_TC_WARPS 4
+#endif
+#ifndef DC_TC_ROWS_PER_WARP
+#define DC_TC_ROWS_PER_WARP 128
+#endif
+constexpr int TC_WARPS = DC_TC_WARPS;                       // warps per CTA
+constexpr int TC_ROWS_PER_WARP = DC_TC_ROWS_PER_WARP;       // m16 tiles per warp, times 16
 constexpr int TC_UNIT_ROWS = TC_WARPS * TC_ROWS_PER_WARP;   // rows per work unit (512)
 constexpr int TC_CHUNK = 256;                               // columns per staged chunk
 constexpr int TC_BLOCK = 128;                               // columns per key block
@@ -82,6 +89,30 @@ constexpr long long TC_DYN_UNITS_PER_CTA = 16;
 static_assert(ROW_PAD % TC_UNIT_ROWS == 0 && COL_PAD % TC_CHUNK == 0 &&
                   TC_CHUNK % TC_BLOCK == 0 && TC_ROWS_PER_WARP % 16 == 0,
               "the tensor-core tiles nest in the padded sizes");
+
+// Form position of the point with form index p. Within a block of TC_BLOCK columns the MMA
+// fragments give quad lane t the positions 8 g + 2 t + e (g < 16, e < 2); the point
+// 32 t + 2 g + e is stored there, so that every lane's quarter of a block is 32 consecutive
+// points, which the recovery re-reads as whole lines (with the quarters interleaved, a
+// quarter's 32 points spanned the block's 128). Frames start at multiples of TC_BLOCK rows
+// and columns, so the map stays inside each frame, and rows are permuted the same way.
+__host__ __device__ inline long long tc_form_pos(long long p) {
+    const int b = (int)(p & (TC_BLOCK - 1));
+    return (p & ~(long long)(TC_BLOCK - 1)) | (((b >> 1) & 15) << 3) | ((b >> 5) << 1) | (b & 1);
+}
+// The point that staging thread slot p handles when the forms are written: within a block
+// the bit fields [6:5] and [4:3] of p are swapped, so that the 32 lanes of a warp (slots
+// 32 w .. 32 w + 31) take the points 32 t + 8 w + x (t < 4, x < 8), whose forms fill the 32
+// consecutive positions 32 w .. 32 w + 31 (whole lines), and whose other per-point records
+// are four runs of 8 consecutive points. An involution, inside each block.
+__host__ __device__ inline int tc_stage_point(int p) {
+    return (p & ~(TC_BLOCK - 1)) | (((p >> 3) & 3) << 5) | (((p >> 5) & 3) << 3) | (p & 7);
+}
+static_assert(TC_BLOCK == 128, "tc_form_pos splits a block into 4 quarters of 16 pairs");
+static_assert(ROW_PAD % TC_BLOCK == 0 && COL_PAD % TC_BLOCK == 0,
+              "frames start at block boundaries of the forms");
+static_assert(TC_BLOCK % TC_ROWS_PER_WARP == 0 || TC_ROWS_PER_WARP % TC_BLOCK == 0,
+              "a warp's rows are part of a block or whole blocks");
 
 // ENGINE_TC: the filter on warp-level MMAs; ENGINE_TC5: on tcgen05 MMAs into tensor memory.
 // Both write the same keys, which the same kernels merge and resolve.

@@ -116,28 +116,82 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiA
     const int i0 = (int)((long long)N * sl / e.slices);
     const int i1 = (int)((long long)N * (sl + 1) / e.slices);
     const bool exact = e.exact != 0 && rescan;
+    constexpr int STEP = NW * 8;  // rows of one warp step of the CTA
     float sab = 0.f, cab_c = 0.f;
-    for (int base = i0 + warp * 8; base < i1; base += NW * 8) {
+    if (exact) {
+        // The recovery kernels left (distance bits << 32 | neighbour) for every row. Two warp
+        // steps at a time, every load of both before any store: each lane keeps its rows and
+        // their order (the loss partials are those of one step at a time), and both rows'
+        // chains of dependent loads are in flight together.
+        for (int base = i0 + warp * 8; base < i1; base += 2 * STEP) {
+            int ir[2], nr[2];
+            bool vr[2];
+            u64 pr[2];
+            float4 xr[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                ir[r] = base + r * STEP + grp;
+                vr[r] = ir[r] < i1;
+                const int g = row0 + (vr[r] ? ir[r] : i0);
+                pr[r] = vr[r] ? __ldg(&w.pab[g]) : EMPTY;
+                xr[r] = __ldg(&w.x[g]);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                int nn = -1;
+                if (vr[r] && pr[r] != EMPTY) nn = (int)(pr[r] & 0xffffffffu);
+                if (vr[r] && q == 0) {
+                    if (pr[r] != EMPTY && want_loss)
+                        kahan_add(sab, cab_c, __uint_as_float((unsigned)(pr[r] >> 32)));
+                    if (pr[r] == EMPTY || (unsigned)nn >= (unsigned)M)
+                        set_status(&w.hdr->status, DC_EDEVICE);
+                    fr->nn_ab[ir[r]] = nn;
+                }
+                nr[r] = vr[r] && (unsigned)nn < (unsigned)M && q < 3 ? nn : -1;
+            }
+            if (grad) {
+                float yr[2][3] = {};
+                int4 fr4[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    fr4[r] = make_int4(-1, 0, 0, 0);
+                    if (nr[r] >= 0) {
+                        yr[r][0] = __ldg(&PX[nr[r]]);
+                        yr[r][1] = __ldg(&PY[nr[r]]);
+                        yr[r][2] = __ldg(&PZ[nr[r]]);
+                        fr4[r] = __ldg(&w.fw[row0 + ir[r]]);
+                    }
+                }
+                int vv[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    vv[r] = fr4[r].x >= 0 ? __ldg(&faces[3 * fr4[r].x + q]) : -1;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int v = vv[r];
+                    if ((unsigned)v < (unsigned)V) {
+                        const int4 fq = fr4[r];
+                        const float wq = __int_as_float(q == 0 ? fq.y : (q == 1 ? fq.z : fq.w));
+                        const float4 x = xr[r];
+                        atomicAdd(&G[3 * v + 0],
+                                  __fmul_rn(wq, __fmul_rn(cab, __fsub_rn(x.x, yr[r][0]))));
+                        atomicAdd(&G[3 * v + 1],
+                                  __fmul_rn(wq, __fmul_rn(cab, __fsub_rn(x.y, yr[r][1]))));
+                        atomicAdd(&G[3 * v + 2],
+                                  __fmul_rn(wq, __fmul_rn(cab, __fsub_rn(x.z, yr[r][2]))));
+                    }
+                }
+            }
+        }
+    }
+    for (int base = i0 + warp * 8; !exact && base < i1; base += STEP) {
         const int i = base + grp;
         const bool valid = i < i1;
         const int g = row0 + (valid ? i : i0);
         const float4 x = w.x[g];
         int nn = -1;
         float dmin = 0.f;
-        if (exact) {
-            // the recovery kernels left (distance bits << 32 | neighbour) for every row
-            const u64 p = valid ? w.pab[g] : EMPTY;
-            if (valid && p != EMPTY) {
-                nn = (int)(p & 0xffffffffu);
-                dmin = __uint_as_float((unsigned)(p >> 32));
-            }
-            if (valid && q == 0) {
-                if (p != EMPTY && want_loss) kahan_add(sab, cab_c, dmin);
-                if (p == EMPTY || (unsigned)nn >= (unsigned)M) set_status(&w.hdr->status, DC_EDEVICE);
-                fr->nn_ab[i] = nn;
-            }
-            if ((unsigned)nn >= (unsigned)M) nn = -1;
-        } else if (rescan) {
+        if (rescan) {
             const u64 p = valid ? w.pab[g] : EMPTY;
             int first = 0x7fffffff;
             if (p != EMPTY) {
@@ -202,27 +256,78 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_epilogue(Ws w, EpiA
     if (e.bidir) {
         const int j0 = (int)((long long)M * sl / e.slices);
         const int j1 = (int)((long long)M * (sl + 1) / e.slices);
-        for (int base = j0 + warp * 8; base < j1; base += NW * 8) {
+        if (exact) {
+            // as for the rows: two warp steps at a time, every load of both before any store
+            for (int base = j0 + warp * 8; base < j1; base += 2 * STEP) {
+                int jr[2], nr[2];
+                bool vr[2];
+                u64 pr[2];
+                float tr[2][3];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    jr[r] = base + r * STEP + grp;
+                    vr[r] = jr[r] < j1;
+                    const int jj = vr[r] ? jr[r] : j0;
+                    pr[r] = vr[r] ? __ldg(&w.pba[col0 + jj]) : EMPTY;
+                    tr[r][0] = __ldg(&PX[jj]);
+                    tr[r][1] = __ldg(&PY[jj]);
+                    tr[r][2] = __ldg(&PZ[jj]);
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    int nn = -1;
+                    if (vr[r] && pr[r] != EMPTY) nn = (int)(pr[r] & 0xffffffffu);
+                    if (vr[r] && q == 0) {
+                        if (pr[r] != EMPTY && want_loss)
+                            kahan_add(sba, cba_c, __uint_as_float((unsigned)(pr[r] >> 32)));
+                        if (pr[r] == EMPTY || (unsigned)nn >= (unsigned)N)
+                            set_status(&w.hdr->status, DC_EDEVICE);
+                        fr->nn_ba[jr[r]] = nn;
+                    }
+                    nr[r] = vr[r] && (unsigned)nn < (unsigned)N && q < 3 ? nn : -1;
+                }
+                if (grad) {
+                    float4 xm[2];
+                    int4 fr4[2];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        xm[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        fr4[r] = make_int4(-1, 0, 0, 0);
+                        if (nr[r] >= 0) {
+                            xm[r] = __ldg(&w.x[row0 + nr[r]]);
+                            fr4[r] = __ldg(&w.fw[row0 + nr[r]]);
+                        }
+                    }
+                    int vv[2];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+                        vv[r] = fr4[r].x >= 0 ? __ldg(&faces[3 * fr4[r].x + q]) : -1;
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int v = vv[r];
+                        if ((unsigned)v < (unsigned)V) {
+                            const int4 fq = fr4[r];
+                            const float wq =
+                                __int_as_float(q == 0 ? fq.y : (q == 1 ? fq.z : fq.w));
+                            atomicAdd(&G[3 * v + 0],
+                                      __fmul_rn(wq, __fmul_rn(cba, __fsub_rn(xm[r].x, tr[r][0]))));
+                            atomicAdd(&G[3 * v + 1],
+                                      __fmul_rn(wq, __fmul_rn(cba, __fsub_rn(xm[r].y, tr[r][1]))));
+                            atomicAdd(&G[3 * v + 2],
+                                      __fmul_rn(wq, __fmul_rn(cba, __fsub_rn(xm[r].z, tr[r][2]))));
+                        }
+                    }
+                }
+            }
+        }
+        for (int base = j0 + warp * 8; !exact && base < j1; base += STEP) {
             const int j = base + grp;
             const bool valid = j < j1;
             const int jj = valid ? j : j0;
             const float tx = PX[jj], ty = PY[jj], tz = PZ[jj];
             int nn = -1;
             float dmin = 0.f;
-            if (exact) {
-                const u64 p = valid ? w.pba[col0 + jj] : EMPTY;
-                if (valid && p != EMPTY) {
-                    nn = (int)(p & 0xffffffffu);
-                    dmin = __uint_as_float((unsigned)(p >> 32));
-                }
-                if (valid && q == 0) {
-                    if (p != EMPTY && want_loss) kahan_add(sba, cba_c, dmin);
-                    if (p == EMPTY || (unsigned)nn >= (unsigned)N)
-                        set_status(&w.hdr->status, DC_EDEVICE);
-                    fr->nn_ba[j] = nn;
-                }
-                if ((unsigned)nn >= (unsigned)N) nn = -1;
-            } else if (rescan) {
+            if (rescan) {
                 const u64 p = valid ? w.pba[col0 + jj] : EMPTY;
                 int first = 0x7fffffff;
                 if (p != EMPTY) {

@@ -107,9 +107,9 @@ __device__ __forceinline__ unsigned pack_h2(__half lo, __half hi) {
     return (unsigned)__half_as_ushort(lo) | ((unsigned)__half_as_ushort(hi) << 16);
 }
 
-// The A and B forms of form index p for the point (x, y, z) of a frame with box `box`; a
-// padding point gets forms that never win a minimum (A = 0; B adds TC_PAD_NORM, above any
-// real scaled squared distance, 4 * 3 * 64^2).
+// The A and B forms of form index p for the point (x, y, z) of a frame with box `box`,
+// stored at position tc_form_pos(p); a padding point gets forms that never win a minimum
+// (A = 0; B adds TC_PAD_NORM, above any real scaled squared distance, 4 * 3 * 64^2).
 __device__ __forceinline__ void write_forms(const Ws& w, long long p, float x, float y, float z,
                                             float4 box, bool real) {
     uint4 a0, a1, b0, b1;
@@ -141,8 +141,9 @@ __device__ __forceinline__ void write_forms(const Ws& w, long long p, float x, f
         a0 = a1 = b0 = make_uint4(0u, 0u, 0u, 0u);
         b1 = make_uint4(0u, 0u, pack_h2(pad, zero), pack_h2(one, one));
     }
-    // group of 8 points = 16 uint4: K 0..7 of the 8 points, then K 8..15
-    const long long q = (p >> 3) * 16 + (p & 7);
+    // group of 8 positions = 16 uint4: K 0..7 of the 8 points, then K 8..15
+    const long long s = tc_form_pos(p);
+    const long long q = (s >> 3) * 16 + (s & 7);
     w.tca[q] = a0;
     w.tca[q + 8] = a1;
     w.tcb[q] = b0;
@@ -589,7 +590,9 @@ __device__ __forceinline__ void fold_area_err(const Ws& w, int k) {
 
 __global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows, int fold, int tc) {
     pdl_entry();
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += gridDim.x * blockDim.x) {
+    // rows is a whole number of blocks, so the staging order covers every row once
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < rows; s += gridDim.x * blockDim.x) {
+        const int g = tc ? tc_stage_point(s) : s;
         const int k = last_le(w.rowpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
         if (fold && g == fr->row0) fold_area_err(w, k);
@@ -601,7 +604,8 @@ __global__ void __launch_bounds__(256) k_sample(Ws w, int n_frames, int rows, in
 
 __global__ void __launch_bounds__(256) k_targets(Ws w, int n_frames, int cols, int tc) {
     pdl_entry();
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < cols; g += gridDim.x * blockDim.x) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < cols; s += gridDim.x * blockDim.x) {
+        const int g = tc ? tc_stage_point(s) : s;
         const int k = last_le(w.colpre, n_frames, g);
         const FrameDesc* fr = w.frames + k;
         if (tc && g == fr->col0) {  // the frame's fallback lists start empty
@@ -635,17 +639,24 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage(Ws w, int slices, int r
     if (sampled)
         for (int f = threadIdx.x; f < fr->F; f += STAGE_THREADS) s_cdf[f] = w.cdf[fr->cdf0 + f];
     __syncthreads();
+    // slices of whole blocks, so that the staging order stays inside each slice
     if (rows) {
-        const int a = (int)((long long)fr->Npad * sl / slices);
-        const int b = (int)((long long)fr->Npad * (sl + 1) / slices);
-        for (int i = a + threadIdx.x; i < b; i += STAGE_THREADS)
+        const int nb = fr->Npad / TC_BLOCK;
+        const int a = (int)((long long)nb * sl / slices) * TC_BLOCK;
+        const int b = (int)((long long)nb * (sl + 1) / slices) * TC_BLOCK;
+        for (int s = a + threadIdx.x; s < b; s += STAGE_THREADS) {
+            const int i = tc ? tc_stage_point(s) : s;
             sample_row(w, fr, i, fr->row0 + i, s_cdf, tc != 0, box);
+        }
     }
     if (cols) {
-        const int a = (int)((long long)fr->Mpad * sl / slices);
-        const int b = (int)((long long)fr->Mpad * (sl + 1) / slices);
-        for (int j = a + threadIdx.x; j < b; j += STAGE_THREADS)
+        const int nb = fr->Mpad / TC_BLOCK;
+        const int a = (int)((long long)nb * sl / slices) * TC_BLOCK;
+        const int b = (int)((long long)nb * (sl + 1) / slices) * TC_BLOCK;
+        for (int s = a + threadIdx.x; s < b; s += STAGE_THREADS) {
+            const int j = tc ? tc_stage_point(s) : s;
             stage_target(w, fr, j, fr->col0 + j, tc != 0, box);
+        }
     }
 }
 

@@ -6,10 +6,11 @@
 // split-fp16 forms that the staging kernel wrote (dc_internal.cuh): one m16n8k16 MMA gives
 // 16 rows x 8 columns of approximate scaled squared distances (k_tcpass; k_tcpass5 does the
 // same with tcgen05 MMAs of 128 x 128). Each of the four lanes that share a row sees a
-// quarter of every block's columns (2 of every 8); per row and lane the filter keeps the
-// three smallest block keys (approximate minimum over the lane's columns of a block of
-// TC_BLOCK, truncated, with the block); it never decides a neighbour. k_tcrecover
-// re-evaluates the candidate blocks those keys admit, and k_tcfallback every column of the
+// quarter of every block's columns (2 of every 8 positions, which tc_form_pos fills with 32
+// consecutive points); per row and lane the filter keeps the three smallest block keys
+// (approximate minimum over the lane's columns of a block of TC_BLOCK, truncated, with the
+// block); it never decides a neighbour. k_tcrecover re-evaluates the candidate block
+// quarters those keys admit, and k_tcfallback every column of the
 // rows they do not certify, in the exact float32 direct form of the oracle, so neighbours
 // and losses are those of the direct form.
 //
@@ -45,13 +46,18 @@ struct TcSeg {
     long long arow;  // form index of the unit's first row
     long long bcol;  // form index of the frame's first column
     unsigned* kout;  // final keys of the unit's first row
-    int rows_live;   // rows of the unit that exist (padded rows included), from its first
+    int rows_live;   // rows of the unit to filter, from its first (k_tcpass: up to the
+                     // end of the block of the side's last point; k_tcpass5: every padded row)
     int c_lo, c_hi;  // chunk range of this segment
     int whole, slot;
 };
 
 constexpr int TC_THREADS = 32 * TC_WARPS;
-constexpr int TC_MIN_BLOCKS = 3;  // 12 warps per SM
+constexpr int TC_MT = TC_ROWS_PER_WARP / 16;  // m16 tiles per warp
+#ifndef DC_TC_MIN_BLOCKS
+#define DC_TC_MIN_BLOCKS 3
+#endif
+constexpr int TC_MIN_BLOCKS = DC_TC_MIN_BLOCKS;  // 3: 12 warps per SM
 
 // Work split. Stream-K (dyn = 0): CTA b takes the contiguous range [b per, (b + 1) per) of
 // the (unit, chunk) list, so every CTA gets the same number of chunks and a unit may be
@@ -115,7 +121,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
             const int side = urb >> 30, rb = urb & 0x3fffffff;
             const int upre = w.tc_upre[u], unext = w.tc_upre[u + 1];
             const long long first = (long long)rb * TC_UNIT_ROWS;
-            s_u.rows_live = (side ? fr->Mpad : fr->Npad) - (int)first;
+            // rows up to the end of the block of the side's last point: the forms spread a
+            // block's points over all its positions, and a warp tile beyond has no keys to
+            // give (nothing reads them)
+            s_u.rows_live = round_up(side ? fr->M : fr->N, TC_BLOCK) - (int)first;
             s_u.arow = (side ? tot_rows + fr->col0 : (long long)fr->row0) + first;
             s_u.bcol = side ? (long long)fr->row0 : tot_rows + fr->col0;
             s_u.kout = side ? w.kba + TC_KEYS * ((long long)fr->col0 + first)
@@ -137,14 +146,14 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
         }
         __syncthreads();
         const int wrow0 = warp * TC_ROWS_PER_WARP;  // within the unit
-        // a frame's padded row count is a multiple of 256, so a warp's 128 rows are all
-        // inside it or all beyond it (units of 512 rows may overhang the target side)
+        // a warp's rows lie in blocks that hold a point of the side, or in none (units of
+        // 512 rows may overhang the last point)
         const bool wactive = wrow0 < s_u.rows_live;
 
-        // this warp's eight m16 tiles of A forms, in registers for the whole segment
-        unsigned a[8][4];
+        // this warp's m16 tiles of A forms, in registers for the whole segment
+        unsigned a[TC_MT][4];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
+        for (int m = 0; m < TC_MT; ++m) {
             const long long p = wactive ? s_u.arow + wrow0 + 16 * m : 0;
             const long long G = p >> 3;  // first of the tile's two groups of 8 rows
             a[m][0] = A32[G * 64 + g * 4 + t];
@@ -152,9 +161,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
             a[m][2] = A32[G * 64 + 32 + g * 4 + t];
             a[m][3] = A32[(G + 1) * 64 + 32 + g * 4 + t];
         }
-        unsigned k1[16], k2[16], k3[16];  // rows 16 m + g (2 m) and 16 m + g + 8 (2 m + 1)
+        // rows 16 m + g (2 m) and 16 m + g + 8 (2 m + 1)
+        unsigned k1[2 * TC_MT], k2[2 * TC_MT], k3[2 * TC_MT];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) k1[r] = k2[r] = k3[r] = TC_EMPTY;
+        for (int r = 0; r < 2 * TC_MT; ++r) k1[r] = k2[r] = k3[r] = TC_EMPTY;
 
         const int c_lo = s_u.c_lo, c_hi = s_u.c_hi;
         for (int c = c_lo; c <= c_hi; ++c, ++seq) {
@@ -169,14 +179,14 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
                 const unsigned* S = s_b[b];
 #pragma unroll
                 for (int half = 0; half < TC_CHUNK / TC_BLOCK; ++half) {
-                    float bm[16];
+                    float bm[2 * TC_MT];
 #pragma unroll
                     for (int nt = 0; nt < TC_BLOCK / 8; ++nt) {
                         const int grp = half * (TC_BLOCK / 8) + nt;  // group of 8 columns
                         const unsigned b0 = S[grp * 64 + g * 4 + t];
                         const unsigned b1 = S[grp * 64 + 32 + g * 4 + t];
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) {
+                        for (int m = 0; m < TC_MT; ++m) {
                             float d[4];
                             mma_f16(d, a[m], b0, b1);
                             if (nt == 0) {
@@ -192,7 +202,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
                     // it), truncated, with the block (the lane is implied by the key's slot)
                     const unsigned id = (unsigned)(c * (TC_CHUNK / TC_BLOCK) + half);
 #pragma unroll
-                    for (int r = 0; r < 16; ++r)
+                    for (int r = 0; r < 2 * TC_MT; ++r)
                         top3_insert(k1[r], k2[r], k3[r],
                                     (__float_as_uint(fmaxf(bm[r], 0.0f)) & TC_VALUE_MASK) | id);
                 }
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MIN_BLOCKS) k_tcpass(Ws w, int 
                                 ? s_u.kout
                                 : w.kpart + TC_KEYS * ((2LL * blockIdx.x + s_u.slot) * TC_UNIT_ROWS);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < 2 * TC_MT; ++r) {
                 const int ru = wrow0 + 16 * (r >> 1) + g + 8 * (r & 1);
                 unsigned* o = out + TC_KEYS * ru + 3 * t;
                 o[0] = k1[r];
@@ -274,7 +284,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tcmerge(Ws w, int grid) {
     const int urb = w.tc_urb[u];
     const int side = urb >> 30, rb = urb & 0x3fffffff;
     const long long first = (long long)rb * TC_UNIT_ROWS;
-    const int rows = min(TC_UNIT_ROWS, (side ? fr->Mpad : fr->Npad) - (int)first);
+    // the rows whose keys are read: up to the end of the block of the side's last point
+    const int rows = min(TC_UNIT_ROWS, round_up(side ? fr->M : fr->N, TC_BLOCK) - (int)first);
     unsigned* out = side ? w.kba + TC_KEYS * ((long long)fr->col0 + first)
                          : w.kab + TC_KEYS * ((long long)fr->row0 + first);
     // one thread per (row, lane) list
@@ -383,15 +394,17 @@ constexpr int REC_MAX_CAND = 2 * 4;  // candidates per row: two blocks per colum
 // The rows' exact minima from their keys: rows [0, rows) are sim points, rows
 // [rows, total) targets (Eq. 1 only). Each CTA takes a contiguous range of rows, 256 at a
 // time (frames are padded to multiples of 256 rows, so a step's rows lie in one frame, found
-// by walking the frame table forward). Each thread takes one row: it reads the row's 12 keys,
-// computes the threshold once, and lists the candidate blocks (per quarter of the columns,
-// the first two keys under the threshold); a warp prefix sum lays the warp's candidates out in
-// shared memory, and the warp re-checks them eight at a time, four lanes per candidate (its
-// 32 columns, eight per lane) in the direct form, merging into the row's minimum with a shared
-// atomicMin. A row that the keys do not certify (a quarter's third key under the threshold)
-// is queued in its frame's list for k_tcfallback. Writes (distance bits << 32 | index) to
-// pab / pba. (Four lanes per row, each with one quarter's keys, took 81 warp instructions
-// per row: the threshold was computed four times and a warp step covered only 8 rows.)
+// by walking the frame table forward). Each thread takes one row: it reads the row's 12 keys
+// (at the row's form position), computes the threshold once, and lists the candidate block
+// quarters (per quarter, the first two keys under the threshold); a warp prefix sum lays the
+// warp's candidates out in shared memory, and the warp re-checks them four at a time, eight
+// lanes per candidate (its 32 consecutive columns, four per lane) in the direct form, merging
+// into the row's minimum with a shared atomicMin. A row that the keys do not certify (a
+// quarter's third key under the threshold) is queued in its frame's list for k_tcfallback.
+// Writes (distance bits << 32 | index) to pab / pba. (Four lanes per row, each with one
+// quarter's keys, took 81 warp instructions per row: the threshold was computed four times
+// and a warp step covered only 8 rows. With the quarters interleaved in the block, a
+// candidate's re-check read 12 lines of targets for 384 bytes.)
 __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int total) {
     pdl_entry();
     constexpr int NW = REC_THREADS / 32;
@@ -403,7 +416,6 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
     const int st0 = blockIdx.x * per, st1 = min(steps, st0 + per);
     const int n_frames = w.hdr->n_frames;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sub = lane >> 2, l4 = lane & 3;
     int k = -1, side = -1;
     for (int st = st0; st < st1; ++st) {
         const int base = st * REC_THREADS;
@@ -428,8 +440,9 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
         bool full = false;
         float qx = 0.f, qy = 0.f, qz = 0.f;
         if (valid) {
-            const uint4* p =
-                reinterpret_cast<const uint4*>((side ? w.kba : w.kab) + (long long)TC_KEYS * g);
+            // the pass wrote the row's keys at its form position
+            const uint4* p = reinterpret_cast<const uint4*>((side ? w.kba : w.kab) +
+                                                            (long long)TC_KEYS * tc_form_pos(g));
             const uint4 v0 = p[0], v1 = p[1], v2 = p[2];
             // quarter t's keys are kk[3 t], kk[3 t + 1], kk[3 t + 2], smallest first
             kk[0] = v0.x, kk[1] = v0.y, kk[2] = v0.z, kk[3] = v0.w;
@@ -483,44 +496,54 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
                     ((((kk[(j >> 1) * 3 + (j & 1)] & ~TC_VALUE_MASK) << 2) | (unsigned)(j >> 1))
                      << 5) | (unsigned)lane;
         __syncwarp();
-        // each candidate is scanned by four lanes and merged into its row's minimum
-        for (int e0 = 0; e0 < tot; e0 += 8) {
-            const int e = e0 + sub;
+        // each candidate quarter (32 consecutive columns) is scanned by eight lanes, four
+        // candidates per warp step, each instruction reading one whole line per candidate,
+        // and merged into its row's minimum
+        const int c8 = lane >> 3, l8 = lane & 7;
+        for (int e0 = 0; e0 < tot; e0 += 4) {
+            const int e = e0 + c8;
             float bd = INFINITY;
             int bj = 0x7fffffff, er = -1;
             if (e < tot) {
                 const unsigned ent = s_list[warp][e];
                 er = (int)(ent & 31u);
                 const unsigned c = ent >> 5;
-                const int blk = (int)(c >> 2), tq = (int)(c & 3u);
+                // the quarter tq of block blk: points 32 tq .. 32 tq + 31 of the block
+                const int q0 = (int)(c >> 2) * TC_BLOCK + (int)(c & 3u) * (TC_BLOCK / 4);
                 const float ex = s_q[warp][er][0], ey = s_q[warp][er][1], ez = s_q[warp][er][2];
+                if (C.P) {
+                    // sim points: this lane takes q0 + l8 + 8 h (a frame's rows are padded to
+                    // whole blocks, so every load stays inside it)
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    // the block's columns that the pass's lane tq saw: 2 of every group of 8;
-                    // this lane takes groups l4, l4 + 4, l4 + 8 and l4 + 12
-                    const int j0 = blk * TC_BLOCK + 8 * (l4 + 4 * h) + 2 * tq;
-                    if (j0 >= C.n) continue;
-                    float ax, ay, az, bx, by, bz;
-                    if (C.P) {
-                        const float4 p0 = C.P[j0], p1 = C.P[j0 + 1];
-                        ax = p0.x, ay = p0.y, az = p0.z, bx = p1.x, by = p1.y, bz = p1.z;
-                    } else {  // j0 is even and the planes are 8-byte aligned
-                        const float2 X = *reinterpret_cast<const float2*>(C.X + j0);
-                        const float2 Y = *reinterpret_cast<const float2*>(C.Y + j0);
-                        const float2 Z = *reinterpret_cast<const float2*>(C.Z + j0);
-                        ax = X.x, ay = Y.x, az = Z.x, bx = X.y, by = Y.y, bz = Z.y;
+                    for (int h = 0; h < 4; ++h) {
+                        const int j = q0 + l8 + 8 * h;
+                        const float4 p = C.P[j];
+                        const float d = dist2(ex, ey, ez, p.x, p.y, p.z);
+                        if (j < C.n && d < bd) bd = d, bj = j;
                     }
-                    const float d0 = dist2(ex, ey, ez, ax, ay, az);
-                    if (d0 < bd) bd = d0, bj = j0;
-                    const float d1 = dist2(ex, ey, ez, bx, by, bz);
-                    if (j0 + 1 < C.n && d1 < bd) bd = d1, bj = j0 + 1;
+                } else {
+                    // targets: this lane takes q0 + 4 l8 .. q0 + 4 l8 + 3 of each plane (16-byte
+                    // aligned: the planes start at multiples of 256 columns)
+                    const int j = q0 + 4 * l8;
+                    const float4 X = *reinterpret_cast<const float4*>(C.X + j);
+                    const float4 Y = *reinterpret_cast<const float4*>(C.Y + j);
+                    const float4 Z = *reinterpret_cast<const float4*>(C.Z + j);
+                    const float d0 = dist2(ex, ey, ez, X.x, Y.x, Z.x);
+                    const float d1 = dist2(ex, ey, ez, X.y, Y.y, Z.y);
+                    const float d2 = dist2(ex, ey, ez, X.z, Y.z, Z.z);
+                    const float d3 = dist2(ex, ey, ez, X.w, Y.w, Z.w);
+                    if (j < C.n && d0 < bd) bd = d0, bj = j;
+                    if (j + 1 < C.n && d1 < bd) bd = d1, bj = j + 1;
+                    if (j + 2 < C.n && d2 < bd) bd = d2, bj = j + 2;
+                    if (j + 3 < C.n && d3 < bd) bd = d3, bj = j + 3;
                 }
             }
             // (distance bits << 32 | index): the smallest is the lowest index among equals
             u64 key = bj == 0x7fffffff ? EMPTY : pack_d(bd, bj);
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 1));
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 2));
-            if (l4 == 0 && er >= 0) atomicMin(&s_best[warp][er], key);
+            key = min64(key, __shfl_xor_sync(0xffffffffu, key, 4));
+            if (l8 == 0 && er >= 0) atomicMin(&s_best[warp][er], key);
         }
         __syncwarp();
         if (valid) {
@@ -967,7 +990,8 @@ __global__ void __launch_bounds__(T5_THREADS, 1) k_tcpass5(Ws w, int stall, int 
     pdl_trigger();
 }
 
-int g_tc_ctas[64];  // per device: resident CTAs of the persistent grid
+int g_tc_ctas[64];   // per device: resident CTAs of the persistent grid
+int g_rec_ctas[64];  // per device: resident CTAs of the recovery
 
 }  // namespace
 
@@ -1044,8 +1068,18 @@ cudaError_t launch_tcpass(const Ws& w, int engine, int grid, long long total_chu
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one wave of the recovery: its CTAs take equal ranges of row steps
+    if (dev >= 0 && dev < 64 && g_rec_ctas[dev] == 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tcrecover, REC_THREADS, 0) !=
+                cudaSuccess ||
+            occ <= 0)
+            occ = 4;
+        g_rec_ctas[dev] = occ * (sms > 0 ? sms : 1);
+    }
     const int steps = div_up(total, REC_THREADS);
-    const int rgrid = std::min(steps, 8 * (sms > 0 ? sms : 1));
+    const int rgrid =
+        std::min(steps, dev >= 0 && dev < 64 ? g_rec_ctas[dev] : 4 * std::max(sms, 1));
     e = launch_pdl(k_tcrecover, rgrid, REC_THREADS, 0, s, w, rows, total);
     count_launch();
     if (e) return e;
