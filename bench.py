@@ -44,10 +44,10 @@ MMA_SYNC_TFLOPS = 600.0
 #       -k 'regex:k_tcpass$' -s 3 -c 1 python bench.py --workload trajectory_50x50 --steps 3 \
 #       --warmup 3 --no-cpu-baseline [--mode eq2]  (and --workload trajectory_100x100;
 #       -k regex:k_chamfer for --workload single_frame)
-CHAMFER_TRAFFIC_BYTES = {("batched_uneven", "k_tcpass", "eq1"): 7.73e9 + 5.46e9,
-                         ("trajectory_50x50", "k_tcpass", "eq1"): 53.94e6 + 8.33e6,
-                         ("trajectory_50x50", "k_tcpass", "eq2"): 26.27e6 + 0.03e6,
-                         ("trajectory_100x100", "k_tcpass", "eq1"): 429.73e6 + 280.78e6,
+CHAMFER_TRAFFIC_BYTES = {("batched_uneven", "k_tcpass", "eq1"): 7.72e9 + 5.41e9,
+                         ("trajectory_50x50", "k_tcpass", "eq1"): 53.58e6 + 8.11e6,
+                         ("trajectory_50x50", "k_tcpass", "eq2"): 26.11e6 + 0.04e6,
+                         ("trajectory_100x100", "k_tcpass", "eq1"): 431.75e6 + 281.22e6,
                          # the direct engine (--shape direct:2), -k regex:k_chamfer; the
                          # single frame runs on it by default
                          ("single_frame", "k_chamfer<true>", "eq1"): 182.53e3,

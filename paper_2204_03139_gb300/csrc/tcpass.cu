@@ -389,23 +389,29 @@ __device__ __forceinline__ float3 frame_row(const Ws& w, const FrameDesc* fr, in
 }
 
 constexpr int REC_THREADS = 256;     // one row per thread: 256 rows per CTA step
+constexpr int REC_MIN_BLOCKS = 4;    // 64 registers (one small spill): 32 warps per SM
 constexpr int REC_MAX_CAND = 2 * 4;  // candidates per row: two blocks per column quarter
 
 // The rows' exact minima from their keys: rows [0, rows) are sim points, rows
 // [rows, total) targets (Eq. 1 only). Each CTA takes a contiguous range of rows, 256 at a
 // time (frames are padded to multiples of 256 rows, so a step's rows lie in one frame, found
 // by walking the frame table forward). Each thread takes one row: it reads the row's 12 keys
-// (at the row's form position), computes the threshold once, and lists the candidate block
-// quarters (per quarter, the first two keys under the threshold); a warp prefix sum lays the
-// warp's candidates out in shared memory, and the warp re-checks them four at a time, eight
-// lanes per candidate (its 32 consecutive columns, four per lane) in the direct form, merging
-// into the row's minimum with a shared atomicMin. A row that the keys do not certify (a
-// quarter's third key under the threshold) is queued in its frame's list for k_tcfallback.
-// Writes (distance bits << 32 | index) to pab / pba. (Four lanes per row, each with one
-// quarter's keys, took 81 warp instructions per row: the threshold was computed four times
-// and a warp step covered only 8 rows. With the quarters interleaved in the block, a
+// (at the row's form position; loaded during the CTA's previous step), computes the
+// threshold once, and lists the candidate block quarters (per quarter, the first two keys
+// under the threshold); a warp prefix sum lays the warp's candidates out in shared memory,
+// and the warp re-checks them eight at a time, four lanes per candidate (its 32 consecutive
+// columns, eight per lane, in loads of 64 contiguous bytes per candidate) in the direct
+// form, merging into the row's minimum with a shared atomicMin. A row that the keys do not
+// certify (a quarter's third key under the threshold) is queued in its frame's list for
+// k_tcfallback. Writes (distance bits << 32 | index) to pab / pba. Measured on 64 uneven
+// trajectories (176.8 ms per batch): eight lanes per candidate (a whole line per load, four
+// candidates per warp step) took 2.8 to 4.0 ms more, other register budgets (3, 5 or 6 CTAs
+// per SM) 2.2 to 3.3 ms more, no key prefetch 1.9 ms more. (Four lanes per row, each with
+// one quarter's keys, took 81 warp instructions per row: the threshold was computed four
+// times and a warp step covered only 8 rows. With the quarters interleaved in the block, a
 // candidate's re-check read 12 lines of targets for 384 bytes.)
-__global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int total) {
+__global__ void __launch_bounds__(REC_THREADS, REC_MIN_BLOCKS)
+    k_tcrecover(Ws w, int rows, int total) {
     pdl_entry();
     constexpr int NW = REC_THREADS / 32;
     __shared__ float s_q[NW][32][3];                 // per warp: each row's query point
@@ -417,7 +423,25 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
     const int n_frames = w.hdr->n_frames;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int k = -1, side = -1;
+    // the keys of the CTA's next step are loaded during this step's re-checks (every step's
+    // rows lie inside the key arrays: both sides are whole numbers of steps)
+    auto key_ptr = [&](int st_) {
+        const int b_ = st_ * REC_THREADS;
+        const int g_ = (b_ >= rows ? b_ - rows : b_) + (int)threadIdx.x;
+        return reinterpret_cast<const uint4*>((b_ >= rows ? w.kba : w.kab) +
+                                              (long long)TC_KEYS * tc_form_pos(g_));
+    };
+    uint4 n0 = make_uint4(0, 0, 0, 0), n1 = n0, n2 = n0;
+    if (st0 < st1) {
+        const uint4* p = key_ptr(st0);
+        n0 = p[0], n1 = p[1], n2 = p[2];
+    }
     for (int st = st0; st < st1; ++st) {
+        const uint4 v0 = n0, v1 = n1, v2 = n2;  // this step's rows' keys
+        if (st + 1 < st1) {
+            const uint4* p = key_ptr(st + 1);
+            n0 = p[0], n1 = p[1], n2 = p[2];
+        }
         const int base = st * REC_THREADS;
         const int sd = base >= rows ? 1 : 0;
         const int g0 = sd ? base - rows : base;  // first row of the step within its side
@@ -440,10 +464,6 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
         bool full = false;
         float qx = 0.f, qy = 0.f, qz = 0.f;
         if (valid) {
-            // the pass wrote the row's keys at its form position
-            const uint4* p = reinterpret_cast<const uint4*>((side ? w.kba : w.kab) +
-                                                            (long long)TC_KEYS * tc_form_pos(g));
-            const uint4 v0 = p[0], v1 = p[1], v2 = p[2];
             // quarter t's keys are kk[3 t], kk[3 t + 1], kk[3 t + 2], smallest first
             kk[0] = v0.x, kk[1] = v0.y, kk[2] = v0.z, kk[3] = v0.w;
             kk[4] = v1.x, kk[5] = v1.y, kk[6] = v1.z, kk[7] = v1.w;
@@ -496,12 +516,13 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
                     ((((kk[(j >> 1) * 3 + (j & 1)] & ~TC_VALUE_MASK) << 2) | (unsigned)(j >> 1))
                      << 5) | (unsigned)lane;
         __syncwarp();
-        // each candidate quarter (32 consecutive columns) is scanned by eight lanes, four
-        // candidates per warp step, each instruction reading one whole line per candidate,
-        // and merged into its row's minimum
-        const int c8 = lane >> 3, l8 = lane & 7;
-        for (int e0 = 0; e0 < tot; e0 += 4) {
-            const int e = e0 + c8;
+        // each candidate quarter (32 consecutive columns) is scanned by four lanes, eight
+        // candidates per warp step, eight columns per lane in contiguous loads (the four
+        // lanes of a candidate read 64 contiguous bytes per instruction), and merged into its
+        // row's minimum
+        const int sub = lane >> 2, l4 = lane & 3;
+        for (int e0 = 0; e0 < tot; e0 += 8) {
+            const int e = e0 + sub;
             float bd = INFINITY;
             int bj = 0x7fffffff, er = -1;
             if (e < tot) {
@@ -512,38 +533,47 @@ __global__ void __launch_bounds__(REC_THREADS) k_tcrecover(Ws w, int rows, int t
                 const int q0 = (int)(c >> 2) * TC_BLOCK + (int)(c & 3u) * (TC_BLOCK / 4);
                 const float ex = s_q[warp][er][0], ey = s_q[warp][er][1], ez = s_q[warp][er][2];
                 if (C.P) {
-                    // sim points: this lane takes q0 + l8 + 8 h (a frame's rows are padded to
+                    // sim points: this lane takes q0 + l4 + 4 h (a frame's rows are padded to
                     // whole blocks, so every load stays inside it)
+                    float4 p[8];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int j = q0 + l8 + 8 * h;
-                        const float4 p = C.P[j];
-                        const float d = dist2(ex, ey, ez, p.x, p.y, p.z);
+                    for (int h = 0; h < 8; ++h) p[h] = C.P[q0 + l4 + 4 * h];
+#pragma unroll
+                    for (int h = 0; h < 8; ++h) {
+                        const int j = q0 + l4 + 4 * h;
+                        const float d = dist2(ex, ey, ez, p[h].x, p[h].y, p[h].z);
                         if (j < C.n && d < bd) bd = d, bj = j;
                     }
                 } else {
-                    // targets: this lane takes q0 + 4 l8 .. q0 + 4 l8 + 3 of each plane (16-byte
-                    // aligned: the planes start at multiples of 256 columns)
-                    const int j = q0 + 4 * l8;
-                    const float4 X = *reinterpret_cast<const float4*>(C.X + j);
-                    const float4 Y = *reinterpret_cast<const float4*>(C.Y + j);
-                    const float4 Z = *reinterpret_cast<const float4*>(C.Z + j);
-                    const float d0 = dist2(ex, ey, ez, X.x, Y.x, Z.x);
-                    const float d1 = dist2(ex, ey, ez, X.y, Y.y, Z.y);
-                    const float d2 = dist2(ex, ey, ez, X.z, Y.z, Z.z);
-                    const float d3 = dist2(ex, ey, ez, X.w, Y.w, Z.w);
-                    if (j < C.n && d0 < bd) bd = d0, bj = j;
-                    if (j + 1 < C.n && d1 < bd) bd = d1, bj = j + 1;
-                    if (j + 2 < C.n && d2 < bd) bd = d2, bj = j + 2;
-                    if (j + 3 < C.n && d3 < bd) bd = d3, bj = j + 3;
+                    // targets: this lane takes q0 + 4 l4 + 16 h .. q0 + 4 l4 + 16 h + 3 (h < 2)
+                    // of each plane (16-byte aligned: the planes start at multiples of 256)
+                    float4 X[2], Y[2], Z[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = q0 + 4 * l4 + 16 * h;
+                        X[h] = *reinterpret_cast<const float4*>(C.X + j);
+                        Y[h] = *reinterpret_cast<const float4*>(C.Y + j);
+                        Z[h] = *reinterpret_cast<const float4*>(C.Z + j);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = q0 + 4 * l4 + 16 * h;
+                        const float d0 = dist2(ex, ey, ez, X[h].x, Y[h].x, Z[h].x);
+                        const float d1 = dist2(ex, ey, ez, X[h].y, Y[h].y, Z[h].y);
+                        const float d2 = dist2(ex, ey, ez, X[h].z, Y[h].z, Z[h].z);
+                        const float d3 = dist2(ex, ey, ez, X[h].w, Y[h].w, Z[h].w);
+                        if (j < C.n && d0 < bd) bd = d0, bj = j;
+                        if (j + 1 < C.n && d1 < bd) bd = d1, bj = j + 1;
+                        if (j + 2 < C.n && d2 < bd) bd = d2, bj = j + 2;
+                        if (j + 3 < C.n && d3 < bd) bd = d3, bj = j + 3;
+                    }
                 }
             }
             // (distance bits << 32 | index): the smallest is the lowest index among equals
             u64 key = bj == 0x7fffffff ? EMPTY : pack_d(bd, bj);
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 1));
             key = min64(key, __shfl_xor_sync(0xffffffffu, key, 2));
-            key = min64(key, __shfl_xor_sync(0xffffffffu, key, 4));
-            if (l8 == 0 && er >= 0) atomicMin(&s_best[warp][er], key);
+            if (l4 == 0 && er >= 0) atomicMin(&s_best[warp][er], key);
         }
         __syncwarp();
         if (valid) {
