@@ -619,6 +619,8 @@ __global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows, int s
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int PER_CTA = FB_ROWS_PER_WARP * (FB_THREADS / 32);
     for (int r0 = 0; r0 < n; r0 += PER_CTA) {
+        // a warp without a queued row only helps stage the tiles (most lists are short)
+        const bool wrows = r0 + warp * FB_ROWS_PER_WARP < n;
         float qx[FB_ROWS_PER_WARP], qy[FB_ROWS_PER_WARP], qz[FB_ROWS_PER_WARP];
         u64 best[FB_ROWS_PER_WARP];
 #pragma unroll
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows, int s
                 s_c[2][j] = z;
             }
             __syncthreads();
-            const int jn = min(FB_TILE, jb - j0);
+            const int jn = wrows ? min(FB_TILE, jb - j0) : 0;
             for (int j = lane; j < jn; j += 32) {
                 const float cx = s_c[0][j], cy = s_c[1][j], cz = s_c[2][j];
 #pragma unroll
@@ -672,8 +674,8 @@ __global__ void __launch_bounds__(FB_THREADS) k_tcfallback(Ws w, int rows, int s
 // odd ones. 8 consumer warps hold one row per thread (tile t is read by warps 4t .. 4t+3, one
 // lane quarter each) and read their tile's two slots in turn, so a slot's refill with the
 // block after next runs while the warp reads the other one. Each warp folds a block into the
-// four column subsets (2 of every 8) and their keys exactly as the warp-level kernel does, so
-// the keys, their merge across CTAs and the recovery are shared. One MMA warp per slot
+// four column subsets (2 of every 8 positions) and their keys exactly as the warp-level kernel
+// does, so the keys, their merge across CTAs and the recovery are shared. One MMA warp per slot
 // issues its MMAs (a bounded wait for the slot's release and for the chunk, then the MMA and
 // its commit), and a producer warp streams the column chunks through four shared-memory
 // buffers with bulk copies.
