@@ -65,7 +65,7 @@ constexpr unsigned long long EMPTY = ~0ull;
 #define DC_TC_ROWS_PER_WARP 128
 #endif
 constexpr int TC_WARPS = DC_TC_WARPS;                       // warps per CTA
-constexpr int TC_ROWS_PER_WARP = DC_TC_ROWS_PER_WARP;       // m16 tiles per warp, times 16
+constexpr int TC_ROWS_PER_WARP = DC_TC_ROWS_PER_WARP;       // rows per warp (16 per m16 tile)
 constexpr int TC_UNIT_ROWS = TC_WARPS * TC_ROWS_PER_WARP;   // rows per work unit (512)
 constexpr int TC_CHUNK = 256;                               // columns per staged chunk
 constexpr int TC_BLOCK = 128;                               // columns per key block
